@@ -1,0 +1,155 @@
+/*
+ * tenergy.h - C ABI of the GB300 library for the closed-shell perturbative
+ * triples energy E(T) of an embedded cluster (supplement section "The In-situ
+ * Form of Perturbative (T) in SIE", Eqs. E_corr_CCSD_T, W, V, D, P and R, with
+ * the fragment projector C^f taken as the identity).
+ *
+ *   E(T) = (1/3) sum_{ijk} sum_{abc} W~_{ijk}^{abc} R[W~ + Y]_{ijk}^{abc} / D_{ijk}^{abc}
+ *
+ *   W~ = P[ sum_d (ia|bd) t_kj^cd - sum_l (ia|jl) t_lk^bc ]      (Eq. W times D)
+ *   Y  = 1/2 P[ (ia|jb) t_k^c ]                                   (Eq. V times D)
+ *   D  = e_i + e_j + e_k - e_a - e_b - e_c                         (Eq. D)
+ *
+ * which equals the printed restricted sum 2 sum_{a>=b>=c} A R[Z] W~ (Eq.
+ * E_corr_CCSD_T) exactly.  Clusters are independent (Eq. C_f: E = sum_x E_x).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - All array pointers are DEVICE pointers to float64, C-contiguous
+ *   (row-major), owned by the caller; the library never frees them:
+ *     eps_o [o]          occupied orbital energies (Ha)
+ *     eps_v [v]          virtual orbital energies (Ha)
+ *     ovvv  [o][v][v][v] ovvv[i,a,b,d] = (ia|bd)
+ *     ooov  [o][o][o][v] ooov[j,l,i,a] = (jl|ia)  (= (ia|jl) for real orbitals)
+ *     ovov  [o][v][o][v] ovov[i,a,j,b] = (ia|jb)
+ *     t1    [o][v]       t1[i,a]       = t_i^a
+ *     t2    [o][o][v][v] t2[i,j,a,b]   = t_ij^ab
+ *   with o = nocc >= 1, v = nvir >= 1.  No symmetry of any array is assumed.
+ * - The orbital energies must satisfy max(eps_o) < min(eps_v) (every D < 0);
+ *   they need not be sorted.  Inputs must be finite.
+ * - Calls are asynchronous on the given CUDA stream (0 = legacy default
+ *   stream).  Argument errors are reported before any launch (TE_EINVAL),
+ *   workspace allocation failures as TE_ENOMEM, launch failures as TE_ECUDA.
+ *   A device-side watchdog never traps: a kernel whose bounded wait expires
+ *   records an error word and returns; te_sync() reports it as TE_ETIMEOUT.
+ * - Results are deterministic: fixed-order reductions, no floating-point
+ *   atomics; repeated calls give bitwise identical outputs.
+ * - A handle owns its workspace (operand copies for the mixed modes, partial
+ *   results); one handle must not be used from two host threads at once, and
+ *   calls made on one handle with different streams must be ordered by the
+ *   caller.  No exception crosses the ABI.
+ *
+ * Precision modes (the paper states no precision):
+ *   TE_FP64    W~ contractions and everything else in float64 (DFMA);
+ *   TE_TF32    W~ contractions on tcgen05 tensor cores, operands rounded to
+ *              TF32, FP32 accumulation;
+ *   TE_BF16X3  operands split x = hi + lo (hi = bf16(x), lo = bf16(x - hi)),
+ *              three products hi*hi + hi*lo + lo*hi on tcgen05 (kind::f16),
+ *              FP32 accumulation;
+ *   TE_TF32X3  the same split with TF32 parts (kind::tf32).
+ *   In every mode D, 1/D, the products with 1/D and all sums are float64.
+ */
+#ifndef TENERGY_H
+#define TENERGY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* te_stream_t; /* the same type as cudaStream_t */
+
+typedef enum {
+  TE_OK = 0,
+  TE_EINVAL = 1,        /* bad argument: null pointer, size, ordering of eps */
+  TE_ENOMEM = 2,        /* workspace could not be allocated */
+  TE_ECUDA = 3,         /* a CUDA runtime/driver call or launch failed */
+  TE_ETIMEOUT = 4,      /* a device-side bounded wait expired (see te_sync) */
+  TE_EUNSUPPORTED = 5   /* mode or size not supported on this device */
+} te_status;
+
+typedef enum {
+  TE_FP64 = 0,
+  TE_TF32 = 1,
+  TE_BF16X3 = 2,
+  TE_TF32X3 = 3
+} te_precision;
+
+typedef struct {
+  int64_t nocc, nvir;
+  const double *eps_o, *eps_v, *ovvv, *ooov, *ovov, *t1, *t2;
+} te_cluster;
+
+/* Gradient buffers: device float64, same shapes as the te_cluster arrays,
+ * caller-allocated, overwritten (not accumulated).  A null member skips that
+ * gradient. */
+typedef struct {
+  double *eps_o, *eps_v, *ovvv, *ooov, *ovov, *t1, *t2;
+} te_cluster_grad;
+
+typedef struct te_handle_s* te_handle;
+
+/* Create a handle bound to CUDA device `device`.  Allocates nothing on the
+ * device until the first compute call.  *h is set to NULL on failure. */
+te_status te_create(te_handle* h, int device);
+
+/* Free the handle and its workspace (synchronises the device first). */
+te_status te_destroy(te_handle h);
+
+/* E(T) of one cluster.  e_out: device pointer to one double, overwritten.
+ * The sum over unique occupied triples (i >= j >= k, not all equal) of the
+ * per-triple shares (see t_energy_triples), reduced in a fixed order with
+ * compensated float64 summation. */
+te_status t_energy(te_handle h, const te_cluster* c, te_precision p,
+                   double* e_out, te_stream_t s);
+
+/* Per-triple shares of E(T) for the unique occupied triples with canonical
+ * index t in [t_begin, t_end).  Canonical order: lexicographic in (i, j, k)
+ * over i >= j >= k with i = j = k left out (there R vanishes), i.e. for
+ * nocc = 3: (1,0,0) (1,1,0) (2,0,0) (2,1,0) (2,1,1) (2,2,0) (2,2,1).  There are
+ * nocc (nocc+1)(nocc+2)/6 - nocc triples.  e_triples: device array of
+ * (t_end - t_begin) doubles, overwritten with (m/3) e_ijk where m is the
+ * number of distinct orderings of (i,j,k) and
+ *   e_ijk = sum_{abc} W~_{ijk}^{abc} R[W~ + Y]_{ijk}^{abc} / D_{ijk}^{abc}.
+ * Summed over all triples this is E(T).  Useful to shard a cluster, to
+ * resume, or to check sampled triples. */
+te_status t_energy_triples(te_handle h, const te_cluster* c, te_precision p,
+                           int64_t t_begin, int64_t t_end,
+                           double* e_triples, te_stream_t s);
+
+/* E(T) of n independent clusters (Eq. C_f: clusters do not interact).
+ * cs: HOST array of n cluster descriptors (their array pointers are device
+ * pointers).  e_out: device array of n doubles, e_out[x] = E(T) of cluster x. */
+te_status t_energy_batched(te_handle h, const te_cluster* cs, int64_t n,
+                           te_precision p, double* e_out, te_stream_t s);
+
+/* Vector-Jacobian product of E(T): g.X = gE * dE/dX for every non-null member
+ * of *g, every stored entry of every input treated as an independent variable
+ * (no symmetrisation of t2 or of the integrals).  If e_out is non-null it
+ * receives E(T) (one device double). */
+te_status t_energy_vjp(te_handle h, const te_cluster* c, te_precision p,
+                       double gE, double* e_out, te_cluster_grad* g,
+                       te_stream_t s);
+
+/* Wait for the work of handle h on stream s and report a device-side
+ * watchdog expiry (TE_ETIMEOUT) or an asynchronous CUDA error (TE_ECUDA). */
+te_status te_sync(te_handle h, te_stream_t s);
+
+/* Device bytes the handle's workspace would need for this cluster and mode
+ * (before any call), so a caller can check memory up front. */
+te_status te_workspace_bytes(te_handle h, const te_cluster* c, te_precision p,
+                             size_t* bytes);
+
+/* Message for the last non-OK status returned on the calling host thread. */
+const char* te_last_error(void);
+
+/* Test hook for the device watchdog: limit (ns) for every bounded wait of
+ * later launches on this handle; 0 restores the default (4 s). */
+te_status te_set_wait_limit_ns(te_handle h, uint64_t ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TENERGY_H */

@@ -1,0 +1,237 @@
+"""GB300-native perturbative-triples energy E(T) of embedded clusters.
+
+Thin Python binding of libtenergy (C ABI in include/tenergy.h): it marshals
+torch tensors into the C descriptors and passes torch's current CUDA stream.
+Every step of the computation runs in the library's CUDA kernels; if the
+library is missing, importing the compute functions raises.
+
+Inputs (float64; CUDA tensors are used in place, host tensors or numpy arrays
+are copied to the device first):
+  eps_o [o], eps_v [v], ovvv [o,v,v,v] = (ia|bd), ooov [o,o,o,v] = (jl|ia),
+  ovov [o,v,o,v] = (ia|jb), t1 [o,v], t2 [o,o,v,v].
+Precision: "fp64", "tf32", "bf16x3", "tf32x3".
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import PRECISIONS, TEnergyError, TeCluster, TeClusterGrad
+
+NAMES = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
+
+__all__ = ["Handle", "t_energy", "t_energy_triples", "t_energy_batched", "t_energy_vjp",
+           "TEnergy", "num_unique_triples", "flop_count", "TEnergyError", "NAMES"]
+
+
+def num_unique_triples(nocc: int) -> int:
+    """Occupied triples i >= j >= k with i = j = k left out."""
+    return nocc * (nocc + 1) * (nocc + 2) // 6 - nocc
+
+
+def flop_count(nocc: int, nvir: int) -> float:
+    """Algorithmic flops of one cluster: F = 12 (C(o+2,3) - o) v^3 (v + o)."""
+    return 12.0 * num_unique_triples(nocc) * float(nvir) ** 3 * (nvir + nocc)
+
+
+class Handle:
+    """Owns the library handle (workspace) for one CUDA device."""
+
+    def __init__(self, device=None):
+        lib = _lib.load()
+        if device is None:
+            dev = torch.cuda.current_device()
+        elif isinstance(device, int):
+            dev = device
+        else:
+            dev = torch.device(device).index or 0
+        h = ctypes.c_void_p()
+        _lib.check(lib.te_create(ctypes.byref(h), dev))
+        self._h = h
+        self.device = dev
+
+    @property
+    def ptr(self):
+        if self._h is None:
+            raise RuntimeError("handle closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.load().te_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sync(self, stream=None):
+        s = _stream(self.device, stream)
+        _lib.check(_lib.load().te_sync(self.ptr, s))
+
+    def set_wait_limit_ns(self, ns: int):
+        _lib.check(_lib.load().te_set_wait_limit_ns(self.ptr, int(ns)))
+
+    def workspace_bytes(self, cluster, precision="fp64") -> int:
+        t = _tensors(cluster, self.device)
+        c = _struct(t)
+        out = ctypes.c_size_t()
+        _lib.check(_lib.load().te_workspace_bytes(self.ptr, ctypes.byref(c), _prec(precision),
+                                                  ctypes.byref(out)))
+        return int(out.value)
+
+
+_DEFAULT = {}
+
+
+def _handle(handle, device):
+    if handle is not None:
+        return handle
+    if device not in _DEFAULT:
+        _DEFAULT[device] = Handle(device)
+    return _DEFAULT[device]
+
+
+def _prec(p):
+    if isinstance(p, int):
+        return p
+    try:
+        return PRECISIONS[p.lower()]
+    except KeyError:
+        raise ValueError(f"unknown precision {p!r}; one of {sorted(PRECISIONS)}") from None
+
+
+def _stream(device, stream):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _as_dict(cluster):
+    if isinstance(cluster, dict):
+        return cluster
+    if hasattr(cluster, "arrays"):
+        return cluster.arrays()
+    if isinstance(cluster, (tuple, list)) and len(cluster) == 7:
+        return dict(zip(NAMES, cluster))
+    raise TypeError("cluster must be a dict, a 7-tuple or an object with .arrays()")
+
+
+def _tensors(cluster, device):
+    d = _as_dict(cluster)
+    dev = torch.device("cuda", device)
+    out = {}
+    for n in NAMES:
+        x = d[n]
+        t = x if isinstance(x, torch.Tensor) else torch.as_tensor(x)
+        if t.dtype != torch.float64:
+            raise TypeError(f"{n} must be float64, got {t.dtype}")
+        if t.device != dev:
+            t = t.to(dev, non_blocking=True)
+        out[n] = t.contiguous()
+    o, v = out["eps_o"].shape[0], out["eps_v"].shape[0]
+    want = dict(eps_o=(o,), eps_v=(v,), ovvv=(o, v, v, v), ooov=(o, o, o, v), ovov=(o, v, o, v),
+                t1=(o, v), t2=(o, o, v, v))
+    for n, shp in want.items():
+        if tuple(out[n].shape) != shp:
+            raise ValueError(f"{n} has shape {tuple(out[n].shape)}, expected {shp}")
+    return out
+
+
+def _struct(t):
+    return TeCluster(t["eps_o"].shape[0], t["eps_v"].shape[0],
+                     *(ctypes.c_void_p(t[n].data_ptr()) for n in NAMES))
+
+
+def _device_of(cluster, device):
+    if device is not None:
+        return torch.device(device).index if not isinstance(device, int) else device
+    for n in NAMES:
+        x = _as_dict(cluster)[n]
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            return x.device.index
+    return torch.cuda.current_device()
+
+
+def t_energy(cluster, precision="fp64", handle=None, device=None, stream=None) -> torch.Tensor:
+    """E(T) of one cluster as a 0-dim float64 CUDA tensor."""
+    dev = _device_of(cluster, device)
+    h = _handle(handle, dev)
+    t = _tensors(cluster, dev)
+    c = _struct(t)
+    out = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
+    _lib.check(_lib.load().t_energy(h.ptr, ctypes.byref(c), _prec(precision),
+                                    ctypes.c_void_p(out.data_ptr()), _stream(dev, stream)))
+    return out
+
+
+def t_energy_triples(cluster, t_begin=0, t_end=None, precision="fp64", handle=None, device=None,
+                     stream=None) -> torch.Tensor:
+    """Per-triple shares (m/3) e_ijk for canonical triple indices [t_begin, t_end)."""
+    dev = _device_of(cluster, device)
+    h = _handle(handle, dev)
+    t = _tensors(cluster, dev)
+    if t_end is None:
+        t_end = num_unique_triples(t["eps_o"].shape[0])
+    out = torch.empty((max(0, t_end - t_begin),), dtype=torch.float64, device=torch.device("cuda", dev))
+    c = _struct(t)
+    _lib.check(_lib.load().t_energy_triples(h.ptr, ctypes.byref(c), _prec(precision), int(t_begin),
+                                            int(t_end), ctypes.c_void_p(out.data_ptr()),
+                                            _stream(dev, stream)))
+    return out
+
+
+def t_energy_batched(clusters, precision="fp64", handle=None, device=None, stream=None) -> torch.Tensor:
+    """E(T) of each of several independent clusters (float64 CUDA tensor [n])."""
+    clusters = list(clusters)
+    dev = _device_of(clusters[0], device) if clusters else (device or torch.cuda.current_device())
+    h = _handle(handle, dev)
+    ts = [_tensors(c, dev) for c in clusters]
+    arr = (TeCluster * max(1, len(ts)))(*[_struct(t) for t in ts])
+    out = torch.empty((len(ts),), dtype=torch.float64, device=torch.device("cuda", dev))
+    _lib.check(_lib.load().t_energy_batched(h.ptr, arr, len(ts), _prec(precision),
+                                            ctypes.c_void_p(out.data_ptr()), _stream(dev, stream)))
+    return out
+
+
+def t_energy_vjp(cluster, gE=1.0, precision="fp64", handle=None, device=None, stream=None):
+    """(E, grads): grads[name] = gE * dE/d(name) for all seven inputs."""
+    dev = _device_of(cluster, device)
+    h = _handle(handle, dev)
+    t = _tensors(cluster, dev)
+    grads = {n: torch.empty_like(t[n]) for n in NAMES}
+    g = TeClusterGrad(*(ctypes.c_void_p(grads[n].data_ptr()) for n in NAMES))
+    e = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
+    c = _struct(t)
+    _lib.check(_lib.load().t_energy_vjp(h.ptr, ctypes.byref(c), _prec(precision), float(gE),
+                                        ctypes.c_void_p(e.data_ptr()), ctypes.byref(g),
+                                        _stream(dev, stream)))
+    return e, grads
+
+
+class TEnergy(torch.autograd.Function):
+    """E(T) as a differentiable function of (eps_o, eps_v, ovvv, ooov, ovov, t1, t2);
+    the backward pass calls the library's adjoint (t_energy_vjp)."""
+
+    @staticmethod
+    def forward(ctx, eps_o, eps_v, ovvv, ooov, ovov, t1, t2, precision="fp64"):
+        cl = dict(zip(NAMES, (eps_o, eps_v, ovvv, ooov, ovov, t1, t2)))
+        ctx.save_for_backward(eps_o, eps_v, ovvv, ooov, ovov, t1, t2)
+        ctx.precision = precision
+        return t_energy(cl, precision)
+
+    @staticmethod
+    def backward(ctx, gout):
+        cl = dict(zip(NAMES, ctx.saved_tensors))
+        _, g = t_energy_vjp(cl, float(gout), ctx.precision)
+        return tuple(g[n] for n in NAMES) + (None,)

@@ -1,0 +1,383 @@
+// C-ABI entry points of libtenergy (declared in include/tenergy.h): argument
+// validation, handle workspace, and the launch sequence of each call.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "te_internal.h"
+#include "tc_path.h"
+
+namespace te {
+
+static thread_local char g_last_error[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
+
+te_status fail(te_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+std::vector<Triple> unique_triples(int nocc) {
+  std::vector<Triple> out;
+  for (int i = 0; i < nocc; ++i)
+    for (int j = 0; j <= i; ++j)
+      for (int k = 0; k <= j; ++k) {
+        if (i == j && j == k) continue;
+        const int m = (i == j || j == k) ? 3 : 6;
+        out.push_back(Triple{i, j, k, m});
+      }
+  return out;
+}
+
+int64_t num_unique_triples(int64_t nocc) { return nocc * (nocc + 1) * (nocc + 2) / 6 - nocc; }
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Bump allocator over the handle workspace.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+static te_status ensure_workspace(Handle* h, size_t bytes) {
+  if (h->ws_bytes >= bytes) return TE_OK;
+  if (h->ws) {
+    cudaDeviceSynchronize();  // no launch may still read the old workspace
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  const size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->ws = nullptr;
+      return fail(TE_ENOMEM, "workspace allocation of %zu bytes failed", bytes);
+    }
+    h->ws_bytes = bytes;
+    return TE_OK;
+  }
+  h->ws_bytes = want;
+  return TE_OK;
+}
+
+static te_status ensure_triples(Handle* h, int nocc) {
+  if (h->triples_nocc == nocc) return TE_OK;
+  std::vector<Triple> t = unique_triples(nocc);
+  const size_t need = std::max<size_t>(1, t.size());
+  if (h->triples_cap < need) {
+    if (h->d_triples) {
+      cudaDeviceSynchronize();
+      cudaFree(h->d_triples);
+      h->d_triples = nullptr;
+    }
+    if (cudaMalloc(&h->d_triples, need * sizeof(Triple)) != cudaSuccess) {
+      cudaGetLastError();
+      h->d_triples = nullptr;
+      h->triples_cap = 0;
+      h->triples_nocc = -1;
+      return fail(TE_ENOMEM, "triple table allocation failed");
+    }
+    h->triples_cap = need;
+  } else {
+    cudaDeviceSynchronize();  // earlier launches may still read the table
+  }
+  if (!t.empty() && cudaMemcpy(h->d_triples, t.data(), t.size() * sizeof(Triple),
+                               cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(TE_ECUDA, "triple table upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->triples_nocc = nocc;
+  return TE_OK;
+}
+
+static te_status validate(const Handle* h, const te_cluster* c, te_precision p, cudaStream_t s) {
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (!c) return fail(TE_EINVAL, "null cluster descriptor");
+  if (c->nocc < 1 || c->nvir < 1) return fail(TE_EINVAL, "nocc and nvir must be >= 1 (got %lld, %lld)",
+                                              (long long)c->nocc, (long long)c->nvir);
+  if (c->nocc > 2048 || c->nvir > 4096)
+    return fail(TE_EUNSUPPORTED, "cluster too large (nocc <= 2048, nvir <= 4096)");
+  if (!c->eps_o || !c->eps_v || !c->ovvv || !c->ooov || !c->ovov || !c->t1 || !c->t2)
+    return fail(TE_EINVAL, "null array pointer in cluster descriptor");
+  if (p != TE_FP64 && p != TE_TF32 && p != TE_BF16X3 && p != TE_TF32X3)
+    return fail(TE_EINVAL, "unknown precision mode %d", (int)p);
+  // every denominator must be negative: max eps_o < min eps_v
+  std::vector<double> eo(c->nocc), ev(c->nvir);
+  if (cudaMemcpyAsync(eo.data(), c->eps_o, c->nocc * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(ev.data(), c->eps_v, c->nvir * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(TE_ECUDA, "reading orbital energies failed: %s", cudaGetErrorString(cudaGetLastError()));
+  double mo = -1e300, mv = 1e300;
+  for (double x : eo) {
+    if (!(x == x) || x > 1e300 || x < -1e300) return fail(TE_EINVAL, "non-finite eps_o");
+    mo = std::max(mo, x);
+  }
+  for (double x : ev) {
+    if (!(x == x) || x > 1e300 || x < -1e300) return fail(TE_EINVAL, "non-finite eps_v");
+    mv = std::min(mv, x);
+  }
+  if (!(mo < mv)) return fail(TE_EINVAL, "max(eps_o) = %g must be below min(eps_v) = %g", mo, mv);
+  return TE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 path
+// ---------------------------------------------------------------------------
+
+struct Fp64Plan {
+  int nslots;
+  int64_t nbt;
+  size_t bytes;
+};
+
+static int fp64_slots(const Handle* h, int64_t v, int64_t ntri) {
+  const int64_t tiles = ((v * v + 63) / 64) * ((v + 63) / 64) * 3;
+  int64_t want = (8LL * std::max(1, h->num_sms) + tiles - 1) / tiles;
+  const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(1536LL << 20) / (24 * v * v * v));
+  want = std::min<int64_t>({want, mem_cap, 4096, std::max<int64_t>(1, ntri)});
+  return (int)std::max<int64_t>(1, want);
+}
+
+static size_t fp64_carve(Carver& cv, int64_t o, int64_t v, int nslots, int64_t nbt, int64_t ntri,
+                         Prepared* P, double** gbuf, double** partials, double** etri) {
+  P->t2L = cv.take<double>(o * v * v * o);
+  P->nooT = cv.take<double>(o * o * v * o);
+  P->ovs = cv.take<double>(o * v * o * v);
+  P->ovs32 = nullptr;
+  P->t1_32 = nullptr;
+  *gbuf = cv.take<double>((size_t)nslots * 3 * v * v * v);
+  *partials = cv.take<double>((size_t)nslots * nbt);
+  *etri = cv.take<double>((size_t)std::max<int64_t>(1, ntri));
+  return cv.off;
+}
+
+static te_status run_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_end,
+                          double* e_tri_out, double* e_total_out, cudaStream_t s) {
+  const int64_t o = c->nocc, v = c->nvir;
+  const int64_t ntri_all = num_unique_triples(o);
+  const int64_t nt = t_end - t_begin;
+  const int nslots = fp64_slots(h, v, nt);
+  const int64_t nbt = energy_num_block_triples(v);
+  Prepared P{};
+  double *gbuf, *partials, *etri;
+  Carver probe(nullptr);
+  const size_t bytes = fp64_carve(probe, o, v, nslots, nbt, ntri_all, &P, &gbuf, &partials, &etri);
+  te_status st = ensure_workspace(h, bytes);
+  if (st != TE_OK) return st;
+  st = ensure_triples(h, (int)o);
+  if (st != TE_OK) return st;
+  Carver cv(h->ws);
+  fp64_carve(cv, o, v, nslots, nbt, ntri_all, &P, &gbuf, &partials, &etri);
+  P.o = (int)o;
+  P.v = (int)v;
+  P.eps_o = c->eps_o;
+  P.eps_v = c->eps_v;
+  P.ovvv = c->ovvv;
+  P.t2 = c->t2;
+  P.t1 = c->t1;
+  cudaError_t e = launch_prep_fp64(c, &P, s);
+  if (e != cudaSuccess) return fail(TE_ECUDA, "prep launch: %s", cudaGetErrorString(e));
+  double* out = e_tri_out ? e_tri_out : etri;
+  for (int64_t t0 = t_begin; t0 < t_end; t0 += nslots) {
+    const int ns = (int)std::min<int64_t>(nslots, t_end - t0);
+    e = launch_gemm_fp64(&P, h->d_triples, t0, ns, gbuf, s);
+    if (e == cudaSuccess) e = launch_energy_f64(&P, h->d_triples, t0, ns, gbuf, partials, nbt, s);
+    if (e == cudaSuccess)
+      e = launch_reduce_triples(partials, nbt, h->d_triples, t0, ns, out + (t0 - t_begin), s);
+    if (e != cudaSuccess) return fail(TE_ECUDA, "fp64 launch: %s", cudaGetErrorString(e));
+  }
+  if (e_total_out) {
+    e = launch_reduce_total(out, nt, e_total_out, s);
+    if (e != cudaSuccess) return fail(TE_ECUDA, "reduction launch: %s", cudaGetErrorString(e));
+  }
+  return TE_OK;
+}
+
+static te_status run_any(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin,
+                         int64_t t_end, double* e_tri_out, double* e_total_out, cudaStream_t s) {
+  if (p == TE_FP64) return run_fp64(h, c, t_begin, t_end, e_tri_out, e_total_out, s);
+  return run_tc(h, c, p, t_begin, t_end, e_tri_out, e_total_out, s);
+}
+
+}  // namespace te
+
+using namespace te;
+
+extern "C" {
+
+te_status te_create(te_handle* out, int device) {
+  if (!out) return fail(TE_EINVAL, "null handle pointer");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return fail(TE_ECUDA, "no CUDA device available");
+  }
+  if (device < 0 || device >= ndev) return fail(TE_EINVAL, "device %d out of range [0,%d)", device, ndev);
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+    return fail(TE_ECUDA, "cudaGetDeviceProperties failed");
+  Handle* h = new Handle();
+  h->device = device;
+  h->num_sms = prop.multiProcessorCount;
+  h->smem_optin = prop.sharedMemPerBlockOptin;
+  h->cc_major = prop.major;
+  h->cc_minor = prop.minor;
+  if (cudaMalloc(&h->d_err, sizeof(unsigned int) * 4) != cudaSuccess ||
+      cudaMemset(h->d_err, 0, sizeof(unsigned int) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(TE_ENOMEM, "error-word allocation failed");
+  }
+  *out = reinterpret_cast<te_handle>(h);
+  return TE_OK;
+}
+
+te_status te_destroy(te_handle hh) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return TE_OK;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->d_triples) cudaFree(h->d_triples);
+  if (h->d_err) cudaFree(h->d_err);
+  destroy_tc_state(h);
+  delete h;
+  return TE_OK;
+}
+
+te_status t_energy_triples(te_handle hh, const te_cluster* c, te_precision p, int64_t t_begin,
+                           int64_t t_end, double* e_triples, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  DeviceGuard g(h->device);
+  te_status st = validate(h, c, p, s);
+  if (st != TE_OK) return st;
+  const int64_t nt = num_unique_triples(c->nocc);
+  if (t_begin < 0 || t_end > nt || t_begin > t_end)
+    return fail(TE_EINVAL, "triple range [%lld,%lld) outside [0,%lld)", (long long)t_begin,
+                (long long)t_end, (long long)nt);
+  if (t_begin == t_end) return TE_OK;
+  if (!e_triples) return fail(TE_EINVAL, "null e_triples");
+  return run_any(h, c, p, t_begin, t_end, e_triples, nullptr, s);
+}
+
+te_status t_energy(te_handle hh, const te_cluster* c, te_precision p, double* e_out, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (!e_out) return fail(TE_EINVAL, "null e_out");
+  DeviceGuard g(h->device);
+  te_status st = validate(h, c, p, s);
+  if (st != TE_OK) return st;
+  const int64_t nt = num_unique_triples(c->nocc);
+  if (nt == 0) {
+    if (cudaMemsetAsync(e_out, 0, sizeof(double), s) != cudaSuccess)
+      return fail(TE_ECUDA, "memset failed");
+    return TE_OK;
+  }
+  return run_any(h, c, p, 0, nt, nullptr, e_out, s);
+}
+
+te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_precision p,
+                           double* e_out, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (n < 0) return fail(TE_EINVAL, "negative batch size");
+  if (n == 0) return TE_OK;
+  if (!cs || !e_out) return fail(TE_EINVAL, "null cluster array or e_out");
+  for (int64_t x = 0; x < n; ++x) {
+    te_status st = t_energy(hh, cs + x, p, e_out + x, ss);
+    if (st != TE_OK) {
+      char msg[512];
+      snprintf(msg, sizeof(msg), "cluster %lld: %s", (long long)x, te_last_error());
+      return fail(st, "%s", msg);
+    }
+  }
+  return TE_OK;
+}
+
+te_status t_energy_vjp(te_handle hh, const te_cluster* c, te_precision p, double gE, double* e_out,
+                       te_cluster_grad* gr, te_stream_t ss) {
+  (void)hh; (void)c; (void)p; (void)gE; (void)e_out; (void)gr; (void)ss;
+  return fail(TE_EUNSUPPORTED, "t_energy_vjp is not available in this build");
+}
+
+te_status te_sync(te_handle hh, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  DeviceGuard g(h->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(TE_ECUDA, "stream synchronise: %s", cudaGetErrorString(e));
+  unsigned int err[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(TE_ECUDA, "error word read failed");
+  if (err[0] != 0) {
+    cudaMemset(h->d_err, 0, sizeof(err));
+    if (err[0] & ERR_WAIT_TIMEOUT)
+      return fail(TE_ETIMEOUT, "device wait expired (code %u, site %u, block %u)", err[0], err[1], err[2]);
+    return fail(TE_ECUDA, "device check failed (code %u, site %u, block %u)", err[0], err[1], err[2]);
+  }
+  return TE_OK;
+}
+
+te_status te_workspace_bytes(te_handle hh, const te_cluster* c, te_precision p, size_t* bytes) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !c || !bytes) return fail(TE_EINVAL, "null argument");
+  if (c->nocc < 1 || c->nvir < 1) return fail(TE_EINVAL, "nocc and nvir must be >= 1");
+  const int64_t o = c->nocc, v = c->nvir;
+  const int64_t nt = num_unique_triples(o);
+  if (p == TE_FP64) {
+    Prepared P{};
+    double *a, *b, *d;
+    Carver probe(nullptr);
+    *bytes = fp64_carve(probe, o, v, fp64_slots(h, v, nt), energy_num_block_triples(v), nt, &P, &a, &b, &d);
+    return TE_OK;
+  }
+  return tc_workspace_bytes(h, c, p, bytes);
+}
+
+const char* te_last_error(void) { return g_last_error; }
+
+te_status te_set_wait_limit_ns(te_handle hh, uint64_t ns) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  h->wait_limit_ns = ns ? ns : 4000000000ull;
+  return TE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations shared by the host-side translation units of
+// libtenergy.  Nothing here is part of the C ABI (include/tenergy.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tenergy.h"
+
+namespace te {
+
+// Device error word bits (written by kernels, read by te_sync).
+enum : unsigned int {
+  ERR_WAIT_TIMEOUT = 1u,   // a bounded mbarrier/flag wait expired
+  ERR_BAD_TILE = 2u,       // a tile coordinate check failed (skipped access)
+};
+
+// One occupied triple of the canonical unique list.
+struct Triple {
+  int i, j, k, m;  // i >= j >= k, m = number of distinct orderings (3 or 6)
+};
+
+// A view of the prepared operands of one cluster, as the kernels see them.
+struct Prepared {
+  int o, v;
+  // float64 originals (caller-owned)
+  const double* eps_o;
+  const double* eps_v;
+  const double* ovvv;
+  const double* t2;
+  const double* t1;
+  // float64 prepared copies (handle workspace)
+  double* t2L;   // [o][v][v][o]  t2L[q][a][b][l] = t2[l,q,a,b]
+  double* nooT;  // [o][o][v][o]  nooT[p][r][g][l] = -ooov[p,l,r,g]
+  double* ovs;   // [o][v][o][v]  1/2 (ovov[i,a,j,b] + ovov[j,b,i,a])
+  float* ovs32;  // same, float32 (mixed modes)
+  float* t1_32;  // t1 as float32 (mixed modes)
+};
+
+struct Handle {
+  int device = 0;
+  int num_sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  size_t smem_optin = 0;
+  uint64_t wait_limit_ns = 4000000000ull;
+  unsigned int* d_err = nullptr;     // device error word
+  // workspace (grows, never shrinks until destroy)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // triple table cache
+  Triple* d_triples = nullptr;
+  int triples_nocc = -1;
+  size_t triples_cap = 0;
+  void* tc = nullptr;  // tensor-core path state (tensor maps cache), owned
+};
+
+// thread-local last error message
+void set_error(const char* fmt, ...);
+te_status fail(te_status st, const char* fmt, ...);
+
+// enumerate canonical unique triples
+std::vector<Triple> unique_triples(int nocc);
+int64_t num_unique_triples(int64_t nocc);
+
+// launch wrappers (defined in the .cu files)
+cudaError_t launch_prep_fp64(const te_cluster* c, Prepared* P, cudaStream_t s);
+cudaError_t launch_gemm_fp64(const Prepared* P, const Triple* d_triples, int64_t t0,
+                             int nslots, double* gbuf, cudaStream_t s);
+
+// energy over G buffers: T = float (mixed) or double (fp64)
+cudaError_t launch_energy_f64(const Prepared* P, const Triple* d_triples, int64_t t0,
+                              int nslots, const double* gbuf, double* partials,
+                              int64_t nbt, cudaStream_t s);
+cudaError_t launch_energy_f32(const Prepared* P, const Triple* d_triples, int64_t t0,
+                              int nslots, const float* gbuf, double* partials,
+                              int64_t nbt, cudaStream_t s);
+// writes e_out[slot] = (m/3) * sum of the slot's partials, for triples t0 .. t0+nslots-1
+cudaError_t launch_reduce_triples(const double* partials, int64_t nbt, const Triple* d_triples,
+                                  int64_t t0, int nslots, double* e_out, cudaStream_t s);
+cudaError_t launch_reduce_total(const double* e_triples, int64_t n, double* e_out,
+                                cudaStream_t s);
+
+constexpr int ENERGY_TB = 8;  // virtual block edge of the energy kernel
+inline int64_t energy_num_blocks(int64_t v) { return (v + ENERGY_TB - 1) / ENERGY_TB; }
+inline int64_t energy_num_block_triples(int64_t v) {
+  int64_t nb = energy_num_blocks(v);
+  return nb * (nb + 1) * (nb + 2) / 6;
+}
+
+}  // namespace te
