@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Benchmark: (T) energy of one embedded cluster per GPU on GB300.
+
+One step = one full E(T) evaluation (every unique occupied triple: operand
+split, W~ contractions, energy epilogue, reductions) of the synthetic cluster
+nocc=32, nvir=320, naux=1280 (seed 1), inputs resident in HBM.  The metric is
+algorithmic GFLOP/s, F = 12 (C(o+2,3) - o) v^3 (v+o) per cluster.  Under
+torchrun every rank evaluates its own cluster (independent problems: weak
+scaling, no collective on the data path; one scalar all-reduce of the step
+times for the max over ranks).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+WORKLOAD = "o32v320"
+METRIC = "(T) GFLOP/s & clusters/s, tensor-pipe % of peak, at |dE(T)|<=1e-7 Ha vs FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--check-triples", type=int, default=8,
+                    help="triples checked against the FP64 GPU path for |dE|")
+    ap.add_argument("--cpu-triples", type=int, default=2)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    def __init__(self, device):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={device}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name, device):
+    import tegen
+    o, v, naux, seed = tegen.WORKLOADS[name]
+    cl = tegen.make_cluster(o, v, naux, seed, device="cuda")
+    dev = torch.device("cuda", device)
+    arrs = {}
+    for n, x in cl.arrays().items():
+        t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+        arrs[n] = t.to(dev).contiguous()
+    return (o, v, naux, seed), arrs
+
+
+def cpu_oracle_sample(arrs, o, v, ntrip, seconds_cap=40.0):
+    """The FP64 oracle as it stands on a bounded sample of unique triples."""
+    from oracle import t_energy as O
+    torch.set_num_threads(os.cpu_count() or 1)
+    c = O.inputs(**{n: t.cpu() for n, t in arrs.items()})
+    trip = O.unique_triples(o)
+    pick = [trip[(len(trip) - 1) * q // max(1, ntrip - 1)] for q in range(ntrip)] if ntrip > 1 else [trip[-1]]
+    done, t0 = 0, time.time()
+    for (i, j, k) in pick:
+        O.triple_share(c, i, j, k)
+        done += 1
+        if time.time() - t0 > seconds_cap:
+            break
+    dt = time.time() - t0
+    f = 12.0 * done * v ** 3 * (v + o)
+    return dict(value=f / dt / 1e9, unit="GFLOP/s", cores=torch.get_num_threads(), kind="oracle",
+                sample=f"{done} unique triples of the workload (i>=j>=k, {pick[:done]}), "
+                       f"{dt:.1f} s, FP64 einsum per triple share", seconds=dt)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    (o, v, naux, seed), arrs = make_workload(args.workload, 0)
+    from oracle import t_energy as O
+    torch.set_num_threads(os.cpu_count() or 1)
+    c = O.inputs(**{n: t.cpu() for n, t in arrs.items()})
+    trip = O.unique_triples(o)
+    times = []
+    for s in range(args.warmup + args.steps):
+        i, j, k = trip[(len(trip) - 1) - s % len(trip)]
+        t0 = time.time()
+        O.triple_share(c, i, j, k)
+        if s >= args.warmup:
+            times.append(time.time() - t0)
+    per = sum(times) / len(times)
+    value = 12.0 * v ** 3 * (v + o) / per / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": f"{args.workload} one unique occupied triple per step",
+                                           "nocc": o, "nvir": v, "naux": naux, "seed": seed},
+           "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": torch.get_num_threads(),
+                            "kind": "oracle",
+                            "sample": "one unique occupied triple share per step (FP64 einsum oracle)"},
+           "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2412_18553_gb300 as te
+    (o, v, naux, seed), arrs = make_workload(args.workload, local)
+    F = te.flop_count(o, v)
+    h = te.Handle(local)
+    prec = args.precision
+    nprod = {"fp64": 1, "tf32": 1, "bf16x3": 3, "tf32x3": 3}.get(prec, 10)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        te.t_energy(arrs, prec, handle=h)
+    torch.cuda.synchronize()
+    h.sync()
+    h.profile_read(reset=True)
+    h.profile(True)
+
+    clocks = Clocks(local) if local == 0 else None
+    stream = torch.cuda.current_stream()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e = te.t_energy(arrs, prec, handle=h)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    h.profile(False)
+    prof = h.profile_read(reset=True)
+    h.sync()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    per_step = ms_max / args.steps
+    e_val = float(e.item())
+
+    # |dE| on sampled triples against the FP64 GPU path (parity of the same run)
+    nt = te.num_unique_triples(o)
+    nchk = max(1, args.check_triples)
+    picks = sorted(set([nt - 1 - q * max(1, nt // (4 * nchk)) for q in range(nchk // 2)] +
+                       [q * max(1, nt // nchk) for q in range(nchk - nchk // 2)]))
+    d_sh = []
+    for tt in picks:
+        a = te.t_energy_triples(arrs, tt, tt + 1, prec, handle=h).item()
+        b = te.t_energy_triples(arrs, tt, tt + 1, "fp64", handle=h).item()
+        d_sh.append((tt, a, b))
+    max_d = max(abs(a - b) for _, a, b in d_sh)
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {n: x.cpu().pin_memory() for n, x in arrs.items()}
+        out_host = torch.empty((), dtype=torch.float64).pin_memory()
+        h2d = sum(x.numel() * x.element_size() for x in host.values())
+
+        def e2e_step():
+            dev_in = {n: x.to("cuda", non_blocking=True) for n, x in host.items()}
+            ee = te.t_energy(dev_in, prec, handle=h)
+            out_host.copy_(ee, non_blocking=True)
+            return dev_in
+
+        keep = e2e_step()
+        torch.cuda.synchronize()
+        del keep
+        n_e2e = max(1, min(2, args.steps))
+        barrier()
+        torch.cuda.synchronize()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        x0.record()
+        for _ in range(n_e2e):
+            keep = e2e_step()
+        x1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = x0.elapsed_time(x1) / n_e2e
+        te_ = torch.tensor([ems], device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(te_, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * F / (float(te_.item()) / 1e3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
+        del keep, host
+
+    pk, pk_src = peaks()
+    if prec == "fp64":
+        roof = None
+    else:
+        bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        peak = bf16 if prec in ("bf16x3",) or nprod == 10 else bf16 * (1.1 / 2.25)
+        gemm_avg_ms = prof["gemm_ms"] / max(1, prof["gemm_launches"])
+        alg_per_launch = nprod * F * args.steps / max(1, prof["gemm_launches"])
+        achieved = alg_per_launch / (gemm_avg_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_gemm_tc", "peak_source": f"{pk_src} bf16 sustained"
+                + ("" if prec == "bf16x3" or nprod == 10 else " x 1.1/2.25 (tf32)"),
+                "gemm_share_of_step": prof["gemm_ms"] / max(1e-9, ms),
+                "energy_share_of_step": prof["energy_ms"] / max(1e-9, ms)}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_oracle_sample(arrs, o, v, args.cpu_triples)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": world * F / (per_step / 1e3) / 1e9, "unit": "GFLOP/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": {"fp64": "f64", "tf32": "tf32", "tf32x3": "tf32"}.get(prec, "bf16"),
+               "data": "synthetic",
+               "config": {"workload": f"{args.workload}: one cluster per GPU, nocc={o} nvir={v} "
+                                      f"naux={naux} seed={seed}", "precision": prec,
+                          "l2": "inputs larger than L2 (ovvv alone 8.4 GB FP64)",
+                          "parallelism": f"dp{world} (independent clusters)"},
+               "clusters_per_s": world / (per_step / 1e3),
+               "e_t_ha": e_val,
+               "dE_sampled_triples_max_ha": max_d,
+               "dE_sampled": [{"triple": tt, "share": a, "share_fp64": b} for tt, a, b in d_sh],
+               "gpu_launches": prof["launches"],
+               "profile": prof,
+               "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

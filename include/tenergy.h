@@ -142,6 +142,23 @@ te_status te_sync(te_handle h, te_stream_t s);
 te_status te_workspace_bytes(te_handle h, const te_cluster* c, te_precision p,
                              size_t* bytes);
 
+/* Launch accounting of one handle.  Kernel launches are always counted; with
+ * profiling on, CUDA events are recorded on the caller's stream around every
+ * contraction (GEMM) and energy-epilogue launch, and te_profile_read returns
+ * the summed device durations.  Not part of the paper: measurement support. */
+typedef struct {
+  int64_t launches;         /* kernels launched by the library */
+  int64_t gemm_launches;    /* W~ contraction launches */
+  double gemm_ms;           /* their summed device time (profiling on) */
+  int64_t energy_launches;  /* energy-epilogue launches */
+  double energy_ms;         /* their summed device time (profiling on) */
+  double gemm_flops;        /* tensor/DFMA flops issued by the timed GEMM launches (incl. padding) */
+} te_profile;
+
+te_status te_profile_enable(te_handle h, int on);
+/* Synchronises the device, fills *out, and zeroes the counters if reset != 0. */
+te_status te_profile_read(te_handle h, te_profile* out, int reset);
+
 /* Message for the last non-OK status returned on the calling host thread. */
 const char* te_last_error(void);
 

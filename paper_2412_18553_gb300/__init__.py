@@ -82,6 +82,14 @@ class Handle:
     def set_wait_limit_ns(self, ns: int):
         _lib.check(_lib.load().te_set_wait_limit_ns(self.ptr, int(ns)))
 
+    def profile(self, on: bool = True):
+        _lib.check(_lib.load().te_profile_enable(self.ptr, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        pr = _lib.TeProfile()
+        _lib.check(_lib.load().te_profile_read(self.ptr, ctypes.byref(pr), 1 if reset else 0))
+        return {f: getattr(pr, f) for f, _ in pr._fields_}
+
     def workspace_bytes(self, cluster, precision="fp64") -> int:
         t = _tensors(cluster, self.device)
         c = _struct(t)

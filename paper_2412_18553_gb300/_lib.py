@@ -26,6 +26,12 @@ class TeClusterGrad(ctypes.Structure):
                 ("ooov", c_void_p), ("ovov", c_void_p), ("t1", c_void_p), ("t2", c_void_p)]
 
 
+class TeProfile(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("gemm_launches", c_int64), ("gemm_ms", ctypes.c_double),
+                ("energy_launches", c_int64), ("energy_ms", ctypes.c_double),
+                ("gemm_flops", ctypes.c_double)]
+
+
 # (name, restype, argtypes) for every function of include/tenergy.h
 SIGNATURES = [
     ("te_create", ctypes.c_int, [ctypes.POINTER(c_void_p), ctypes.c_int]),
@@ -42,6 +48,8 @@ SIGNATURES = [
                                           ctypes.POINTER(ctypes.c_size_t)]),
     ("te_last_error", ctypes.c_char_p, []),
     ("te_set_wait_limit_ns", ctypes.c_int, [c_void_p, ctypes.c_uint64]),
+    ("te_profile_enable", ctypes.c_int, [c_void_p, ctypes.c_int]),
+    ("te_profile_read", ctypes.c_int, [c_void_p, ctypes.POINTER(TeProfile), ctypes.c_int]),
 ]
 
 _lib = None

@@ -207,22 +207,58 @@ static te_status run_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64
   P.t2 = c->t2;
   P.t1 = c->t1;
   cudaError_t e = launch_prep_fp64(c, &P, s);
+  h->n_launches += 3;
   if (e != cudaSuccess) return fail(TE_ECUDA, "prep launch: %s", cudaGetErrorString(e));
   double* out = e_tri_out ? e_tri_out : etri;
   for (int64_t t0 = t_begin; t0 < t_end; t0 += nslots) {
     const int ns = (int)std::min<int64_t>(nslots, t_end - t0);
+    size_t pm = prof_begin(h, 0, s);
     e = launch_gemm_fp64(&P, h->d_triples, t0, ns, gbuf, s);
-    if (e == cudaSuccess) e = launch_energy_f64(&P, h->d_triples, t0, ns, gbuf, partials, nbt, s);
+    prof_end(h, pm, s);
+    h->gemm_flops += 2.0 * 3.0 * ns * (double)v * v * v * (2.0 * v + 2.0 * o);
+    if (e == cudaSuccess) {
+      pm = prof_begin(h, 1, s);
+      e = launch_energy_f64(&P, h->d_triples, t0, ns, gbuf, partials, nbt, s);
+      prof_end(h, pm, s);
+    }
     if (e == cudaSuccess)
       e = launch_reduce_triples(partials, nbt, h->d_triples, t0, ns, out + (t0 - t_begin), s);
+    h->n_launches += 3;
     if (e != cudaSuccess) return fail(TE_ECUDA, "fp64 launch: %s", cudaGetErrorString(e));
   }
   if (e_total_out) {
+    ++h->n_launches;
     e = launch_reduce_total(out, nt, e_total_out, s);
     if (e != cudaSuccess) return fail(TE_ECUDA, "reduction launch: %s", cudaGetErrorString(e));
   }
   return TE_OK;
 }
+
+size_t prof_begin(Handle* h, int kind, cudaStream_t s) {
+  if (kind == 0) ++h->n_gemm;
+  else ++h->n_energy;
+  if (!h->profiling) return SIZE_MAX;
+  while (h->ev_pool.size() < h->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return SIZE_MAX;
+    }
+    h->ev_pool.push_back(e);
+  }
+  const size_t i = h->ev_used;
+  h->ev_used += 2;
+  cudaEventRecord(h->ev_pool[i], s);
+  h->ev_marks.emplace_back(kind, i);
+  return i;
+}
+
+void prof_end(Handle* h, size_t start, cudaStream_t s) {
+  if (start != SIZE_MAX) cudaEventRecord(h->ev_pool[start + 1], s);
+}
+
+te_status ensure_workspace_public(Handle* h, size_t bytes) { return ensure_workspace(h, bytes); }
+te_status ensure_triples_public(Handle* h, int nocc) { return ensure_triples(h, nocc); }
 
 static te_status run_any(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin,
                          int64_t t_end, double* e_tri_out, double* e_total_out, cudaStream_t s) {
@@ -273,6 +309,7 @@ te_status te_destroy(te_handle hh) {
   if (h->ws) cudaFree(h->ws);
   if (h->d_triples) cudaFree(h->d_triples);
   if (h->d_err) cudaFree(h->d_err);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   destroy_tc_state(h);
   delete h;
   return TE_OK;
@@ -372,6 +409,42 @@ te_status te_workspace_bytes(te_handle hh, const te_cluster* c, te_precision p, 
 }
 
 const char* te_last_error(void) { return g_last_error; }
+
+te_status te_profile_enable(te_handle hh, int on) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  h->profiling = on != 0;
+  return TE_OK;
+}
+
+te_status te_profile_read(te_handle hh, te_profile* out, int reset) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !out) return fail(TE_EINVAL, "null argument");
+  DeviceGuard g(h->device);
+  if (cudaDeviceSynchronize() != cudaSuccess)
+    return fail(TE_ECUDA, "synchronise: %s", cudaGetErrorString(cudaGetLastError()));
+  double ms[2] = {0.0, 0.0};
+  for (const auto& m : h->ev_marks) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->ev_pool[m.second], h->ev_pool[m.second + 1]) == cudaSuccess)
+      ms[m.first] += t;
+    else
+      cudaGetLastError();
+  }
+  out->launches = h->n_launches;
+  out->gemm_launches = h->n_gemm;
+  out->gemm_ms = ms[0];
+  out->energy_launches = h->n_energy;
+  out->energy_ms = ms[1];
+  out->gemm_flops = h->gemm_flops;
+  if (reset) {
+    h->n_launches = h->n_gemm = h->n_energy = 0;
+    h->gemm_flops = 0.0;
+    h->ev_used = 0;
+    h->ev_marks.clear();
+  }
+  return TE_OK;
+}
 
 te_status te_set_wait_limit_ns(te_handle hh, uint64_t ns) {
   Handle* h = reinterpret_cast<Handle*>(hh);

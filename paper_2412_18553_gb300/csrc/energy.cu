@@ -63,7 +63,7 @@ __device__ __forceinline__ void position(const T* cube, const T* ovsS, const T* 
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_energy(const T* __restrict__ gbuf, int o, int v, const Triple* __restrict__ triples, int64_t t0,
+k_energy(const T* __restrict__ gbuf, int o, int v, int ldz, const Triple* __restrict__ triples, int64_t t0,
          const double* __restrict__ eps_o, const double* __restrict__ eps_v,
          const T* __restrict__ ovs, const T* __restrict__ t1, double* __restrict__ partials,
          int64_t nbt) {
@@ -81,8 +81,9 @@ k_energy(const T* __restrict__ gbuf, int o, int v, const Triple* __restrict__ tr
   int blk[3];
   decode_block_triple(bt, blk[0], blk[1], blk[2]);
   const Triple tr = triples[t0 + slot];
-  const int64_t v2 = (int64_t)v * v, v3 = v2 * v;
-  const T* G = gbuf + (int64_t)slot * 3 * v3;
+  const int64_t v2 = (int64_t)v * v;
+  const int64_t gstride = v2 * ldz;  // one G block: [v][v][ldz]
+  const T* G = gbuf + (int64_t)slot * 3 * gstride;
 
   for (int idx = tid; idx < 18 * TB3; idx += blockDim.x) {
     const int e = idx % TB3, cp = idx / TB3;
@@ -92,7 +93,7 @@ k_energy(const T* __restrict__ gbuf, int o, int v, const Triple* __restrict__ tr
     const int y = blk[c_perm[pid][1]] * TB + w;
     const int zz = blk[c_perm[pid][2]] * TB + z;
     T val = T(0);
-    if (x < v && y < v && zz < v) val = G[g * v3 + ((int64_t)x * v + y) * v + zz];
+    if (x < v && y < v && zz < v) val = G[g * gstride + ((int64_t)x * v + y) * ldz + zz];
     cube[idx] = val;
   }
   for (int idx = tid; idx < 27 * TB * TB; idx += blockDim.x) {
@@ -157,7 +158,7 @@ k_energy(const T* __restrict__ gbuf, int o, int v, const Triple* __restrict__ tr
 
 template <typename T>
 static cudaError_t launch_energy(const Prepared* P, const Triple* d_triples, int64_t t0, int nslots,
-                                 const T* gbuf, const T* ovs, const T* t1, double* partials,
+                                 const T* gbuf, int ldz, const T* ovs, const T* t1, double* partials,
                                  int64_t nbt, cudaStream_t s) {
   constexpr int TB = ENERGY_TB, TB3 = TB * TB * TB;
   const size_t smem = sizeof(T) * (18 * TB3 + 27 * TB * TB + 9 * TB + (sizeof(T) == 4 ? 8 : 0)) +
@@ -171,19 +172,19 @@ static cudaError_t launch_energy(const Prepared* P, const Triple* d_triples, int
     done = true;
   }
   dim3 grid((unsigned)nbt, (unsigned)nslots);
-  k_energy<T><<<grid, 256, smem, s>>>(gbuf, P->o, P->v, d_triples, t0, P->eps_o, P->eps_v, ovs, t1,
+  k_energy<T><<<grid, 256, smem, s>>>(gbuf, P->o, P->v, ldz, d_triples, t0, P->eps_o, P->eps_v, ovs, t1,
                                       partials, nbt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_energy_f64(const Prepared* P, const Triple* d_triples, int64_t t0, int nslots,
                               const double* gbuf, double* partials, int64_t nbt, cudaStream_t s) {
-  return launch_energy<double>(P, d_triples, t0, nslots, gbuf, P->ovs, P->t1, partials, nbt, s);
+  return launch_energy<double>(P, d_triples, t0, nslots, gbuf, P->v, P->ovs, P->t1, partials, nbt, s);
 }
 
 cudaError_t launch_energy_f32(const Prepared* P, const Triple* d_triples, int64_t t0, int nslots,
-                              const float* gbuf, double* partials, int64_t nbt, cudaStream_t s) {
-  return launch_energy<float>(P, d_triples, t0, nslots, gbuf, P->ovs32, P->t1_32, partials, nbt, s);
+                              const float* gbuf, int ldz, double* partials, int64_t nbt, cudaStream_t s) {
+  return launch_energy<float>(P, d_triples, t0, nslots, gbuf, ldz, P->ovs32, P->t1_32, partials, nbt, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -56,7 +56,18 @@ struct Handle {
   int triples_nocc = -1;
   size_t triples_cap = 0;
   void* tc = nullptr;  // tensor-core path state (tensor maps cache), owned
+  // launch accounting / profiling
+  int64_t n_launches = 0, n_gemm = 0, n_energy = 0;
+  double gemm_flops = 0.0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_marks;  // (kind 0 gemm / 1 energy, start event index)
 };
+
+// Profiling helpers: begin/end a timed launch of `kind` on stream s.
+size_t prof_begin(Handle* h, int kind, cudaStream_t s);
+void prof_end(Handle* h, size_t start, cudaStream_t s);
 
 // thread-local last error message
 void set_error(const char* fmt, ...);
@@ -76,7 +87,7 @@ cudaError_t launch_energy_f64(const Prepared* P, const Triple* d_triples, int64_
                               int nslots, const double* gbuf, double* partials,
                               int64_t nbt, cudaStream_t s);
 cudaError_t launch_energy_f32(const Prepared* P, const Triple* d_triples, int64_t t0,
-                              int nslots, const float* gbuf, double* partials,
+                              int nslots, const float* gbuf, int ldz, double* partials,
                               int64_t nbt, cudaStream_t s);
 // writes e_out[slot] = (m/3) * sum of the slot's partials, for triples t0 .. t0+nslots-1
 cudaError_t launch_reduce_triples(const double* partials, int64_t nbt, const Triple* d_triples,
