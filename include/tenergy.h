@@ -159,6 +159,36 @@ te_status te_profile_enable(te_handle h, int on);
 /* Synchronises the device, fills *out, and zeroes the counters if reset != 0. */
 te_status te_profile_read(te_handle h, te_profile* out, int reset);
 
+/* E(T) in float64 (the TE_FP64 arithmetic) without allocating any device
+ * memory.  The paper has no counterpart: this exists for callers that cannot
+ * let a library allocate - a host program that hands the whole GPU to its own
+ * memory pool and treats any other allocation as a budget violation, or one
+ * that cannot afford cudaMalloc's implicit device-wide synchronisation in the
+ * middle of its work.  No handle is used; the current CUDA device is.
+ *
+ * All scratch (prepared operand copies, G blocks, partial sums, the triple
+ * table) lives in one 64 MiB array compiled into the library; every GPU that
+ * loads the library holds it until the process exits.  A cluster needs about
+ * 8 (2 o^2 v^2 + o^3 v + 3 v^3) bytes plus small tables (nocc = 8, nvir = 80
+ * fits; nocc = 16, nvir = 120 does not); larger clusters are rejected with
+ * TE_EINVAL, and the message names the bytes needed, before any device
+ * memory is touched.  The call allocates nothing: no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture.  Like t_energy it reads eps_o/eps_v back to check max(eps_o) <
+ * min(eps_v), which synchronises stream s.
+ *
+ * Every call shares the one array and it keeps the last call's contents;
+ * each call writes every scratch byte before reading it.  Calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the array
+ * and give wrong results: order them.
+ *
+ * c: cluster (device float64 arrays as above); e_out: device pointer to one
+ * double, overwritten with E(T); s: stream (0 = legacy default stream). */
+te_status t_energy_fp64_noalloc(const te_cluster* c, double* e_out, te_stream_t s);
+
 /* Message for the last non-OK status returned on the calling host thread. */
 const char* te_last_error(void);
 

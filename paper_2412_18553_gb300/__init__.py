@@ -23,6 +23,7 @@ from ._lib import PRECISIONS, TEnergyError, TeCluster, TeClusterGrad
 NAMES = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
 
 __all__ = ["Handle", "t_energy", "t_energy_triples", "t_energy_batched", "t_energy_vjp",
+           "t_energy_fp64_noalloc",
            "TEnergy", "num_unique_triples", "flop_count", "TEnergyError", "NAMES"]
 
 
@@ -225,6 +226,21 @@ def t_energy_vjp(cluster, gE=1.0, precision="fp64", handle=None, device=None, st
                                         ctypes.c_void_p(e.data_ptr()), ctypes.byref(g),
                                         _stream(dev, stream)))
     return e, grads
+
+
+def t_energy_fp64_noalloc(cluster, device=None, stream=None) -> torch.Tensor:
+    """Float64 E(T) through the library's no-allocation entry point (its
+    scratch is a fixed array inside the library; the result tensor here is
+    the caller's own allocation).  For callers whose host program forbids
+    library-side device allocations; small clusters only (64 MiB scratch)."""
+    dev = _device_of(cluster, device)
+    t = _tensors(cluster, dev)
+    c = _struct(t)
+    out = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
+    with torch.cuda.device(dev):
+        _lib.check(_lib.load().t_energy_fp64_noalloc(ctypes.byref(c), ctypes.c_void_p(out.data_ptr()),
+                                                     _stream(dev, stream)))
+    return out
 
 
 class TEnergy(torch.autograd.Function):

@@ -50,6 +50,7 @@ SIGNATURES = [
     ("te_set_wait_limit_ns", ctypes.c_int, [c_void_p, ctypes.c_uint64]),
     ("te_profile_enable", ctypes.c_int, [c_void_p, ctypes.c_int]),
     ("te_profile_read", ctypes.c_int, [c_void_p, ctypes.POINTER(TeProfile), ctypes.c_int]),
+    ("t_energy_fp64_noalloc", ctypes.c_int, [ctypes.POINTER(TeCluster), c_void_p, c_void_p]),
 ]
 
 _lib = None
