@@ -47,7 +47,17 @@
  *              three products hi*hi + hi*lo + lo*hi on tcgen05 (kind::f16),
  *              FP32 accumulation;
  *   TE_TF32X3  the same split with TF32 parts (kind::tf32).
- *   In every mode D, 1/D, the products with 1/D and all sums are float64.
+ *   TE_OZAKI   error-free slicing after Ozaki, Ogita, Oishi and Rump (2012):
+ *              every operand array is scaled by one power of two and cut
+ *              into four 7-bit BF16 slices; the ten slice products down to
+ *              the fifth level run on tcgen05 (kind::f16) into three FP32
+ *              accumulators, the first two of which sum exact integers (no
+ *              rounding in the tensor-core accumulation), and the G blocks
+ *              are kept as FP32 pairs.  Meets 1e-7 Ha where FP32
+ *              accumulation does not.
+ *   In every mode D, 1/D, the products with 1/D and all sums are float64;
+ *   the tensor-core modes form the orbit sum of R from deviations
+ *   W_n - W_0 (no cancellation of the part of W~ that R annihilates).
  */
 #ifndef TENERGY_H
 #define TENERGY_H
@@ -74,7 +84,8 @@ typedef enum {
   TE_FP64 = 0,
   TE_TF32 = 1,
   TE_BF16X3 = 2,
-  TE_TF32X3 = 3
+  TE_TF32X3 = 3,
+  TE_OZAKI = 4
 } te_precision;
 
 typedef struct {

@@ -12,7 +12,7 @@ c_void_p = ctypes.c_void_p
 TE_OK, TE_EINVAL, TE_ENOMEM, TE_ECUDA, TE_ETIMEOUT, TE_EUNSUPPORTED = range(6)
 STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA",
                 4: "TE_ETIMEOUT", 5: "TE_EUNSUPPORTED"}
-PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3}
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3, "ozaki": 4}
 
 
 class TeCluster(ctypes.Structure):

@@ -130,7 +130,7 @@ static te_status validate(const Handle* h, const te_cluster* c, te_precision p, 
     return fail(TE_EUNSUPPORTED, "cluster too large (nocc <= 2048, nvir <= 4096)");
   if (!c->eps_o || !c->eps_v || !c->ovvv || !c->ooov || !c->ovov || !c->t1 || !c->t2)
     return fail(TE_EINVAL, "null array pointer in cluster descriptor");
-  if (p != TE_FP64 && p != TE_TF32 && p != TE_BF16X3 && p != TE_TF32X3)
+  if (p != TE_FP64 && p != TE_TF32 && p != TE_BF16X3 && p != TE_TF32X3 && p != TE_OZAKI)
     return fail(TE_EINVAL, "unknown precision mode %d", (int)p);
   // every denominator must be negative: max eps_o < min eps_v
   std::vector<double> eo(c->nocc), ev(c->nvir);

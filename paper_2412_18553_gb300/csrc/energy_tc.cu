@@ -1,0 +1,384 @@
+// Energy epilogue of the tensor-core modes: a persistent kernel fed by TMA.
+//
+// Work item = (triple slot, block triple X >= Y >= Z of 8-wide virtual
+// blocks).  One warp issues the item's TMA loads into the idle half of a
+// double buffer (18 G cubes: 3 G blocks x 6 block orders; 27 8x8 blocks of
+// the symmetrised ovov; 9 t1 rows; 3 eps_v rows) while all eight warps work
+// on the other half.  G is either FP32 (BF16X3/TF32/TF32X3) or an FP32 pair
+// hi + lo (OZAKI), CW = 1 or 2 floats per element.
+//
+// Orbit sum without cancellation: the 6x6 coefficient matrix C of R between
+// the six orbit positions (T = sum_nm W_n C_nm V_m) has zero row and column
+// sums, so T is unchanged when W_0 and V_0 are subtracted from every
+// position.  The deviations w_n = W_n - W_0 are formed G block by G block
+// (differences of close FP32 numbers are nearly exact), so the symmetric
+// part of W~, which R annihilates, never enters a rounded product.
+//   T = 3 sum_n w_n v_n + Ae Se + Ao So - 2 (Ae So + Ao Se)
+// D, its reciprocal (FP32 seed + one Newton step in FP64: error ~1e-14),
+// A T / D and the sums are FP64.
+#include "energy_tc.h"
+#include "ptx_sm100.cuh"
+
+namespace te {
+
+namespace {
+
+constexpr int TB = 8;
+constexpr int THREADS = 256;
+
+__constant__ int c_perm_tc[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+template <int N>
+struct Pos {
+  static constexpr int s0 = (N <= 1) ? 0 : (N <= 3) ? 1 : 2;
+  static constexpr int s1 = (N == 0) ? 1 : (N == 1) ? 2 : (N == 2) ? 0 : (N == 3) ? 2 : (N == 4) ? 0 : 1;
+  static constexpr int s2 = 3 - s0 - s1;
+  static constexpr int r1 = (N == 0) ? 3 : (N == 1) ? 5 : (N == 2) ? 1 : (N == 3) ? 4 : (N == 4) ? 0 : 2;
+  static constexpr int r2 = (N == 0) ? 4 : (N == 1) ? 2 : (N == 2) ? 5 : (N == 3) ? 0 : (N == 4) ? 3 : 1;
+};
+
+template <int CW>
+struct Layout {
+  static constexpr uint32_t cube_bytes = TB * TB * TB * 4 * CW;
+  static constexpr uint32_t cubes = 18 * cube_bytes;
+  static constexpr uint32_t ovs = 27 * TB * TB * 4;
+  static constexpr uint32_t t1 = 9 * 128;
+  static constexpr uint32_t eps = 3 * 128;
+  static constexpr uint32_t buf = cubes + ovs + t1 + eps;
+  static constexpr uint32_t tx = 18 * cube_bytes + 27 * TB * TB * 4 + 9 * TB * 4 + 3 * TB * 8;
+};
+
+__device__ __forceinline__ void decode_bt(int64_t bt, int* blk) {
+  // bt = X(X+1)(X+2)/6 + Y(Y+1)/2 + Z, X >= Y >= Z >= 0 (FP32 estimate, exact integer fix-up)
+  int x = (int)cbrtf(6.0f * (float)bt);
+  while (x > 0 && (int64_t)x * (x + 1) * (x + 2) / 6 > bt) --x;
+  while ((int64_t)(x + 1) * (x + 2) * (x + 3) / 6 <= bt) ++x;
+  const int64_t rem = bt - (int64_t)x * (x + 1) * (x + 2) / 6;
+  int y = (int)sqrtf(2.0f * (float)rem);
+  while (y > 0 && (int64_t)y * (y + 1) / 2 > rem) --y;
+  while ((int64_t)(y + 1) * (y + 2) / 2 <= rem) ++y;
+  blk[0] = x;
+  blk[1] = y;
+  blk[2] = (int)(rem - (int64_t)y * (y + 1) / 2);
+}
+
+// ---- double-float (pair of FP32) arithmetic: error-free transformations ----
+// Knuth two-sum, FMA two-product; the rn intrinsics forbid contraction.
+struct df {
+  float h, l;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ df df_norm(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  const df s = df_two_sum(a.h, b.h);
+  return df_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = fmaf(a.h, b.h, -p);
+  return df_norm(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.h, b.l), __fmul_rn(a.l, b.h))));
+}
+
+__device__ __forceinline__ df df_scale(df a, float k) {  // k a small integer
+  const float p = __fmul_rn(a.h, k);
+  const float e = fmaf(a.h, k, -p);
+  return df_norm(p, __fadd_rn(e, __fmul_rn(a.l, k)));
+}
+
+// G value of block g at cube `pid`, local (x, y, z): hi and lo parts.
+template <int CW>
+__device__ __forceinline__ void gval(const float* cube, int g, int pid, int x, int y, int z, float& hi,
+                                     float& lo) {
+  const float* p = cube + (((g * 6 + pid) * TB + x) * TB + y) * TB * CW + z * CW;
+  hi = p[0];
+  lo = (CW == 2) ? p[1] : 0.f;
+}
+
+// deviation of W~ at position N from position 0, and Y at position N
+template <int CW, int N>
+__device__ __forceinline__ float w_dev(const float* cube, const int* l) {
+  constexpr int s0 = Pos<N>::s0, s1 = Pos<N>::s1, s2 = Pos<N>::s2;
+  const int x = l[s0], y = l[s1], z = l[s2];
+  float h0, l0, hn, ln, d = 0.f, dl = 0.f;
+  // G0[x][y][z] at cube N, minus G0[a][b][c] at cube 0
+  gval<CW>(cube, 0, N, x, y, z, hn, ln);
+  gval<CW>(cube, 0, 0, l[0], l[1], l[2], h0, l0);
+  d += hn - h0;
+  dl += ln - l0;
+  // G1[y][z][x] at cube r1(N), minus G1[b][c][a] at cube 3
+  gval<CW>(cube, 1, Pos<N>::r1, y, z, x, hn, ln);
+  gval<CW>(cube, 1, 3, l[1], l[2], l[0], h0, l0);
+  d += hn - h0;
+  dl += ln - l0;
+  // G2[z][x][y] at cube r2(N), minus G2[c][a][b] at cube 4
+  gval<CW>(cube, 2, Pos<N>::r2, z, x, y, hn, ln);
+  gval<CW>(cube, 2, 4, l[2], l[0], l[1], h0, l0);
+  d += hn - h0;
+  dl += ln - l0;
+  return d + dl;
+}
+
+// double-float deviation of W~ at position N from position 0 (CW = 2)
+template <int N>
+__device__ __forceinline__ df w_dev_df(const float* cube, const int* l) {
+  constexpr int s0 = Pos<N>::s0, s1 = Pos<N>::s1, s2 = Pos<N>::s2;
+  const int x = l[s0], y = l[s1], z = l[s2];
+  float h0, l0, hn, ln;
+  gval<2>(cube, 0, N, x, y, z, hn, ln);
+  gval<2>(cube, 0, 0, l[0], l[1], l[2], h0, l0);
+  df acc = df_two_sum(hn, -h0);
+  float lsum = __fsub_rn(ln, l0);
+  gval<2>(cube, 1, Pos<N>::r1, y, z, x, hn, ln);
+  gval<2>(cube, 1, 3, l[1], l[2], l[0], h0, l0);
+  acc = df_add(acc, df_two_sum(hn, -h0));
+  lsum = __fadd_rn(lsum, __fsub_rn(ln, l0));
+  gval<2>(cube, 2, Pos<N>::r2, z, x, y, hn, ln);
+  gval<2>(cube, 2, 4, l[2], l[0], l[1], h0, l0);
+  acc = df_add(acc, df_two_sum(hn, -h0));
+  lsum = __fadd_rn(lsum, __fsub_rn(ln, l0));
+  return df_add(acc, df{lsum, 0.f});
+}
+
+template <int N>
+__device__ __forceinline__ float y_at(const float* ovsS, const float* t1S, const int* l) {
+  constexpr int s0 = Pos<N>::s0, s1 = Pos<N>::s1, s2 = Pos<N>::s2;
+  const int x = l[s0], y = l[s1], z = l[s2];
+  return ovsS[((0 * 3 + s0) * 3 + s1) * 64 + x * 8 + y] * t1S[(2 * 3 + s2) * 32 + z] +
+         ovsS[((1 * 3 + s1) * 3 + s2) * 64 + y * 8 + z] * t1S[(0 * 3 + s0) * 32 + x] +
+         ovsS[((2 * 3 + s0) * 3 + s2) * 64 + x * 8 + z] * t1S[(1 * 3 + s1) * 32 + y];
+}
+
+struct EnergyMaps {
+  CUtensorMap g;    // G buffer, 5D (z*CW, y, x, g, slot)
+  CUtensorMap ovs;  // ovs32 [o][v][o][vq], 4D (b, j, a, i)
+  CUtensorMap t1;   // t1 [o][vq], 2D (a, i)
+  CUtensorMap eps;  // eps_v copy, 1D FP64
+};
+
+struct EnergyParams {
+  int o, v, nslots;
+  int64_t nbt, items, t0;
+  const Triple* triples;
+  const double* eps_o;
+  double* partials;
+  unsigned int* err;
+  unsigned long long wait_ns;
+};
+
+template <int CW>
+__global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant__ EnergyMaps M, const EnergyParams P) {
+  using L = Layout<CW>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                                         ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * L::buf);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(full + 2);
+  int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][4]: X, Y, Z per buffer
+  __shared__ double red[THREADS / 32];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    ptx::mbar_init(&full[0], 1);
+    ptx::mbar_init(&full[1], 1);
+    *abort_flag = 0;
+    ptx::fence_barrier_init();
+  }
+  __syncthreads();
+
+  // issue the loads of item `it` into buffer `b` (warp 0, all lanes)
+  auto issue = [&](int64_t it, int b) {
+    const int slot = (int)(it / P.nbt);
+    const int64_t bt = it % P.nbt;
+    int blk[3];
+    decode_bt(bt, blk);
+    const Triple tr = P.triples[P.t0 + slot];
+    unsigned char* base = smem + (size_t)b * L::buf;
+    if (lane == 0) {
+      meta[b * 4 + 0] = blk[0];
+      meta[b * 4 + 1] = blk[1];
+      meta[b * 4 + 2] = blk[2];
+      ptx::mbar_arrive_expect_tx(&full[b], L::tx);
+    }
+    __syncwarp();
+    for (int q = lane; q < 57; q += 32) {
+      if (q < 18) {
+        const int g = q / 6, pid = q % 6;
+        ptx::tma_load_5d(base + q * L::cube_bytes, &M.g, &full[b], blk[c_perm_tc[pid][2]] * TB * CW,
+                         blk[c_perm_tc[pid][1]] * TB, blk[c_perm_tc[pid][0]] * TB, g, slot);
+      } else if (q < 45) {
+        const int r = q - 18, pair = r / 9, sx = (r / 3) % 3, sy = r % 3;
+        const int P1 = (pair == 1) ? tr.j : tr.i;
+        const int P2 = (pair == 0) ? tr.j : tr.k;
+        ptx::tma_load_4d(base + L::cubes + r * 256, &M.ovs, &full[b], blk[sy] * TB, P2, blk[sx] * TB, P1);
+      } else if (q < 54) {
+        const int r = q - 45, which = r / 3, s = r % 3;
+        const int occ = which == 0 ? tr.i : (which == 1 ? tr.j : tr.k);
+        ptx::tma_load_2d(base + L::cubes + L::ovs + r * 128, &M.t1, &full[b], blk[s] * TB, occ);
+      } else {
+        const int s = q - 54;
+        ptx::tma_load_1d(base + L::cubes + L::ovs + L::t1 + s * 128, &M.eps, &full[b], blk[s] * TB);
+      }
+    }
+  };
+
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  int64_t it = blockIdx.x;
+  if (warp == 0 && it < P.items) {
+    issue(it, 0);
+    pending[0] = true;
+  }
+  int b = 0;
+  for (; it < P.items; it += gridDim.x, b ^= 1) {
+    const int64_t nxt = it + gridDim.x;
+    if (warp == 0 && nxt < P.items && !*abort_flag) {
+      issue(nxt, b ^ 1);
+      pending[b ^ 1] = true;
+    }
+    // every thread observes the phase completion
+    const bool ok = ptx::mbar_wait(&full[b], phase[b], P.wait_ns);
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      if (tid == 0) {
+        *abort_flag = 1;
+        if (atomicOr(P.err, ERR_WAIT_TIMEOUT) == 0) {
+          P.err[1] = 10;
+          P.err[2] = blockIdx.x;
+        }
+      }
+      break;
+    }
+    pending[b] = false;
+    phase[b] ^= 1u;
+
+    const int slot = (int)(it / P.nbt);
+    const int64_t bt = it % P.nbt;
+    const int blk[3] = {meta[b * 4 + 0], meta[b * 4 + 1], meta[b * 4 + 2]};
+    const Triple tr = P.triples[P.t0 + slot];
+    const unsigned char* base = smem + (size_t)b * L::buf;
+    const float* cube = reinterpret_cast<const float*>(base);
+    const float* ovsS = reinterpret_cast<const float*>(base + L::cubes);
+    const float* t1S = reinterpret_cast<const float*>(base + L::cubes + L::ovs);
+    const double* epsS = reinterpret_cast<const double*>(base + L::cubes + L::ovs + L::t1);
+
+    const double eo = P.eps_o[tr.i] + P.eps_o[tr.j] + P.eps_o[tr.k];
+    const int pr = tid >> 2, la = pr >> 3, lb = pr & 7;
+    const int a = blk[0] * TB + la, bb = blk[1] * TB + lb;
+    double acc = 0.0;
+    const bool ab_ok = a < P.v && bb < P.v && !(blk[0] == blk[1] && la < lb);
+    if (ab_ok) {
+      const double dab = eo - epsS[la] - epsS[16 + lb];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int lc = (tid & 3) + 4 * h;
+        const int c = blk[2] * TB + lc;
+        if (c >= P.v || (blk[1] == blk[2] && lb < lc)) continue;
+        const int l[3] = {la, lb, lc};
+        double Td;
+        if constexpr (CW == 2) {
+          const df w1 = w_dev_df<1>(cube, l), w2 = w_dev_df<2>(cube, l), w3 = w_dev_df<3>(cube, l);
+          const df w4 = w_dev_df<4>(cube, l), w5 = w_dev_df<5>(cube, l);
+          const float y0 = y_at<0>(ovsS, t1S, l);
+          const df v1 = df_add(w1, df{__fsub_rn(y_at<1>(ovsS, t1S, l), y0), 0.f});
+          const df v2 = df_add(w2, df{__fsub_rn(y_at<2>(ovsS, t1S, l), y0), 0.f});
+          const df v3 = df_add(w3, df{__fsub_rn(y_at<3>(ovsS, t1S, l), y0), 0.f});
+          const df v4 = df_add(w4, df{__fsub_rn(y_at<4>(ovsS, t1S, l), y0), 0.f});
+          const df v5 = df_add(w5, df{__fsub_rn(y_at<5>(ovsS, t1S, l), y0), 0.f});
+          const df Ae = df_add(w3, w4), Ao = df_add(df_add(w1, w2), w5);
+          const df Se = df_add(v3, v4), So = df_add(df_add(v1, v2), v5);
+          df dot = df_mul(w1, v1);
+          dot = df_add(dot, df_mul(w2, v2));
+          dot = df_add(dot, df_mul(w3, v3));
+          dot = df_add(dot, df_mul(w4, v4));
+          dot = df_add(dot, df_mul(w5, v5));
+          df T = df_add(df_scale(dot, 3.f), df_add(df_mul(Ae, Se), df_mul(Ao, So)));
+          T = df_add(T, df_scale(df_add(df_mul(Ae, So), df_mul(Ao, Se)), -2.f));
+          Td = (double)T.h + (double)T.l;
+        } else {
+          const float w1 = w_dev<CW, 1>(cube, l), w2 = w_dev<CW, 2>(cube, l), w3 = w_dev<CW, 3>(cube, l);
+          const float w4 = w_dev<CW, 4>(cube, l), w5 = w_dev<CW, 5>(cube, l);
+          const float y0 = y_at<0>(ovsS, t1S, l);
+          const float v1 = w1 + (y_at<1>(ovsS, t1S, l) - y0), v2 = w2 + (y_at<2>(ovsS, t1S, l) - y0);
+          const float v3 = w3 + (y_at<3>(ovsS, t1S, l) - y0), v4 = w4 + (y_at<4>(ovsS, t1S, l) - y0);
+          const float v5 = w5 + (y_at<5>(ovsS, t1S, l) - y0);
+          const float Ae = w3 + w4, Ao = w1 + w2 + w5;
+          const float Se = v3 + v4, So = v1 + v2 + v5;
+          const float dot = w1 * v1 + w2 * v2 + w3 * v3 + w4 * v4 + w5 * v5;
+          Td = (double)(3.f * dot + Ae * Se + Ao * So - 2.f * (Ae * So + Ao * Se));
+        }
+        const double D = dab - epsS[32 + lc];
+        const double r0 = (double)__frcp_rn((float)D);
+        const double r1 = fma(r0, fma(-D, r0, 1.0), r0);
+        const double wA = (a == bb && bb == c) ? (1.0 / 6.0) : ((a == bb || bb == c) ? 0.5 : 1.0);
+        acc = fma(wA * Td, r1, acc);
+      }
+    }
+    // fixed-order block reduction -> one partial per item
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();  // also frees buffer b for the issue two items ahead
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+      P.partials[(int64_t)slot * P.nbt + bt] = s;
+    }
+  }
+  // loads still in flight land before the CTA exits
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q)
+      if (pending[q]) ptx::mbar_wait(&full[q], phase[q], P.wait_ns);
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+size_t energy_tc_smem(int cw) {
+  const size_t buf = cw == 2 ? Layout<2>::buf : Layout<1>::buf;
+  return 2 * buf + 128 + 128;
+}
+
+cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
+  EnergyMaps M;
+  M.g = *e.map_g;
+  M.ovs = *e.map_ovs;
+  M.t1 = *e.map_t1;
+  M.eps = *e.map_eps;
+  EnergyParams P;
+  P.o = e.o;
+  P.v = e.v;
+  P.nslots = e.nslots;
+  P.nbt = e.nbt;
+  P.items = (int64_t)e.nslots * e.nbt;
+  P.t0 = e.t0;
+  P.triples = e.triples;
+  P.eps_o = e.eps_o;
+  P.partials = e.partials;
+  P.err = e.err;
+  P.wait_ns = e.wait_ns;
+  const size_t smem = energy_tc_smem(e.cw);
+  const int64_t grid = std::min<int64_t>(P.items, (int64_t)e.num_sms * (e.cw == 2 ? 1 : 2));
+  cudaError_t err;
+  if (e.cw == 2) {
+    err = cudaFuncSetAttribute(k_energy_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_energy_tc<2><<<(unsigned)grid, THREADS, smem, s>>>(M, P);
+  } else {
+    err = cudaFuncSetAttribute(k_energy_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_energy_tc<1><<<(unsigned)grid, THREADS, smem, s>>>(M, P);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace te

@@ -1,4 +1,4 @@
-// Tensor-core path (TF32, BF16x3, TF32x3) for the W~ contractions.
+// Tensor-core path (TF32, BF16x3, TF32x3, OZAKI) for the W~ contractions.
 //
 // The same three G blocks as the float64 path (see gemm_fp64.cu):
 //   W~_{ijk}[a,b,c] = G(i,j,k)[a,b,c] + G(j,k,i)[b,c,a] + G(k,i,j)[c,a,b]
@@ -6,12 +6,24 @@
 //   S1 ovvv[p,x,y,:] . t2[r,q,z,:]     S2 ovvv[q,y,x,:] . t2[r,p,z,:]
 //   S3 t2L[p,y,x,:] . nooT[q,r,z,:]    S4 t2L[q,x,y,:] . nooT[p,r,z,:]
 // run on tcgen05: TMA brings 128-row A tiles (TA values of x times TB of y)
-// and NT-row B tiles into swizzled shared memory; one elected thread issues
-// tcgen05.mma into a double-buffered FP32 accumulator in tensor memory; four
-// epilogue warps drain TMEM into the FP32 G buffer.  Operands are split once
-// per call: x = hi + lo with hi, lo the nearest 8-bit (BF16) or 11-bit (TF32)
-// significands, found by Veltkamp splitting; BF16x3/TF32x3 accumulate
-// hi*hi + hi*lo + lo*hi, TF32 uses hi only.
+// and NT-row B tiles into swizzled shared memory; one thread issues
+// tcgen05.mma into FP32 accumulators in tensor memory; four epilogue warps
+// drain TMEM into the G buffer.
+//
+// Operand forms, prepared once per call:
+//  * TF32, BF16X3, TF32X3: x = hi + lo, hi and lo the nearest 11-bit (TF32)
+//    or 8-bit (BF16) significands (Veltkamp splitting); the products
+//    hi*hi + hi*lo + lo*hi (hi*hi only for TF32) share one accumulator.
+//  * OZAKI (Ozaki, Ogita, Oishi, Rump 2012, error-free slicing): each array
+//    is scaled by 2^-s (s from its largest magnitude, chosen so that every
+//    segment of the K axis has the same unit) and cut into four slices
+//    m_k 2^-7k, |m_k| <= 128, exact in BF16.  Slice products are then exact
+//    multiples of 2^-7(k+l); the level-2 product and the two level-3
+//    products each go to their own accumulator, where every partial sum is
+//    an integer multiple of the level's unit below 2^24 units - exact, so the
+//    tensor core's FP32 accumulation cannot round them.  The seven products
+//    of levels 4 and 5 share a third accumulator.  The epilogue adds the
+//    three with an exact two-sum and stores G as an FP32 pair (hi, lo).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -19,19 +31,36 @@
 #include <algorithm>
 #include <cstring>
 
+#include "energy_tc.h"
 #include "ptx_sm100.cuh"
 #include "tc_path.h"
 
 namespace te {
 
-enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2 };
+enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2, TC_OZAKI = 3 };
 
 static int tc_mode_of(te_precision p) {
-  return p == TE_TF32 ? TC_TF32 : (p == TE_BF16X3 ? TC_BF16X3 : TC_TF32X3);
+  switch (p) {
+    case TE_TF32: return TC_TF32;
+    case TE_BF16X3: return TC_BF16X3;
+    case TE_TF32X3: return TC_TF32X3;
+    default: return TC_OZAKI;
+  }
 }
 
+template <int MODE>
+struct ModeTraits {
+  static constexpr bool tf32 = (MODE == TC_TF32 || MODE == TC_TF32X3);
+  static constexpr int nparts = (MODE == TC_TF32) ? 1 : (MODE == TC_OZAKI ? 4 : 2);
+  static constexpr int nacc = (MODE == TC_OZAKI) ? 3 : 1;   // accumulators per tile
+  static constexpr int nbuf = (MODE == TC_OZAKI) ? 1 : 2;   // TMEM buffering
+};
+
+constexpr int OZ_BETA = 7;    // bits per slice
+constexpr int OZ_SLICES = 4;
+
 // ---------------------------------------------------------------------------
-// operand splitting
+// operand preparation
 // ---------------------------------------------------------------------------
 
 // Round x to the nearest value with `bits` significant bits (Veltkamp split).
@@ -42,37 +71,60 @@ __device__ __forceinline__ double round_sig(double x) {
   return __dsub_rn(c, __dsub_rn(c, x));
 }
 
+struct Parts {
+  void* p[4];
+};
+
+// Element `idx` of every part plane.  For OZAKI, `scale` is 2^-s of the array.
 template <int MODE>
-__device__ __forceinline__ void split_store(double x, void* hi, void* lo, int64_t idx) {
+__device__ __forceinline__ void split_store(double x, const Parts& parts, int64_t idx, double scale) {
   if (MODE == TC_BF16X3) {
     const double h = round_sig<8>(x);
     const double l = round_sig<8>(x - h);
-    reinterpret_cast<__nv_bfloat16*>(hi)[idx] = __float2bfloat16_rn((float)h);
-    reinterpret_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn((float)l);
+    reinterpret_cast<__nv_bfloat16*>(parts.p[0])[idx] = __float2bfloat16_rn((float)h);
+    reinterpret_cast<__nv_bfloat16*>(parts.p[1])[idx] = __float2bfloat16_rn((float)l);
+  } else if (MODE == TC_OZAKI) {
+    double t = x * scale;  // |t| < 1, exact power-of-two scaling
+#pragma unroll
+    for (int k = 0; k < OZ_SLICES; ++k) {
+      t = t * (double)(1 << OZ_BETA);
+      const double m = rint(t);
+      t = t - m;
+      // m 2^-7(k+1) is exact in BF16 (|m| <= 128)
+      reinterpret_cast<__nv_bfloat16*>(parts.p[k])[idx] =
+          __float2bfloat16_rn((float)(m * (1.0 / (double)(1ull << (OZ_BETA * (k + 1))))));
+    }
   } else {
     const double h = round_sig<11>(x);
-    reinterpret_cast<float*>(hi)[idx] = (float)h;
-    if (MODE == TC_TF32X3) reinterpret_cast<float*>(lo)[idx] = (float)round_sig<11>(x - h);
+    reinterpret_cast<float*>(parts.p[0])[idx] = (float)h;
+    if (MODE == TC_TF32X3) reinterpret_cast<float*>(parts.p[1])[idx] = (float)round_sig<11>(x - h);
   }
+}
+
+__device__ __forceinline__ double scale_of(const int* exps, int which) {
+  return exps ? ldexp(1.0, -exps[which]) : 1.0;
 }
 
 // dst[row][kp] = src[row][k] (k < K) or 0, rows x Kp
 template <int MODE>
-__global__ void k_split_rows(const double* __restrict__ src, void* hi, void* lo, int64_t rows, int K,
-                             int Kp) {
+__global__ void k_split_rows(const double* __restrict__ src, Parts parts, int64_t rows, int K, int Kp,
+                             const int* exps, int which) {
+  const double sc = scale_of(exps, which);
   const int64_t n = rows * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(idx % Kp);
     const int64_t row = idx / Kp;
     const double x = k < K ? src[row * K + k] : 0.0;
-    split_store<MODE>(x, hi, lo, idx);
+    split_store<MODE>(x, parts, idx, sc);
   }
 }
 
 // t2L[q][x][y][l] = t2[l][q][x][y], l padded to op
 template <int MODE>
-__global__ void k_split_t2L(const double* __restrict__ t2, void* hi, void* lo, int o, int v, int op) {
+__global__ void k_split_t2L(const double* __restrict__ t2, Parts parts, int o, int v, int op, const int* exps,
+                            int which) {
+  const double sc = scale_of(exps, which);
   const int64_t n = (int64_t)o * v * v * op;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -83,13 +135,15 @@ __global__ void k_split_t2L(const double* __restrict__ t2, void* hi, void* lo, i
     const int x = (int)(rest % v);
     const int q = (int)(rest / v);
     const double val = l < o ? t2[(((int64_t)l * o + q) * v + x) * v + y] : 0.0;
-    split_store<MODE>(val, hi, lo, idx);
+    split_store<MODE>(val, parts, idx, sc);
   }
 }
 
 // nooT[p][r][z][l] = -ooov[p][l][r][z], l padded to op
 template <int MODE>
-__global__ void k_split_noo(const double* __restrict__ ooov, void* hi, void* lo, int o, int v, int op) {
+__global__ void k_split_noo(const double* __restrict__ ooov, Parts parts, int o, int v, int op, const int* exps,
+                            int which) {
+  const double sc = scale_of(exps, which);
   const int64_t n = (int64_t)o * o * v * op;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -100,28 +154,77 @@ __global__ void k_split_noo(const double* __restrict__ ooov, void* hi, void* lo,
     const int r = (int)(rest % o);
     const int p = (int)(rest / o);
     const double val = l < o ? -ooov[(((int64_t)p * o + l) * o + r) * v + z] : 0.0;
-    split_store<MODE>(val, hi, lo, idx);
+    split_store<MODE>(val, parts, idx, sc);
   }
 }
 
-__global__ void k_ovs32(const double* __restrict__ ovov, float* __restrict__ ovs32, int o, int v) {
-  const int64_t n = (int64_t)o * v * o * v;
+// ovs32[i][a][j][b] = 1/2 (ovov[i,a,j,b] + ovov[j,b,i,a]), b padded to vq
+__global__ void k_ovs32(const double* __restrict__ ovov, float* __restrict__ ovs32, int o, int v, int vq) {
+  const int64_t n = (int64_t)o * v * o * vq;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(idx % v);
-    int64_t rest = idx / v;
+    const int b = (int)(idx % vq);
+    int64_t rest = idx / vq;
     const int j = (int)(rest % o);
     rest /= o;
     const int a = (int)(rest % v);
     const int i = (int)(rest / v);
-    ovs32[idx] = (float)(0.5 * (ovov[idx] + ovov[(((int64_t)j * v + b) * o + i) * v + a]));
+    float val = 0.f;
+    if (b < v)
+      val = (float)(0.5 * (ovov[(((int64_t)i * v + a) * o + j) * v + b] +
+                           ovov[(((int64_t)j * v + b) * o + i) * v + a]));
+    ovs32[idx] = val;
   }
 }
 
-__global__ void k_t1_32(const double* __restrict__ t1, float* __restrict__ out, int64_t n) {
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
-       idx += (int64_t)gridDim.x * blockDim.x)
-    out[idx] = (float)t1[idx];
+// t1_32[i][a] (a padded to vq) and a copy of eps_v
+__global__ void k_small_copies(const double* __restrict__ t1, const double* __restrict__ eps_v,
+                               float* __restrict__ t1_32, double* __restrict__ eps_copy, int o, int v, int vq) {
+  const int64_t n = (int64_t)o * vq;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n + v;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < n) {
+      const int a = (int)(idx % vq);
+      const int i = (int)(idx / vq);
+      t1_32[idx] = a < v ? (float)t1[(int64_t)i * v + a] : 0.f;
+    } else {
+      eps_copy[idx - n] = eps_v[idx - n];
+    }
+  }
+}
+
+// max |x| of three arrays (bit patterns of non-negative doubles order as integers)
+__global__ void k_maxabs(const double* __restrict__ a, int64_t na, const double* __restrict__ b, int64_t nb,
+                         const double* __restrict__ c, int64_t nc, unsigned long long* out) {
+  const double* src[3] = {a, b, c};
+  const int64_t n[3] = {na, nb, nc};
+  for (int w = 0; w < 3; ++w) {
+    double m = 0.0;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n[w];
+         idx += (int64_t)gridDim.x * blockDim.x)
+      m = fmax(m, fabs(src[w][idx]));
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out + w, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// Scale exponents: every segment of the K axis gets the unit 2^U.
+// exps = {s_ovvv, s_t2, s_t2L, s_nooT, U}
+__global__ void k_exponents(const unsigned long long* maxbits, int* exps) {
+  int e[3];
+  for (int w = 0; w < 3; ++w) {
+    const double m = __longlong_as_double((long long)maxbits[w]);
+    int ex = 0;
+    if (m > 0.0) frexp(m, &ex);  // m < 2^ex
+    e[w] = ex;
+  }
+  const int Eovvv = e[0], Et2 = e[1], Eooov = e[2];
+  const int U = max(Eovvv + Et2, Et2 + Eooov);
+  exps[0] = U - Et2;    // ovvv slices
+  exps[1] = Et2;        // t2 slices
+  exps[2] = U - Eooov;  // t2L slices
+  exps[3] = Eooov;      // nooT slices
+  exps[4] = U;
 }
 
 static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 16384); }
@@ -131,12 +234,12 @@ static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1,
 // ---------------------------------------------------------------------------
 
 struct TcMaps {
-  CUtensorMap a_nat[2];  // ovvv split, dims (Kp, y, x, p): rows (x,y) of ovvv[p]
-  CUtensorMap a_tr[2];   // ovvv split, dims (Kp, y, x, q) with strides swapped: ovvv[q,y,x,:]
-  CUtensorMap l_nat[2];  // t2L split natural
-  CUtensorMap l_tr[2];   // t2L split transposed
-  CUtensorMap b_t2[2];   // t2 split, dims (Kp, z, q, r)
-  CUtensorMap b_noo[2];  // nooT split, dims (Kp, z, r, p)
+  CUtensorMap a_nat[4];  // ovvv parts, dims (Kp, y, x, p): rows (x,y) of ovvv[p]
+  CUtensorMap a_tr[4];   // ovvv parts, dims (Kp, y, x, q) with strides swapped: ovvv[q,y,x,:]
+  CUtensorMap l_nat[4];  // t2L parts natural
+  CUtensorMap l_tr[4];   // t2L parts transposed
+  CUtensorMap b_t2[4];   // t2 parts, dims (Kp, z, q, r)
+  CUtensorMap b_noo[4];  // nooT parts, dims (Kp, z, r, p)
 };
 
 struct TcParams {
@@ -153,7 +256,8 @@ struct TcParams {
   int64_t t0;
   const Triple* triples;
   float* gbuf;
-  int ldz;
+  int ldz;                 // G row stride in elements (an element is 1 or 2 floats)
+  const int* exps;         // OZAKI scale exponents
   unsigned int* err;
   unsigned long long wait_ns;
 };
@@ -193,11 +297,20 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& P, int64_t tt) 
   return c;
 }
 
+// Knuth's two-sum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMaps maps, const TcParams P) {
-  constexpr bool TF32 = (MODE != TC_BF16X3);
-  constexpr bool X3 = (MODE != TC_TF32);
-  constexpr int NPART = X3 ? 2 : 1;
+  using MT = ModeTraits<MODE>;
+  constexpr bool TF32 = MT::tf32;
+  constexpr int NPART = MT::nparts;
+  constexpr int NACC = MT::nacc;
+  constexpr int NBUF = MT::nbuf;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~uintptr_t(1023));
@@ -313,8 +426,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t d_tmem = tmem_base + acc * (uint32_t)P.NT;
-        uint32_t accum = 0;
+        const uint32_t d_tmem = tmem_base + acc * (uint32_t)(NACC * P.NT);
+        uint32_t first = 1;
         for (int seg = 0; ok && seg < 4; ++seg) {
           const bool wide = seg < 2;
           const int nch = wide ? P.kw_chunks : P.ko_chunks;
@@ -332,16 +445,33 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
             const uint32_t a0 = ptx::smem_u32(sa);
             const uint32_t b0 = ptx::smem_u32(sa + NPART * P.a_part_bytes);
             for (int ks = 0; ks < cb / 32; ++ks) {
-              const uint64_t ah = ptx::smem_desc(a0 + ks * 32, sbo, lay);
-              const uint64_t bh = ptx::smem_desc(b0 + ks * 32, sbo, lay);
-              ptx::mma<TF32>(d_tmem, ah, bh, idesc, accum);
-              accum = 1;
-              if (X3) {
-                const uint64_t al = ptx::smem_desc(a0 + P.a_part_bytes + ks * 32, sbo, lay);
-                const uint64_t bl = ptx::smem_desc(b0 + P.b_part_bytes + ks * 32, sbo, lay);
-                ptx::mma<TF32>(d_tmem, ah, bl, idesc, 1);
-                ptx::mma<TF32>(d_tmem, al, bh, idesc, 1);
+              uint64_t ad[NPART], bd[NPART];
+#pragma unroll
+              for (int k = 0; k < NPART; ++k) {
+                ad[k] = ptx::smem_desc(a0 + k * P.a_part_bytes + ks * 32, sbo, lay);
+                bd[k] = ptx::smem_desc(b0 + k * P.b_part_bytes + ks * 32, sbo, lay);
               }
+              const uint32_t acc_in = first ? 0u : 1u;
+              if constexpr (MODE == TC_OZAKI) {
+                const uint32_t d2 = d_tmem, d3 = d_tmem + P.NT, dr = d_tmem + 2 * P.NT;
+                ptx::mma<false>(d2, ad[0], bd[0], idesc, acc_in);  // level 2
+                ptx::mma<false>(d3, ad[0], bd[1], idesc, acc_in);  // level 3
+                ptx::mma<false>(d3, ad[1], bd[0], idesc, 1);
+                ptx::mma<false>(dr, ad[0], bd[2], idesc, acc_in);  // levels 4 and 5
+                ptx::mma<false>(dr, ad[1], bd[1], idesc, 1);
+                ptx::mma<false>(dr, ad[2], bd[0], idesc, 1);
+                ptx::mma<false>(dr, ad[0], bd[3], idesc, 1);
+                ptx::mma<false>(dr, ad[1], bd[2], idesc, 1);
+                ptx::mma<false>(dr, ad[2], bd[1], idesc, 1);
+                ptx::mma<false>(dr, ad[3], bd[0], idesc, 1);
+              } else {
+                ptx::mma<TF32>(d_tmem, ad[0], bd[0], idesc, acc_in);
+                if constexpr (NPART == 2) {
+                  ptx::mma<TF32>(d_tmem, ad[0], bd[1], idesc, 1);
+                  ptx::mma<TF32>(d_tmem, ad[1], bd[0], idesc, 1);
+                }
+              }
+              first = 0;
             }
             issued = true;
             ptx::mma_commit(&empty[stage]);
@@ -353,8 +483,12 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
         }
         if (!ok) break;
         ptx::mma_commit(&tfull[acc]);
-        acc ^= 1u;
-        if (acc == 0) acc_phase ^= 1u;
+        if (NBUF == 2) {
+          acc ^= 1u;
+          if (acc == 0) acc_phase ^= 1u;
+        } else {
+          acc_phase ^= 1u;
+        }
       }
       // every issued MMA completes before TMEM is released
       if (issued) {
@@ -367,6 +501,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     const int64_t v2 = (int64_t)P.v * P.v;
+    float gscale = 1.f;
+    if (MODE == TC_OZAKI) gscale = ldexpf(1.f, P.exps[4]);
     uint32_t acc = 0, acc_phase = 0;
     for (int64_t tt = blockIdx.x; tt < P.total_tiles; tt += gridDim.x) {
       const TileCoord c = decode_tile(P, tt);
@@ -381,30 +517,54 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
       const int x = c.x0 + row / P.TB;
       const int y = c.y0 + row % P.TB;
       const bool valid = x < P.v && y < P.v;
-      float* out = P.gbuf + ((int64_t)(c.slot * 3 + c.g) * v2 + (int64_t)x * P.v + y) * P.ldz;
-      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)P.NT;
+      const int64_t orow = ((int64_t)(c.slot * 3 + c.g) * v2 + (int64_t)x * P.v + y) * P.ldz;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)(NACC * P.NT);
       for (int c0 = 0; c0 < P.NT; c0 += 16) {
-        float vals[16];
-        ptx::tmem_ld16(tbase + c0, vals);
         const int z = c.z0 + c0;
-        if (valid) {
-          if (z + 16 <= P.ldz) {
-            float4* o4 = reinterpret_cast<float4*>(out + z);
+        if constexpr (MODE == TC_OZAKI) {
+          float a2[16], a3[16], ar[16];
+          ptx::tmem_ld16(tbase + c0, a2);
+          ptx::tmem_ld16(tbase + P.NT + c0, a3);
+          ptx::tmem_ld16(tbase + 2 * P.NT + c0, ar);
+          if (valid) {
+            float2* out = reinterpret_cast<float2*>(P.gbuf) + orow;
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4)
-              o4[q4] = make_float4(vals[4 * q4], vals[4 * q4 + 1], vals[4 * q4 + 2], vals[4 * q4 + 3]);
-          } else {
+            for (int j = 0; j < 16; ++j) {
+              float s, e;
+              two_sum(a2[j], a3[j], s, e);
+              const float lo = __fadd_rn(e, ar[j]);
+              const float hi = __fadd_rn(s, lo);
+              const float lo2 = __fsub_rn(lo, __fsub_rn(hi, s));
+              if (z + j < P.v) out[z + j] = make_float2(hi * gscale, lo2 * gscale);
+            }
+          }
+        } else {
+          float vals[16];
+          ptx::tmem_ld16(tbase + c0, vals);
+          if (valid) {
+            float* out = P.gbuf + orow;
+            if (z + 16 <= P.ldz) {
+              float4* o4 = reinterpret_cast<float4*>(out + z);
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (z + j < P.v) out[z + j] = vals[j];
+              for (int q4 = 0; q4 < 4; ++q4)
+                o4[q4] = make_float4(vals[4 * q4], vals[4 * q4 + 1], vals[4 * q4 + 2], vals[4 * q4 + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (z + j < P.v) out[z + j] = vals[j];
+            }
           }
         }
       }
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
-      acc ^= 1u;
-      if (acc == 0) acc_phase ^= 1u;
+      if (NBUF == 2) {
+        acc ^= 1u;
+        if (acc == 0) acc_phase ^= 1u;
+      } else {
+        acc_phase ^= 1u;
+      }
     }
   }
 
@@ -422,7 +582,6 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
 
 struct TcState {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  bool attr_done[3] = {false, false, false};
 };
 
 static TcState* tc_state(Handle* h) {
@@ -450,8 +609,8 @@ static te_status get_encoder(TcState* st) {
 }
 
 struct TcPlan {
-  int mode, es;
-  int vp, op;
+  int mode, es, nparts, cw;
+  int vp, op, vq;
   int TA, TB, NT, n_mx, n_my, n_nt;
   int kw_chunks, ko_chunks, kw_elems, ko_elems, cbw, cbo;
   int stages;
@@ -466,9 +625,13 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri) {
   TcPlan pl{};
   pl.mode = mode;
-  pl.es = (mode == TC_BF16X3) ? 2 : 4;
+  pl.es = (mode == TC_BF16X3 || mode == TC_OZAKI) ? 2 : 4;
+  pl.nparts = mode == TC_TF32 ? 1 : (mode == TC_OZAKI ? 4 : 2);
+  pl.cw = mode == TC_OZAKI ? 2 : 1;
+  const int nacc = mode == TC_OZAKI ? 3 : 1, nbuf = mode == TC_OZAKI ? 1 : 2;
   pl.vp = round_up(v, 16);
   pl.op = round_up(o, 16);
+  pl.vq = round_up(v, 4);
   // M tile: TA x-values by TB y-values, TA*TB = 128, least padding
   int bestTB = 128;
   int64_t best = -1;
@@ -484,29 +647,29 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri) {
   pl.TA = 128 / bestTB;
   pl.n_mx = (v + pl.TA - 1) / pl.TA;
   pl.n_my = (v + pl.TB - 1) / pl.TB;
-  pl.n_nt = (v + 255) / 256;
+  const int ntmax = std::min(256, (512 / (nacc * nbuf)) / 16 * 16);
+  pl.n_nt = (v + ntmax - 1) / ntmax;
   pl.NT = round_up((v + pl.n_nt - 1) / pl.n_nt, 16);
-  pl.cbw = 128;
-  pl.kw_elems = 128 / pl.es;
+  pl.cbw = mode == TC_OZAKI ? 64 : 128;
+  pl.kw_elems = pl.cbw / pl.es;
   pl.kw_chunks = (pl.vp + pl.kw_elems - 1) / pl.kw_elems;
   const int obytes = pl.op * pl.es;
-  pl.cbo = obytes <= 32 ? 32 : (obytes <= 64 ? 64 : 128);
+  pl.cbo = obytes <= 32 ? 32 : (obytes <= 64 ? 64 : std::min(128, pl.cbw));
   pl.ko_elems = pl.cbo / pl.es;
   pl.ko_chunks = (pl.op + pl.ko_elems - 1) / pl.ko_elems;
-  const int npart = (mode == TC_TF32) ? 1 : 2;
-  pl.a_part_bytes = 128u * 128u;
-  pl.b_part_bytes = (uint32_t)pl.NT * 128u;
-  pl.stage_bytes = (uint32_t)npart * (pl.a_part_bytes + pl.b_part_bytes);
+  pl.a_part_bytes = 128u * (uint32_t)pl.cbw;
+  pl.b_part_bytes = (uint32_t)pl.NT * (uint32_t)pl.cbw;
+  pl.stage_bytes = (uint32_t)pl.nparts * (pl.a_part_bytes + pl.b_part_bytes);
   const size_t avail = h->smem_optin > 2048 ? h->smem_optin - 2048 : 0;
   pl.stages = (int)std::min<size_t>(8, avail / pl.stage_bytes);
   pl.smem = (size_t)pl.stages * pl.stage_bytes + 1024 + 256;
   uint32_t cols = 32;
-  while (cols < 2u * (uint32_t)pl.NT) cols <<= 1;
+  while (cols < (uint32_t)(nacc * nbuf * pl.NT)) cols <<= 1;
   pl.tmem_cols = cols;
   pl.ldz = round_up(v, 4);
   const int64_t tiles = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
   int64_t want = (4LL * std::max(1, h->num_sms) + tiles - 1) / tiles;
-  const int64_t per_slot = 3LL * v * v * pl.ldz * 4;
+  const int64_t per_slot = 3LL * v * v * pl.ldz * 4 * pl.cw;
   const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(3LL << 30) / per_slot);
   want = std::min<int64_t>({want, mem_cap, 1024, std::max<int64_t>(1, ntri)});
   pl.nslots = (int)std::max<int64_t>(1, want);
@@ -514,9 +677,11 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri) {
 }
 
 struct TcBuffers {
-  void *a_hi, *a_lo, *b_hi, *b_lo, *l_hi, *l_lo, *n_hi, *n_lo;
+  void *a[4], *b[4], *l[4], *n[4];
   float *ovs32, *t1_32, *gbuf;
-  double *partials, *etri;
+  double *eps_copy, *partials, *etri;
+  unsigned long long* maxbits;
+  int* exps;
 };
 
 static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64_t nbt, int64_t ntri,
@@ -528,36 +693,42 @@ static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64
     off += bytes;
     return p;
   };
-  const bool x3 = pl.mode != TC_TF32;
   const size_t es = (size_t)pl.es;
   const size_t na = (size_t)o * v * v * pl.vp, nb = (size_t)o * o * v * pl.vp;
   const size_t nl = (size_t)o * v * v * pl.op, nn = (size_t)o * o * v * pl.op;
-  b->a_hi = take(na * es);
-  b->a_lo = x3 ? take(na * es) : nullptr;
-  b->b_hi = take(nb * es);
-  b->b_lo = x3 ? take(nb * es) : nullptr;
-  b->l_hi = take(nl * es);
-  b->l_lo = x3 ? take(nl * es) : nullptr;
-  b->n_hi = take(nn * es);
-  b->n_lo = x3 ? take(nn * es) : nullptr;
-  b->ovs32 = static_cast<float*>(take((size_t)o * v * o * v * 4));
-  b->t1_32 = static_cast<float*>(take((size_t)o * v * 4));
-  b->gbuf = static_cast<float*>(take((size_t)pl.nslots * 3 * v * v * pl.ldz * 4));
+  for (int k = 0; k < 4; ++k) {
+    const bool use = k < pl.nparts;
+    b->a[k] = use ? take(na * es) : nullptr;
+    b->b[k] = use ? take(nb * es) : nullptr;
+    b->l[k] = use ? take(nl * es) : nullptr;
+    b->n[k] = use ? take(nn * es) : nullptr;
+  }
+  b->ovs32 = static_cast<float*>(take((size_t)o * v * o * pl.vq * 4));
+  b->t1_32 = static_cast<float*>(take((size_t)o * pl.vq * 4));
+  b->eps_copy = static_cast<double*>(take((size_t)v * 8));
+  b->gbuf = static_cast<float*>(take((size_t)pl.nslots * 3 * v * v * pl.ldz * 4 * pl.cw));
   b->partials = static_cast<double*>(take((size_t)pl.nslots * nbt * 8));
   b->etri = static_cast<double*>(take((size_t)std::max<int64_t>(1, ntri) * 8));
+  b->maxbits = static_cast<unsigned long long*>(take(4 * 8));
+  b->exps = static_cast<int*>(take(8 * 4));
   return off + 1024;
 }
 
-static te_status encode_4d(TcState* st, CUtensorMap* m, const void* base, CUtensorMapDataType dt, int es,
-                           const uint64_t dims[4], const uint64_t strides_bytes[3], const uint32_t box[4],
-                           CUtensorMapSwizzle swz, const char* what) {
-  cuuint64_t gd[4] = {dims[0], dims[1], dims[2], dims[3]};
-  cuuint64_t gs[3] = {strides_bytes[0], strides_bytes[1], strides_bytes[2]};
-  cuuint32_t bd[4] = {box[0], box[1], box[2], box[3]};
-  cuuint32_t es1[4] = {1, 1, 1, 1};
-  (void)es;
-  CUresult r = st->encode(m, dt, 4, const_cast<void*>(base), gd, gs, bd, es1, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+static te_status encode(TcState* st, CUtensorMap* m, const void* base, CUtensorMapDataType dt, int rank,
+                        const uint64_t* dims, const uint64_t* strides_bytes, const uint32_t* box,
+                        CUtensorMapSwizzle swz, const char* what) {
+  cuuint64_t gd[5];
+  cuuint64_t gs[4];
+  cuuint32_t bd[5], e1[5];
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bd[i] = box[i];
+    e1[i] = 1;
+    if (i < rank - 1) gs[i] = strides_bytes[i];
+  }
+  CUresult r = st->encode(m, dt, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bd, e1,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TE_ECUDA, "tensor map encoding failed for %s (CUresult %d)", what, (int)r);
   return TE_OK;
 }
@@ -568,46 +739,83 @@ static CUtensorMapSwizzle swz_of(int cb) {
 
 static te_status build_maps(TcState* st, const TcPlan& pl, int o, int v, const TcBuffers& b, TcMaps* M) {
   std::memset(M, 0, sizeof(*M));
-  const CUtensorMapDataType dt =
-      pl.mode == TC_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = pl.es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const uint64_t es = (uint64_t)pl.es;
   const uint64_t vp = pl.vp, op = pl.op, V = v, O = o;
-  const int npart = pl.mode == TC_TF32 ? 1 : 2;
-  for (int k = 0; k < npart; ++k) {
-    const void* A = k ? b.a_lo : b.a_hi;
-    const void* B = k ? b.b_lo : b.b_hi;
-    const void* L = k ? b.l_lo : b.l_hi;
-    const void* N = k ? b.n_lo : b.n_hi;
+  for (int k = 0; k < pl.nparts; ++k) {
     te_status s;
     {  // ovvv[p][x][y][d]: dims (d, y, x, p)
       const uint64_t d[4] = {vp, V, V, O};
       const uint64_t sn[3] = {vp * es, V * vp * es, V * V * vp * es};
       const uint32_t box[4] = {(uint32_t)pl.kw_elems, (uint32_t)pl.TB, (uint32_t)pl.TA, 1};
-      if ((s = encode_4d(st, &M->a_nat[k], A, dt, pl.es, d, sn, box, swz_of(pl.cbw), "ovvv")) != TE_OK) return s;
+      if ((s = encode(st, &M->a_nat[k], b.a[k], dt, 4, d, sn, box, swz_of(pl.cbw), "ovvv")) != TE_OK) return s;
       // transposed rows: element (d, y, x, q) at ovvv[q][y][x][d]
       const uint64_t stt[3] = {V * vp * es, vp * es, V * V * vp * es};
-      if ((s = encode_4d(st, &M->a_tr[k], A, dt, pl.es, d, stt, box, swz_of(pl.cbw), "ovvv^T")) != TE_OK) return s;
+      if ((s = encode(st, &M->a_tr[k], b.a[k], dt, 4, d, stt, box, swz_of(pl.cbw), "ovvv^T")) != TE_OK) return s;
     }
     {  // t2L[q][x][y][l]: dims (l, y, x, q)
       const uint64_t d[4] = {op, V, V, O};
       const uint64_t sn[3] = {op * es, V * op * es, V * V * op * es};
       const uint32_t box[4] = {(uint32_t)pl.ko_elems, (uint32_t)pl.TB, (uint32_t)pl.TA, 1};
-      if ((s = encode_4d(st, &M->l_nat[k], L, dt, pl.es, d, sn, box, swz_of(pl.cbo), "t2L")) != TE_OK) return s;
+      if ((s = encode(st, &M->l_nat[k], b.l[k], dt, 4, d, sn, box, swz_of(pl.cbo), "t2L")) != TE_OK) return s;
       const uint64_t stt[3] = {V * op * es, op * es, V * V * op * es};
-      if ((s = encode_4d(st, &M->l_tr[k], L, dt, pl.es, d, stt, box, swz_of(pl.cbo), "t2L^T")) != TE_OK) return s;
+      if ((s = encode(st, &M->l_tr[k], b.l[k], dt, 4, d, stt, box, swz_of(pl.cbo), "t2L^T")) != TE_OK) return s;
     }
     {  // t2[r][q][z][d]: dims (d, z, q, r)
       const uint64_t d[4] = {vp, V, O, O};
       const uint64_t sn[3] = {vp * es, V * vp * es, O * V * vp * es};
       const uint32_t box[4] = {(uint32_t)pl.kw_elems, (uint32_t)pl.NT, 1, 1};
-      if ((s = encode_4d(st, &M->b_t2[k], B, dt, pl.es, d, sn, box, swz_of(pl.cbw), "t2")) != TE_OK) return s;
+      if ((s = encode(st, &M->b_t2[k], b.b[k], dt, 4, d, sn, box, swz_of(pl.cbw), "t2")) != TE_OK) return s;
     }
     {  // nooT[p][r][z][l]: dims (l, z, r, p)
       const uint64_t d[4] = {op, V, O, O};
       const uint64_t sn[3] = {op * es, V * op * es, O * V * op * es};
       const uint32_t box[4] = {(uint32_t)pl.ko_elems, (uint32_t)pl.NT, 1, 1};
-      if ((s = encode_4d(st, &M->b_noo[k], N, dt, pl.es, d, sn, box, swz_of(pl.cbo), "nooT")) != TE_OK) return s;
+      if ((s = encode(st, &M->b_noo[k], b.n[k], dt, 4, d, sn, box, swz_of(pl.cbo), "nooT")) != TE_OK) return s;
     }
+  }
+  return TE_OK;
+}
+
+struct EnergyMapsHost {
+  CUtensorMap g, ovs, t1, eps;
+};
+
+static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, int nslots, const TcBuffers& b,
+                                   EnergyMapsHost* E) {
+  std::memset(E, 0, sizeof(*E));
+  const uint64_t V = v, O = o, cw = pl.cw, ldz = pl.ldz, vq = pl.vq;
+  te_status s;
+  {  // G [slot][g][x][y][ldz*cw] floats: dims (z*cw, y, x, g, slot)
+    const uint64_t d[5] = {V * cw, V, V, 3, (uint64_t)nslots};
+    const uint64_t sn[4] = {ldz * cw * 4, V * ldz * cw * 4, V * V * ldz * cw * 4, 3 * V * V * ldz * cw * 4};
+    const uint32_t box[5] = {(uint32_t)(8 * cw), 8, 8, 1, 1};
+    if ((s = encode(st, &E->g, b.gbuf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, d, sn, box,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, "G")) != TE_OK)
+      return s;
+  }
+  {  // ovs32 [i][a][j][vq]: dims (b, j, a, i)
+    const uint64_t d[4] = {V, O, V, O};
+    const uint64_t sn[3] = {vq * 4, O * vq * 4, V * O * vq * 4};
+    const uint32_t box[4] = {8, 1, 8, 1};
+    if ((s = encode(st, &E->ovs, b.ovs32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d, sn, box,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, "ovs")) != TE_OK)
+      return s;
+  }
+  {  // t1 [i][vq]: dims (a, i)
+    const uint64_t d[2] = {V, O};
+    const uint64_t sn[1] = {vq * 4};
+    const uint32_t box[2] = {8, 1};
+    if ((s = encode(st, &E->t1, b.t1_32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d, sn, box,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, "t1")) != TE_OK)
+      return s;
+  }
+  {  // eps_v copy [v] FP64
+    const uint64_t d[1] = {V};
+    const uint32_t box[1] = {8};
+    if ((s = encode(st, &E->eps, b.eps_copy, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 1, d, nullptr, box,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, "eps")) != TE_OK)
+      return s;
   }
   return TE_OK;
 }
@@ -615,27 +823,31 @@ static te_status build_maps(TcState* st, const TcPlan& pl, int o, int v, const T
 template <int MODE>
 static cudaError_t launch_prep_tc(const te_cluster* c, const TcPlan& pl, const TcBuffers& b, cudaStream_t s) {
   const int o = (int)c->nocc, v = (int)c->nvir;
-  k_split_rows<MODE><<<gridn((int64_t)o * v * v * pl.vp), 256, 0, s>>>(c->ovvv, b.a_hi, b.a_lo,
-                                                                       (int64_t)o * v * v, v, pl.vp);
-  k_split_rows<MODE><<<gridn((int64_t)o * o * v * pl.vp), 256, 0, s>>>(c->t2, b.b_hi, b.b_lo,
-                                                                       (int64_t)o * o * v, v, pl.vp);
-  k_split_t2L<MODE><<<gridn((int64_t)o * v * v * pl.op), 256, 0, s>>>(c->t2, b.l_hi, b.l_lo, o, v, pl.op);
-  k_split_noo<MODE><<<gridn((int64_t)o * o * v * pl.op), 256, 0, s>>>(c->ooov, b.n_hi, b.n_lo, o, v, pl.op);
-  k_ovs32<<<gridn((int64_t)o * v * o * v), 256, 0, s>>>(c->ovov, b.ovs32, o, v);
-  k_t1_32<<<gridn((int64_t)o * v), 256, 0, s>>>(c->t1, b.t1_32, (int64_t)o * v);
+  const int* ex = nullptr;
+  if (MODE == TC_OZAKI) {
+    cudaMemsetAsync(b.maxbits, 0, 4 * 8, s);
+    k_maxabs<<<1024, 256, 0, s>>>(c->ovvv, (int64_t)o * v * v * v, c->t2, (int64_t)o * o * v * v, c->ooov,
+                                  (int64_t)o * o * o * v, b.maxbits);
+    k_exponents<<<1, 1, 0, s>>>(b.maxbits, b.exps);
+    ex = b.exps;
+  }
+  const Parts A{{b.a[0], b.a[1], b.a[2], b.a[3]}}, B{{b.b[0], b.b[1], b.b[2], b.b[3]}};
+  const Parts Lp{{b.l[0], b.l[1], b.l[2], b.l[3]}}, N{{b.n[0], b.n[1], b.n[2], b.n[3]}};
+  k_split_rows<MODE><<<gridn((int64_t)o * v * v * pl.vp), 256, 0, s>>>(c->ovvv, A, (int64_t)o * v * v, v, pl.vp,
+                                                                       ex, 0);
+  k_split_rows<MODE><<<gridn((int64_t)o * o * v * pl.vp), 256, 0, s>>>(c->t2, B, (int64_t)o * o * v, v, pl.vp,
+                                                                       ex, 1);
+  k_split_t2L<MODE><<<gridn((int64_t)o * v * v * pl.op), 256, 0, s>>>(c->t2, Lp, o, v, pl.op, ex, 2);
+  k_split_noo<MODE><<<gridn((int64_t)o * o * v * pl.op), 256, 0, s>>>(c->ooov, N, o, v, pl.op, ex, 3);
+  k_ovs32<<<gridn((int64_t)o * v * o * pl.vq), 256, 0, s>>>(c->ovov, b.ovs32, o, v, pl.vq);
+  k_small_copies<<<gridn((int64_t)o * pl.vq + v), 256, 0, s>>>(c->t1, c->eps_v, b.t1_32, b.eps_copy, o, v, pl.vq);
   return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_gemm_tc(TcState* st, const Handle* h, const TcMaps& M, const TcParams& P,
-                                  size_t smem, cudaStream_t s) {
-  if (!st->attr_done[MODE]) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    st->attr_done[MODE] = true;
-  } else {
-    cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
+static cudaError_t launch_gemm_tc(const Handle* h, const TcMaps& M, const TcParams& P, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(P.total_tiles, h->num_sms);
   k_gemm_tc<MODE><<<(unsigned)grid, 192, smem, s>>>(M, P);
   return cudaGetLastError();
@@ -666,6 +878,9 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   const int64_t nt = t_end - t_begin;
   const TcPlan pl = make_plan(h, o, v, mode, nt);
   if (pl.stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
+  // exact level-2/3 sums: K * 2^14 (two products per level-3 term, each < 2^13) below 2^24
+  if (mode == TC_OZAKI && 2 * (pl.kw_chunks * pl.kw_elems + pl.ko_chunks * pl.ko_elems) > 1024)
+    return fail(TE_EUNSUPPORTED, "OZAKI mode needs 2 (nvir + nocc) <= 1024 (padded) for exact accumulation");
   const int64_t nbt = energy_num_block_triples(v);
   TcBuffers b;
   const size_t bytes = tc_carve(nullptr, pl, o, v, nbt, ntri, &b);
@@ -679,11 +894,16 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   cudaError_t e;
   if (mode == TC_BF16X3) e = launch_prep_tc<TC_BF16X3>(c, pl, b, s);
   else if (mode == TC_TF32X3) e = launch_prep_tc<TC_TF32X3>(c, pl, b, s);
-  else e = launch_prep_tc<TC_TF32>(c, pl, b, s);
+  else if (mode == TC_TF32) e = launch_prep_tc<TC_TF32>(c, pl, b, s);
+  else e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
+  h->n_launches += mode == TC_OZAKI ? 8 : 6;
   if (e != cudaSuccess) return fail(TE_ECUDA, "operand split launch: %s", cudaGetErrorString(e));
 
   TcMaps M;
   rs = build_maps(st, pl, o, v, b, &M);
+  if (rs != TE_OK) return rs;
+  EnergyMapsHost EM;
+  rs = build_energy_maps(st, pl, o, v, pl.nslots, b, &EM);
   if (rs != TE_OK) return rs;
 
   TcParams P{};
@@ -709,33 +929,45 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   P.triples = h->d_triples;
   P.gbuf = b.gbuf;
   P.ldz = pl.ldz;
+  P.exps = b.exps;
   P.err = h->d_err;
   P.wait_ns = h->wait_limit_ns;
 
-  Prepared Pr{};
-  Pr.o = o;
-  Pr.v = v;
-  Pr.eps_o = c->eps_o;
-  Pr.eps_v = c->eps_v;
-  Pr.ovs32 = b.ovs32;
-  Pr.t1_32 = b.t1_32;
-  h->n_launches += 6;
+  EnergyLaunch EL{};
+  EL.o = o;
+  EL.v = v;
+  EL.cw = pl.cw;
+  EL.num_sms = h->num_sms;
+  EL.nbt = nbt;
+  EL.map_g = &EM.g;
+  EL.map_ovs = &EM.ovs;
+  EL.map_t1 = &EM.t1;
+  EL.map_eps = &EM.eps;
+  EL.triples = h->d_triples;
+  EL.eps_o = c->eps_o;
+  EL.partials = b.partials;
+  EL.err = h->d_err;
+  EL.wait_ns = h->wait_limit_ns;
+
   double* out = e_tri_out ? e_tri_out : b.etri;
-  const double nprod = (mode == TC_TF32) ? 1.0 : 3.0;
+  const double nprod = (mode == TC_TF32) ? 1.0 : (mode == TC_OZAKI ? 10.0 : 3.0);
   const double kpad = 2.0 * pl.kw_chunks * pl.kw_elems + 2.0 * pl.ko_chunks * pl.ko_elems;
   for (int64_t t0 = t_begin; t0 < t_end; t0 += pl.nslots) {
     const int ns = (int)std::min<int64_t>(pl.nslots, t_end - t0);
     P.t0 = t0;
     P.total_tiles = 3LL * ns * pl.n_mx * pl.n_my * pl.n_nt;
     size_t pm = prof_begin(h, 0, s);
-    if (mode == TC_BF16X3) e = launch_gemm_tc<TC_BF16X3>(st, h, M, P, pl.smem, s);
-    else if (mode == TC_TF32X3) e = launch_gemm_tc<TC_TF32X3>(st, h, M, P, pl.smem, s);
-    else e = launch_gemm_tc<TC_TF32>(st, h, M, P, pl.smem, s);
+    if (mode == TC_BF16X3) e = launch_gemm_tc<TC_BF16X3>(h, M, P, pl.smem, s);
+    else if (mode == TC_TF32X3) e = launch_gemm_tc<TC_TF32X3>(h, M, P, pl.smem, s);
+    else if (mode == TC_TF32) e = launch_gemm_tc<TC_TF32>(h, M, P, pl.smem, s);
+    else e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
     prof_end(h, pm, s);
     h->gemm_flops += 2.0 * nprod * (double)P.total_tiles * 128.0 * pl.NT * kpad;
     if (e == cudaSuccess) {
+      EL.nslots = ns;
+      EL.t0 = t0;
       pm = prof_begin(h, 1, s);
-      e = launch_energy_f32(&Pr, h->d_triples, t0, ns, b.gbuf, pl.ldz, b.partials, nbt, s);
+      e = launch_energy_tc(EL, s);
       prof_end(h, pm, s);
     }
     if (e == cudaSuccess)
