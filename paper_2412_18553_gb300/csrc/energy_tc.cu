@@ -1,10 +1,12 @@
 // Energy epilogue of the tensor-core modes: a persistent kernel fed by TMA.
 //
 // Work item = (triple slot, block triple X >= Y >= Z of 8-wide virtual
-// blocks).  One warp issues the item's TMA loads into the idle half of a
-// double buffer (18 G cubes: 3 G blocks x 6 block orders; 27 8x8 blocks of
-// the symmetrised ovov; 9 t1 rows; 3 eps_v rows) while all eight warps work
-// on the other half.  G is either FP32 (BF16X3/TF32/TF32X3) or an FP32 pair
+// blocks).  The G blocks are stored cube-major by the contraction kernel
+// ([X][Y][Z][8][8][8], each 8^3 cube contiguous), so each of the item's 18 G
+// cubes (3 G blocks x 6 block orders) arrives by one bulk copy; 27 8x8 blocks
+// of the symmetrised ovov, 9 t1 rows and 3 eps_v rows come by TMA.  Warp 0
+// issues the loads two items ahead into a double buffer; one thread per
+// orbit candidate (a,b,c) of the 8^3 block triple.  G is either FP32 (BF16X3/TF32/TF32X3) or an FP32 pair
 // hi + lo (OZAKI), CW = 1 or 2 floats per element.
 //
 // Orbit sum without cancellation: the 6x6 coefficient matrix C of R between
@@ -24,7 +26,8 @@ namespace te {
 namespace {
 
 constexpr int TB = 8;
-constexpr int THREADS = 256;
+constexpr int WARPS = 16;                 // compute warps: one orbit candidate (a,b,c) of 8^3 per thread
+constexpr int THREADS = (WARPS + 1) * 32;  // + one producer warp
 
 __constant__ int c_perm_tc[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
@@ -100,9 +103,9 @@ __device__ __forceinline__ df df_scale(df a, float k) {  // k a small integer
 template <int CW>
 __device__ __forceinline__ void gval(const float* cube, int g, int pid, int x, int y, int z, float& hi,
                                      float& lo) {
-  const float* p = cube + (((g * 6 + pid) * TB + x) * TB + y) * TB * CW + z * CW;
+  const float* p = cube + (g * 6 + pid) * (TB * TB * TB * CW) + cube_off(x, y, z);
   hi = p[0];
-  lo = (CW == 2) ? p[1] : 0.f;
+  lo = (CW == 2) ? p[TB * TB * TB] : 0.f;
 }
 
 // deviation of W~ at position N from position 0, and Y at position N
@@ -160,15 +163,15 @@ __device__ __forceinline__ float y_at(const float* ovsS, const float* t1S, const
 }
 
 struct EnergyMaps {
-  CUtensorMap g;    // G buffer, 5D (z*CW, y, x, g, slot)
   CUtensorMap ovs;  // ovs32 [o][v][o][vq], 4D (b, j, a, i)
   CUtensorMap t1;   // t1 [o][vq], 2D (a, i)
   CUtensorMap eps;  // eps_v copy, 1D FP64
 };
 
 struct EnergyParams {
-  int o, v, nslots;
+  int o, v, nslots, nb;
   int64_t nbt, items, t0;
+  const float* gbuf;  // cube-major G blocks: [slot][g][X][Y][Z][CW planes][512, swizzled]
   const Triple* triples;
   const double* eps_o;
   double* partials;
@@ -182,107 +185,141 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                                          ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * L::buf);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(full + 2);
-  int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][4]: X, Y, Z per buffer
-  __shared__ double red[THREADS / 32];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * L::buf);  // [2]
+  uint64_t* empty = full + 2;                                         // [2], one arrival per compute warp
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + 2);
+  int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][4]: X, Y, Z
+  double* meta_eo = reinterpret_cast<double*>(empty + 8);                        // [2]: e_i + e_j + e_k
+  double* red = meta_eo + 2;                                                      // [2][WARPS]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    ptx::mbar_init(&full[0], 1);
-    ptx::mbar_init(&full[1], 1);
+    for (int q = 0; q < 2; ++q) {
+      ptx::mbar_init(&full[q], 1);
+      ptx::mbar_init(&empty[q], WARPS);
+    }
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
   __syncthreads();
 
-  // issue the loads of item `it` into buffer `b` (warp 0, all lanes)
-  auto issue = [&](int64_t it, int b) {
-    const int slot = (int)(it / P.nbt);
-    const int64_t bt = it % P.nbt;
-    int blk[3];
-    decode_bt(bt, blk);
-    const Triple tr = P.triples[P.t0 + slot];
-    unsigned char* base = smem + (size_t)b * L::buf;
-    if (lane == 0) {
-      meta[b * 4 + 0] = blk[0];
-      meta[b * 4 + 1] = blk[1];
-      meta[b * 4 + 2] = blk[2];
-      ptx::mbar_arrive_expect_tx(&full[b], L::tx);
-    }
-    __syncwarp();
-    for (int q = lane; q < 57; q += 32) {
-      if (q < 18) {
-        const int g = q / 6, pid = q % 6;
-        ptx::tma_load_5d(base + q * L::cube_bytes, &M.g, &full[b], blk[c_perm_tc[pid][2]] * TB * CW,
-                         blk[c_perm_tc[pid][1]] * TB, blk[c_perm_tc[pid][0]] * TB, g, slot);
-      } else if (q < 45) {
-        const int r = q - 18, pair = r / 9, sx = (r / 3) % 3, sy = r % 3;
-        const int P1 = (pair == 1) ? tr.j : tr.i;
-        const int P2 = (pair == 0) ? tr.j : tr.k;
-        ptx::tma_load_4d(base + L::cubes + r * 256, &M.ovs, &full[b], blk[sy] * TB, P2, blk[sx] * TB, P1);
-      } else if (q < 54) {
-        const int r = q - 45, which = r / 3, s = r % 3;
-        const int occ = which == 0 ? tr.i : (which == 1 ? tr.j : tr.k);
-        ptx::tma_load_2d(base + L::cubes + L::ovs + r * 128, &M.t1, &full[b], blk[s] * TB, occ);
-      } else {
-        const int s = q - 54;
-        ptx::tma_load_1d(base + L::cubes + L::ovs + L::t1 + s * 128, &M.eps, &full[b], blk[s] * TB);
+  if (warp == WARPS) {
+    // ---------------- producer warp ----------------
+    uint32_t ephase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    uint32_t fphase[2] = {0u, 0u};
+    int64_t done_item[2] = {-1, -1};  // item whose partial sits in red[b]
+    int b = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; ok && it < P.items; it += gridDim.x, b ^= 1) {
+      // buffer b free: all compute warps done with the item it held
+      int good = 1;
+      if (lane == 0) good = ptx::mbar_wait(&empty[b], ephase[b] ^ 1u, P.wait_ns) ? 1 : 0;
+      good = __shfl_sync(0xffffffffu, good, 0);
+      if (!good || *abort_flag) {
+        if (lane == 0 && !*abort_flag) {
+          *abort_flag = 1;
+          if (atomicOr(P.err, ERR_WAIT_TIMEOUT) == 0) {
+            P.err[1] = 11;
+            P.err[2] = blockIdx.x;
+          }
+        }
+        ok = false;
+        break;
       }
-    }
-  };
-
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  int64_t it = blockIdx.x;
-  if (warp == 0 && it < P.items) {
-    issue(it, 0);
-    pending[0] = true;
-  }
-  int b = 0;
-  for (; it < P.items; it += gridDim.x, b ^= 1) {
-    const int64_t nxt = it + gridDim.x;
-    if (warp == 0 && nxt < P.items && !*abort_flag) {
-      issue(nxt, b ^ 1);
-      pending[b ^ 1] = true;
-    }
-    // every thread observes the phase completion
-    const bool ok = ptx::mbar_wait(&full[b], phase[b], P.wait_ns);
-    if (!__syncthreads_and(ok ? 1 : 0)) {
-      if (tid == 0) {
-        *abort_flag = 1;
-        if (atomicOr(P.err, ERR_WAIT_TIMEOUT) == 0) {
-          P.err[1] = 10;
-          P.err[2] = blockIdx.x;
+      ephase[b] ^= 1u;
+      if (lane == 0 && done_item[b] >= 0) {  // fixed-order sum of the finished item's warp partials
+        double sum = 0.0;
+        for (int w = 0; w < WARPS; ++w) sum += red[b * WARPS + w];
+        P.partials[done_item[b]] = sum;
+      }
+      const int slot = (int)(it / P.nbt);
+      const int64_t bt = it % P.nbt;
+      int blk[3];
+      decode_bt(bt, blk);
+      const Triple tr = P.triples[P.t0 + slot];
+      unsigned char* base = smem + (size_t)b * L::buf;
+      if (lane == 0) {
+        meta[b * 4 + 0] = blk[0];
+        meta[b * 4 + 1] = blk[1];
+        meta[b * 4 + 2] = blk[2];
+        meta_eo[b] = P.eps_o[tr.i] + P.eps_o[tr.j] + P.eps_o[tr.k];
+        ptx::mbar_arrive_expect_tx(&full[b], L::tx);
+        pending[b] = true;
+      }
+      __syncwarp();
+      for (int q = lane; q < 57; q += 32) {
+        if (q < 18) {
+          const int g = q / 6, pid = q % 6;
+          const int64_t cube_idx =
+              (((int64_t)slot * 3 + g) * P.nb + blk[c_perm_tc[pid][0]]) * P.nb * P.nb +
+              (int64_t)blk[c_perm_tc[pid][1]] * P.nb + blk[c_perm_tc[pid][2]];
+          ptx::bulk_load(base + q * L::cube_bytes, P.gbuf + cube_idx * (TB * TB * TB * CW), L::cube_bytes,
+                         &full[b]);
+        } else if (q < 45) {
+          const int r = q - 18, pair = r / 9, sx = (r / 3) % 3, sy = r % 3;
+          const int P1 = (pair == 1) ? tr.j : tr.i;
+          const int P2 = (pair == 0) ? tr.j : tr.k;
+          ptx::tma_load_4d(base + L::cubes + r * 256, &M.ovs, &full[b], blk[sy] * TB, P2, blk[sx] * TB, P1);
+        } else if (q < 54) {
+          const int r = q - 45, which = r / 3, s2 = r % 3;
+          const int occ = which == 0 ? tr.i : (which == 1 ? tr.j : tr.k);
+          ptx::tma_load_2d(base + L::cubes + L::ovs + r * 128, &M.t1, &full[b], blk[s2] * TB, occ);
+        } else {
+          const int s2 = q - 54;
+          ptx::tma_load_1d(base + L::cubes + L::ovs + L::t1 + s2 * 128, &M.eps, &full[b], blk[s2] * TB);
         }
       }
-      break;
+      done_item[b] = (int64_t)slot * P.nbt + bt;
+      fphase[b] ^= 1u;
     }
-    pending[b] = false;
-    phase[b] ^= 1u;
+    // partials of the last items once their warps are done; copies in flight land
+    for (int q = 0; q < 2; ++q) {
+      if (done_item[q] < 0 || !ok) continue;
+      int good = 1;
+      if (lane == 0) good = ptx::mbar_wait(&empty[q], ephase[q] ^ 1u, P.wait_ns) ? 1 : 0;
+      good = __shfl_sync(0xffffffffu, good, 0);
+      if (good && lane == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < WARPS; ++w) sum += red[q * WARPS + w];
+        P.partials[done_item[q]] = sum;
+      }
+    }
+    if (lane == 0)
+      for (int q = 0; q < 2; ++q)
+        if (pending[q] && !ok) ptx::mbar_wait(&full[q], fphase[q] ^ 1u, P.wait_ns);
+  } else {
+    // ---------------- compute warps ----------------
+    uint32_t phase[2] = {0u, 0u};
+    int b = 0;
+    const int la = tid >> 6, lb = (tid >> 3) & 7, lc = tid & 7;
+    for (int64_t it = blockIdx.x; it < P.items; it += gridDim.x, b ^= 1) {
+      int got = 0;
+      if (!*abort_flag) got = ptx::mbar_wait(&full[b], phase[b], P.wait_ns) ? 1 : 0;
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0 && !*abort_flag) {
+          *abort_flag = 1;
+          if (atomicOr(P.err, ERR_WAIT_TIMEOUT) == 0) {
+            P.err[1] = 10;
+            P.err[2] = blockIdx.x;
+          }
+        }
+        break;
+      }
+      phase[b] ^= 1u;
+      const int blk[3] = {meta[b * 4 + 0], meta[b * 4 + 1], meta[b * 4 + 2]};
+      const double eo = meta_eo[b];
+      const unsigned char* base = smem + (size_t)b * L::buf;
+      const float* cube = reinterpret_cast<const float*>(base);
+      const float* ovsS = reinterpret_cast<const float*>(base + L::cubes);
+      const float* t1S = reinterpret_cast<const float*>(base + L::cubes + L::ovs);
+      const double* epsS = reinterpret_cast<const double*>(base + L::cubes + L::ovs + L::t1);
 
-    const int slot = (int)(it / P.nbt);
-    const int64_t bt = it % P.nbt;
-    const int blk[3] = {meta[b * 4 + 0], meta[b * 4 + 1], meta[b * 4 + 2]};
-    const Triple tr = P.triples[P.t0 + slot];
-    const unsigned char* base = smem + (size_t)b * L::buf;
-    const float* cube = reinterpret_cast<const float*>(base);
-    const float* ovsS = reinterpret_cast<const float*>(base + L::cubes);
-    const float* t1S = reinterpret_cast<const float*>(base + L::cubes + L::ovs);
-    const double* epsS = reinterpret_cast<const double*>(base + L::cubes + L::ovs + L::t1);
-
-    const double eo = P.eps_o[tr.i] + P.eps_o[tr.j] + P.eps_o[tr.k];
-    const int pr = tid >> 2, la = pr >> 3, lb = pr & 7;
-    const int a = blk[0] * TB + la, bb = blk[1] * TB + lb;
-    double acc = 0.0;
-    const bool ab_ok = a < P.v && bb < P.v && !(blk[0] == blk[1] && la < lb);
-    if (ab_ok) {
-      const double dab = eo - epsS[la] - epsS[16 + lb];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int lc = (tid & 3) + 4 * h;
-        const int c = blk[2] * TB + lc;
-        if (c >= P.v || (blk[1] == blk[2] && lb < lc)) continue;
+      const int a = blk[0] * TB + la, bb = blk[1] * TB + lb, c = blk[2] * TB + lc;
+      double acc = 0.0;
+      const bool valid = a < P.v && bb < P.v && c < P.v && !(blk[0] == blk[1] && la < lb) &&
+                         !(blk[1] == blk[2] && lb < lc);
+      if (valid) {
         const int l[3] = {la, lb, lc};
         double Td;
         if constexpr (CW == 2) {
@@ -316,27 +353,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
           const float dot = w1 * v1 + w2 * v2 + w3 * v3 + w4 * v4 + w5 * v5;
           Td = (double)(3.f * dot + Ae * Se + Ao * So - 2.f * (Ae * So + Ao * Se));
         }
-        const double D = dab - epsS[32 + lc];
+        const double D = eo - epsS[la] - epsS[16 + lb] - epsS[32 + lc];
         const double r0 = (double)__frcp_rn((float)D);
         const double r1 = fma(r0, fma(-D, r0, 1.0), r0);
         const double wA = (a == bb && bb == c) ? (1.0 / 6.0) : ((a == bb || bb == c) ? 0.5 : 1.0);
-        acc = fma(wA * Td, r1, acc);
+        acc = (wA * Td) * r1;
       }
+      // fixed-order warp reduction; the producer sums the 16 warp partials in order
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) {
+        red[b * WARPS + warp] = acc;
+        ptx::mbar_arrive(&empty[b]);  // release: red[] and the buffer reads happen before
+      }
+      __syncwarp();
     }
-    // fixed-order block reduction -> one partial per item
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();  // also frees buffer b for the issue two items ahead
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < THREADS / 32; ++w) s += red[w];
-      P.partials[(int64_t)slot * P.nbt + bt] = s;
-    }
-  }
-  // loads still in flight land before the CTA exits
-  if (tid == 0) {
-    for (int q = 0; q < 2; ++q)
-      if (pending[q]) ptx::mbar_wait(&full[q], phase[q], P.wait_ns);
   }
   __syncthreads();
 }
@@ -345,12 +375,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
 
 size_t energy_tc_smem(int cw) {
   const size_t buf = cw == 2 ? Layout<2>::buf : Layout<1>::buf;
-  return 2 * buf + 128 + 128;
+  return 2 * buf + 128 + 512;
 }
 
 cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   EnergyMaps M;
-  M.g = *e.map_g;
   M.ovs = *e.map_ovs;
   M.t1 = *e.map_t1;
   M.eps = *e.map_eps;
@@ -358,6 +387,8 @@ cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   P.o = e.o;
   P.v = e.v;
   P.nslots = e.nslots;
+  P.nb = (e.v + TB - 1) / TB;
+  P.gbuf = e.gbuf;
   P.nbt = e.nbt;
   P.items = (int64_t)e.nslots * e.nbt;
   P.t0 = e.t0;
@@ -367,7 +398,7 @@ cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   P.err = e.err;
   P.wait_ns = e.wait_ns;
   const size_t smem = energy_tc_smem(e.cw);
-  const int64_t grid = std::min<int64_t>(P.items, (int64_t)e.num_sms * (e.cw == 2 ? 1 : 2));
+  const int64_t grid = std::min<int64_t>(P.items, (int64_t)e.num_sms);
   cudaError_t err;
   if (e.cw == 2) {
     err = cudaFuncSetAttribute(k_energy_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

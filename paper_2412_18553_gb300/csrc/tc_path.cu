@@ -297,6 +297,30 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& P, int64_t tt) 
   return c;
 }
 
+// out[k] = v[k ^ h] for k < 8 (three conditional swap stages, no dynamic indexing)
+__device__ __forceinline__ void xor_permute8(float* v, int h) {
+  if (h & 1) {
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) { const float t = v[k]; v[k] = v[k + 1]; v[k + 1] = t; }
+  }
+  if (h & 2) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if ((k & 2) == 0) { const float t = v[k]; v[k] = v[k + 2]; v[k + 2] = t; }
+  }
+  if (h & 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { const float t = v[k]; v[k] = v[k + 4]; v[k + 4] = t; }
+  }
+}
+
+__device__ __forceinline__ void store8(float* dst, float* v, int h) {
+  xor_permute8(v, h);
+  float4* o4 = reinterpret_cast<float4*>(dst);
+  o4[0] = make_float4(v[0], v[1], v[2], v[3]);
+  o4[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
 // Knuth's two-sum: s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -517,41 +541,50 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
       const int x = c.x0 + row / P.TB;
       const int y = c.y0 + row % P.TB;
       const bool valid = x < P.v && y < P.v;
-      const int64_t orow = ((int64_t)(c.slot * 3 + c.g) * v2 + (int64_t)x * P.v + y) * P.ldz;
+      // cube-major G: [slot][g][X][Y][Z][CW planes][512], swizzled rows (see energy_tc.h);
+      // this row is (x, y) = (X*8 + xl, Y*8 + yl)
+      const int nb = (P.v + 7) >> 3;
+      constexpr int CWF = (MODE == TC_OZAKI) ? 2 : 1;
+      const int64_t cubebase = (((int64_t)(c.slot * 3 + c.g) * nb + (x >> 3)) * nb + (y >> 3)) * nb;
+      const int roff = cube_row(x & 7, y & 7);
+      const int zx = cube_zx(x & 7, y & 7);
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)(NACC * P.NT);
       for (int c0 = 0; c0 < P.NT; c0 += 16) {
-        const int z = c.z0 + c0;
+        const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
         if constexpr (MODE == TC_OZAKI) {
           float a2[16], a3[16], ar[16];
           ptx::tmem_ld16(tbase + c0, a2);
           ptx::tmem_ld16(tbase + P.NT + c0, a3);
           ptx::tmem_ld16(tbase + 2 * P.NT + c0, ar);
           if (valid) {
-            float2* out = reinterpret_cast<float2*>(P.gbuf) + orow;
+            float hv[16], lv[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               float s, e;
               two_sum(a2[j], a3[j], s, e);
               const float lo = __fadd_rn(e, ar[j]);
               const float hi = __fadd_rn(s, lo);
-              const float lo2 = __fsub_rn(lo, __fsub_rn(hi, s));
-              if (z + j < P.v) out[z + j] = make_float2(hi * gscale, lo2 * gscale);
+              hv[j] = hi * gscale;
+              lv[j] = __fsub_rn(lo, __fsub_rn(hi, s)) * gscale;
+            }
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int Z = (z >> 3) + h2;
+              if (Z < nb) {
+                float* cube = P.gbuf + (cubebase + Z) * (512 * CWF);
+                store8(cube + roff, hv + 8 * h2, zx);
+                store8(cube + 512 + roff, lv + 8 * h2, zx);
+              }
             }
           }
         } else {
           float vals[16];
           ptx::tmem_ld16(tbase + c0, vals);
           if (valid) {
-            float* out = P.gbuf + orow;
-            if (z + 16 <= P.ldz) {
-              float4* o4 = reinterpret_cast<float4*>(out + z);
 #pragma unroll
-              for (int q4 = 0; q4 < 4; ++q4)
-                o4[q4] = make_float4(vals[4 * q4], vals[4 * q4 + 1], vals[4 * q4 + 2], vals[4 * q4 + 3]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if (z + j < P.v) out[z + j] = vals[j];
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int Z = (z >> 3) + h2;
+              if (Z < nb) store8(P.gbuf + (cubebase + Z) * 512 + roff, vals + 8 * h2, zx);
             }
           }
         }
@@ -669,8 +702,10 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri) {
   pl.ldz = round_up(v, 4);
   const int64_t tiles = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
   int64_t want = (4LL * std::max(1, h->num_sms) + tiles - 1) / tiles;
-  const int64_t per_slot = 3LL * v * v * pl.ldz * 4 * pl.cw;
+  const int64_t nbk = (v + 7) / 8;
+  const int64_t per_slot = 3LL * nbk * nbk * nbk * 512 * 4 * pl.cw;
   const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(3LL << 30) / per_slot);
+  want = std::max<int64_t>(want, 4);  // fewer launches per cluster
   want = std::min<int64_t>({want, mem_cap, 1024, std::max<int64_t>(1, ntri)});
   pl.nslots = (int)std::max<int64_t>(1, want);
   return pl;
@@ -706,7 +741,8 @@ static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64
   b->ovs32 = static_cast<float*>(take((size_t)o * v * o * pl.vq * 4));
   b->t1_32 = static_cast<float*>(take((size_t)o * pl.vq * 4));
   b->eps_copy = static_cast<double*>(take((size_t)v * 8));
-  b->gbuf = static_cast<float*>(take((size_t)pl.nslots * 3 * v * v * pl.ldz * 4 * pl.cw));
+  const size_t nbk = (size_t)((v + 7) / 8);
+  b->gbuf = static_cast<float*>(take((size_t)pl.nslots * 3 * nbk * nbk * nbk * 512 * 4 * pl.cw));
   b->partials = static_cast<double*>(take((size_t)pl.nslots * nbt * 8));
   b->etri = static_cast<double*>(take((size_t)std::max<int64_t>(1, ntri) * 8));
   b->maxbits = static_cast<unsigned long long*>(take(4 * 8));
@@ -778,7 +814,7 @@ static te_status build_maps(TcState* st, const TcPlan& pl, int o, int v, const T
 }
 
 struct EnergyMapsHost {
-  CUtensorMap g, ovs, t1, eps;
+  CUtensorMap ovs, t1, eps;
 };
 
 static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, int nslots, const TcBuffers& b,
@@ -786,14 +822,6 @@ static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, 
   std::memset(E, 0, sizeof(*E));
   const uint64_t V = v, O = o, cw = pl.cw, ldz = pl.ldz, vq = pl.vq;
   te_status s;
-  {  // G [slot][g][x][y][ldz*cw] floats: dims (z*cw, y, x, g, slot)
-    const uint64_t d[5] = {V * cw, V, V, 3, (uint64_t)nslots};
-    const uint64_t sn[4] = {ldz * cw * 4, V * ldz * cw * 4, V * V * ldz * cw * 4, 3 * V * V * ldz * cw * 4};
-    const uint32_t box[5] = {(uint32_t)(8 * cw), 8, 8, 1, 1};
-    if ((s = encode(st, &E->g, b.gbuf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, d, sn, box,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, "G")) != TE_OK)
-      return s;
-  }
   {  // ovs32 [i][a][j][vq]: dims (b, j, a, i)
     const uint64_t d[4] = {V, O, V, O};
     const uint64_t sn[3] = {vq * 4, O * vq * 4, V * O * vq * 4};
@@ -939,7 +967,7 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   EL.cw = pl.cw;
   EL.num_sms = h->num_sms;
   EL.nbt = nbt;
-  EL.map_g = &EM.g;
+  EL.gbuf = b.gbuf;
   EL.map_ovs = &EM.ovs;
   EL.map_t1 = &EM.t1;
   EL.map_eps = &EM.eps;

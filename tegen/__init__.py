@@ -186,4 +186,7 @@ WORKLOADS = {
     "o32v320": (32, 320, 1280, 1),
     "o16v120": (16, 120, 544, 3),
     "o48v560": (48, 560, 2432, 7),
+    # same virtual space as o32v320 with 8 occupied orbitals: kernel profiling
+    # at full tile shapes with a few GB on the device
+    "o8v320": (8, 320, 1280, 1),
 }
