@@ -46,9 +46,9 @@ struct Layout {
   static constexpr uint32_t cubes = 18 * cube_bytes;
   static constexpr uint32_t ovs = 27 * TB * TB * 4;
   static constexpr uint32_t t1 = 9 * 128;
-  static constexpr uint32_t eps = 3 * 128;
+  static constexpr uint32_t eps = 640;  // dAB[64] = e_ijk - e_a - e_b, epsC[8] (FP64, written by the producer)
   static constexpr uint32_t buf = cubes + ovs + t1 + eps;
-  static constexpr uint32_t tx = 18 * cube_bytes + 27 * TB * TB * 4 + 9 * TB * 4 + 3 * TB * 8;
+  static constexpr uint32_t tx = 18 * cube_bytes + 27 * TB * TB * 4 + 9 * TB * 4;
 };
 
 __device__ __forceinline__ void decode_bt(int64_t bt, int* blk) {
@@ -108,25 +108,30 @@ __device__ __forceinline__ void gval(const float* cube, int g, int pid, int x, i
   lo = (CW == 2) ? p[TB * TB * TB] : 0.f;
 }
 
+template <int S>
+__device__ __forceinline__ int pick(int la, int lb, int lc) {
+  return S == 0 ? la : (S == 1 ? lb : lc);
+}
+
 // deviation of W~ at position N from position 0, and Y at position N
 template <int CW, int N>
-__device__ __forceinline__ float w_dev(const float* cube, const int* l) {
+__device__ __forceinline__ float w_dev(const float* cube, int la, int lb, int lc) {
   constexpr int s0 = Pos<N>::s0, s1 = Pos<N>::s1, s2 = Pos<N>::s2;
-  const int x = l[s0], y = l[s1], z = l[s2];
+  const int x = pick<s0>(la, lb, lc), y = pick<s1>(la, lb, lc), z = pick<s2>(la, lb, lc);
   float h0, l0, hn, ln, d = 0.f, dl = 0.f;
   // G0[x][y][z] at cube N, minus G0[a][b][c] at cube 0
   gval<CW>(cube, 0, N, x, y, z, hn, ln);
-  gval<CW>(cube, 0, 0, l[0], l[1], l[2], h0, l0);
+  gval<CW>(cube, 0, 0, la, lb, lc, h0, l0);
   d += hn - h0;
   dl += ln - l0;
   // G1[y][z][x] at cube r1(N), minus G1[b][c][a] at cube 3
   gval<CW>(cube, 1, Pos<N>::r1, y, z, x, hn, ln);
-  gval<CW>(cube, 1, 3, l[1], l[2], l[0], h0, l0);
+  gval<CW>(cube, 1, 3, lb, lc, la, h0, l0);
   d += hn - h0;
   dl += ln - l0;
   // G2[z][x][y] at cube r2(N), minus G2[c][a][b] at cube 4
   gval<CW>(cube, 2, Pos<N>::r2, z, x, y, hn, ln);
-  gval<CW>(cube, 2, 4, l[2], l[0], l[1], h0, l0);
+  gval<CW>(cube, 2, 4, lc, la, lb, h0, l0);
   d += hn - h0;
   dl += ln - l0;
   return d + dl;
@@ -134,29 +139,29 @@ __device__ __forceinline__ float w_dev(const float* cube, const int* l) {
 
 // double-float deviation of W~ at position N from position 0 (CW = 2)
 template <int N>
-__device__ __forceinline__ df w_dev_df(const float* cube, const int* l) {
+__device__ __forceinline__ df w_dev_df(const float* cube, int la, int lb, int lc) {
   constexpr int s0 = Pos<N>::s0, s1 = Pos<N>::s1, s2 = Pos<N>::s2;
-  const int x = l[s0], y = l[s1], z = l[s2];
+  const int x = pick<s0>(la, lb, lc), y = pick<s1>(la, lb, lc), z = pick<s2>(la, lb, lc);
   float h0, l0, hn, ln;
   gval<2>(cube, 0, N, x, y, z, hn, ln);
-  gval<2>(cube, 0, 0, l[0], l[1], l[2], h0, l0);
+  gval<2>(cube, 0, 0, la, lb, lc, h0, l0);
   df acc = df_two_sum(hn, -h0);
   float lsum = __fsub_rn(ln, l0);
   gval<2>(cube, 1, Pos<N>::r1, y, z, x, hn, ln);
-  gval<2>(cube, 1, 3, l[1], l[2], l[0], h0, l0);
+  gval<2>(cube, 1, 3, lb, lc, la, h0, l0);
   acc = df_add(acc, df_two_sum(hn, -h0));
   lsum = __fadd_rn(lsum, __fsub_rn(ln, l0));
   gval<2>(cube, 2, Pos<N>::r2, z, x, y, hn, ln);
-  gval<2>(cube, 2, 4, l[2], l[0], l[1], h0, l0);
+  gval<2>(cube, 2, 4, lc, la, lb, h0, l0);
   acc = df_add(acc, df_two_sum(hn, -h0));
   lsum = __fadd_rn(lsum, __fsub_rn(ln, l0));
   return df_add(acc, df{lsum, 0.f});
 }
 
 template <int N>
-__device__ __forceinline__ float y_at(const float* ovsS, const float* t1S, const int* l) {
+__device__ __forceinline__ float y_at(const float* ovsS, const float* t1S, int la, int lb, int lc) {
   constexpr int s0 = Pos<N>::s0, s1 = Pos<N>::s1, s2 = Pos<N>::s2;
-  const int x = l[s0], y = l[s1], z = l[s2];
+  const int x = pick<s0>(la, lb, lc), y = pick<s1>(la, lb, lc), z = pick<s2>(la, lb, lc);
   return ovsS[((0 * 3 + s0) * 3 + s1) * 64 + x * 8 + y] * t1S[(2 * 3 + s2) * 32 + z] +
          ovsS[((1 * 3 + s1) * 3 + s2) * 64 + y * 8 + z] * t1S[(0 * 3 + s0) * 32 + x] +
          ovsS[((2 * 3 + s0) * 3 + s2) * 64 + x * 8 + z] * t1S[(1 * 3 + s1) * 32 + y];
@@ -165,7 +170,6 @@ __device__ __forceinline__ float y_at(const float* ovsS, const float* t1S, const
 struct EnergyMaps {
   CUtensorMap ovs;  // ovs32 [o][v][o][vq], 4D (b, j, a, i)
   CUtensorMap t1;   // t1 [o][vq], 2D (a, i)
-  CUtensorMap eps;  // eps_v copy, 1D FP64
 };
 
 struct EnergyParams {
@@ -174,7 +178,8 @@ struct EnergyParams {
   const float* gbuf;  // cube-major G blocks: [slot][g][X][Y][Z][CW planes][512, swizzled]
   const Triple* triples;
   const double* eps_o;
-  double* partials;
+  const double* eps_v;
+  double* partials;  // [slot][grid][WARPS]
   unsigned int* err;
   unsigned long long wait_ns;
 };
@@ -188,33 +193,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * L::buf);  // [2]
   uint64_t* empty = full + 2;                                         // [2], one arrival per compute warp
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + 2);
-  int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][4]: X, Y, Z
-  double* meta_eo = reinterpret_cast<double*>(empty + 8);                        // [2]: e_i + e_j + e_k
-  double* red = meta_eo + 2;                                                      // [2][WARPS]
+  int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][4]: X, Y, Z, slot
+  double* eps_s = reinterpret_cast<double*>(empty + 16);                          // eps_v[v], then eps_o[o]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int q = 0; q < 2; ++q) {
-      ptx::mbar_init(&full[q], 1);
+      ptx::mbar_init(&full[q], 2);  // the copies' arrive.expect_tx and the denominator table's arrive
       ptx::mbar_init(&empty[q], WARPS);
     }
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
+  for (int q = tid; q < P.v + P.o; q += THREADS) eps_s[q] = q < P.v ? P.eps_v[q] : P.eps_o[q - P.v];
   __syncthreads();
 
   if (warp == WARPS) {
     // ---------------- producer warp ----------------
-    uint32_t ephase[2] = {0u, 0u};
-    bool pending[2] = {false, false};
-    uint32_t fphase[2] = {0u, 0u};
-    int64_t done_item[2] = {-1, -1};  // item whose partial sits in red[b]
+    uint32_t ephase = 0u, pending = 0u, fphase = 0u;  // one bit per buffer
     int b = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; ok && it < P.items; it += gridDim.x, b ^= 1) {
       // buffer b free: all compute warps done with the item it held
       int good = 1;
-      if (lane == 0) good = ptx::mbar_wait(&empty[b], ephase[b] ^ 1u, P.wait_ns) ? 1 : 0;
+      if (lane == 0) good = ptx::mbar_wait(&empty[b], ((ephase >> b) & 1u) ^ 1u, P.wait_ns) ? 1 : 0;
       good = __shfl_sync(0xffffffffu, good, 0);
       if (!good || *abort_flag) {
         if (lane == 0 && !*abort_flag) {
@@ -227,12 +229,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
         ok = false;
         break;
       }
-      ephase[b] ^= 1u;
-      if (lane == 0 && done_item[b] >= 0) {  // fixed-order sum of the finished item's warp partials
-        double sum = 0.0;
-        for (int w = 0; w < WARPS; ++w) sum += red[b * WARPS + w];
-        P.partials[done_item[b]] = sum;
-      }
+      ephase ^= 1u << b;
       const int slot = (int)(it / P.nbt);
       const int64_t bt = it % P.nbt;
       int blk[3];
@@ -243,12 +240,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
         meta[b * 4 + 0] = blk[0];
         meta[b * 4 + 1] = blk[1];
         meta[b * 4 + 2] = blk[2];
-        meta_eo[b] = P.eps_o[tr.i] + P.eps_o[tr.j] + P.eps_o[tr.k];
-        ptx::mbar_arrive_expect_tx(&full[b], L::tx);
-        pending[b] = true;
+        meta[b * 4 + 3] = slot;
+        ptx::mbar_arrive_expect_tx(&full[b], L::tx);  // first of the two arrivals
+        pending |= 1u << b;
       }
       __syncwarp();
-      for (int q = lane; q < 57; q += 32) {
+      for (int q = lane; q < 54; q += 32) {
         if (q < 18) {
           const int g = q / 6, pid = q % 6;
           const int64_t cube_idx =
@@ -261,41 +258,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
           const int P1 = (pair == 1) ? tr.j : tr.i;
           const int P2 = (pair == 0) ? tr.j : tr.k;
           ptx::tma_load_4d(base + L::cubes + r * 256, &M.ovs, &full[b], blk[sy] * TB, P2, blk[sx] * TB, P1);
-        } else if (q < 54) {
+        } else {
           const int r = q - 45, which = r / 3, s2 = r % 3;
           const int occ = which == 0 ? tr.i : (which == 1 ? tr.j : tr.k);
           ptx::tma_load_2d(base + L::cubes + L::ovs + r * 128, &M.t1, &full[b], blk[s2] * TB, occ);
-        } else {
-          const int s2 = q - 54;
-          ptx::tma_load_1d(base + L::cubes + L::ovs + L::t1 + s2 * 128, &M.eps, &full[b], blk[s2] * TB);
         }
       }
-      done_item[b] = (int64_t)slot * P.nbt + bt;
-      fphase[b] ^= 1u;
+      {  // FP64 denominator pieces while the copies fly: dAB[la][lb] = e_i+e_j+e_k - e_a - e_b, epsC[lc] = e_c
+        double* dAB = reinterpret_cast<double*>(base + L::cubes + L::ovs + L::t1);
+        const double eo = eps_s[P.v + tr.i] + eps_s[P.v + tr.j] + eps_s[P.v + tr.k];
+        for (int q = lane; q < 72; q += 32) {
+          if (q < 64) {
+            const int qa = blk[0] * TB + (q >> 3), qb = blk[1] * TB + (q & 7);
+            dAB[q] = (qa < P.v && qb < P.v) ? (eo - eps_s[qa]) - eps_s[qb] : 0.0;
+          } else {
+            const int qc = blk[2] * TB + (q - 64);
+            dAB[q] = qc < P.v ? eps_s[qc] : 0.0;
+          }
+        }
+      }
+      __syncwarp();  // every lane's dAB stores are ordered before lane 0's release
+      if (lane == 0) ptx::mbar_arrive(&full[b]);  // second arrival
+      fphase ^= 1u << b;
     }
     // partials of the last items once their warps are done; copies in flight land
-    for (int q = 0; q < 2; ++q) {
-      if (done_item[q] < 0 || !ok) continue;
-      int good = 1;
-      if (lane == 0) good = ptx::mbar_wait(&empty[q], ephase[q] ^ 1u, P.wait_ns) ? 1 : 0;
-      good = __shfl_sync(0xffffffffu, good, 0);
-      if (good && lane == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < WARPS; ++w) sum += red[q * WARPS + w];
-        P.partials[done_item[q]] = sum;
-      }
-    }
     if (lane == 0)
       for (int q = 0; q < 2; ++q)
-        if (pending[q] && !ok) ptx::mbar_wait(&full[q], fphase[q] ^ 1u, P.wait_ns);
+        if (((pending >> q) & 1u) && !ok) ptx::mbar_wait(&full[q], ((fphase >> q) & 1u) ^ 1u, P.wait_ns);
   } else {
     // ---------------- compute warps ----------------
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase = 0u;  // one bit per buffer
     int b = 0;
-    const int la = tid >> 6, lb = (tid >> 3) & 7, lc = tid & 7;
+    const int la = (tid >> 6), lb = (tid >> 3) & 7, lc = tid & 7;
+    double acc = 0.0;  // this thread's sum over the items of the current triple slot
+    int cur_slot = -1;
     for (int64_t it = blockIdx.x; it < P.items; it += gridDim.x, b ^= 1) {
       int got = 0;
-      if (!*abort_flag) got = ptx::mbar_wait(&full[b], phase[b], P.wait_ns) ? 1 : 0;
+      if (!*abort_flag) got = ptx::mbar_wait(&full[b], (phase >> b) & 1u, P.wait_ns) ? 1 : 0;
       if (!__all_sync(0xffffffffu, got)) {
         if (lane == 0 && !*abort_flag) {
           *abort_flag = 1;
@@ -304,33 +303,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
             P.err[2] = blockIdx.x;
           }
         }
+        cur_slot = -1;
         break;
       }
-      phase[b] ^= 1u;
-      const int blk[3] = {meta[b * 4 + 0], meta[b * 4 + 1], meta[b * 4 + 2]};
-      const double eo = meta_eo[b];
+      phase ^= 1u << b;
+      const int bx = meta[b * 4 + 0], by = meta[b * 4 + 1], bz = meta[b * 4 + 2], slot = meta[b * 4 + 3];
+      if (slot != cur_slot) {
+        if (cur_slot >= 0) {  // fixed-order warp reduction of the finished slot
+          for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+          if (lane == 0) P.partials[((int64_t)cur_slot * gridDim.x + blockIdx.x) * WARPS + warp] = acc;
+        }
+        acc = 0.0;
+        cur_slot = slot;
+      }
       const unsigned char* base = smem + (size_t)b * L::buf;
       const float* cube = reinterpret_cast<const float*>(base);
       const float* ovsS = reinterpret_cast<const float*>(base + L::cubes);
       const float* t1S = reinterpret_cast<const float*>(base + L::cubes + L::ovs);
-      const double* epsS = reinterpret_cast<const double*>(base + L::cubes + L::ovs + L::t1);
+      const double* dAB = reinterpret_cast<const double*>(base + L::cubes + L::ovs + L::t1);
 
-      const int a = blk[0] * TB + la, bb = blk[1] * TB + lb, c = blk[2] * TB + lc;
-      double acc = 0.0;
-      const bool valid = a < P.v && bb < P.v && c < P.v && !(blk[0] == blk[1] && la < lb) &&
-                         !(blk[1] == blk[2] && lb < lc);
+      const int a = bx * TB + la, bb = by * TB + lb, c = bz * TB + lc;
+      const bool valid = a < P.v && bb < P.v && c < P.v && !(bx == by && la < lb) && !(by == bz && lb < lc);
       if (valid) {
-        const int l[3] = {la, lb, lc};
-        double Td;
+        // orbit weight A (Eq. E_corr_CCSD_T): 1, 1/2 or 1/6
+        const bool all3 = (a == bb && bb == c), two = (a == bb || bb == c);
+        const double D = dAB[la * 8 + lb] - dAB[64 + lc];
+        const double r0 = (double)__frcp_rn((float)D);
+        const double r1 = fma(r0, fma(-D, r0, 1.0), r0);  // 1/D to ~1e-14 (one Newton step)
         if constexpr (CW == 2) {
-          const df w1 = w_dev_df<1>(cube, l), w2 = w_dev_df<2>(cube, l), w3 = w_dev_df<3>(cube, l);
-          const df w4 = w_dev_df<4>(cube, l), w5 = w_dev_df<5>(cube, l);
-          const float y0 = y_at<0>(ovsS, t1S, l);
-          const df v1 = df_add(w1, df{__fsub_rn(y_at<1>(ovsS, t1S, l), y0), 0.f});
-          const df v2 = df_add(w2, df{__fsub_rn(y_at<2>(ovsS, t1S, l), y0), 0.f});
-          const df v3 = df_add(w3, df{__fsub_rn(y_at<3>(ovsS, t1S, l), y0), 0.f});
-          const df v4 = df_add(w4, df{__fsub_rn(y_at<4>(ovsS, t1S, l), y0), 0.f});
-          const df v5 = df_add(w5, df{__fsub_rn(y_at<5>(ovsS, t1S, l), y0), 0.f});
+          const df w1 = w_dev_df<1>(cube, la, lb, lc), w2 = w_dev_df<2>(cube, la, lb, lc);
+          const df w3 = w_dev_df<3>(cube, la, lb, lc), w4 = w_dev_df<4>(cube, la, lb, lc);
+          const df w5 = w_dev_df<5>(cube, la, lb, lc);
+          const float y0 = y_at<0>(ovsS, t1S, la, lb, lc);
+          const df v1 = df_add(w1, df{__fsub_rn(y_at<1>(ovsS, t1S, la, lb, lc), y0), 0.f});
+          const df v2 = df_add(w2, df{__fsub_rn(y_at<2>(ovsS, t1S, la, lb, lc), y0), 0.f});
+          const df v3 = df_add(w3, df{__fsub_rn(y_at<3>(ovsS, t1S, la, lb, lc), y0), 0.f});
+          const df v4 = df_add(w4, df{__fsub_rn(y_at<4>(ovsS, t1S, la, lb, lc), y0), 0.f});
+          const df v5 = df_add(w5, df{__fsub_rn(y_at<5>(ovsS, t1S, la, lb, lc), y0), 0.f});
           const df Ae = df_add(w3, w4), Ao = df_add(df_add(w1, w2), w5);
           const df Se = df_add(v3, v4), So = df_add(df_add(v1, v2), v5);
           df dot = df_mul(w1, v1);
@@ -340,32 +349,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
           dot = df_add(dot, df_mul(w5, v5));
           df T = df_add(df_scale(dot, 3.f), df_add(df_mul(Ae, Se), df_mul(Ao, So)));
           T = df_add(T, df_scale(df_add(df_mul(Ae, So), df_mul(Ao, Se)), -2.f));
-          Td = (double)T.h + (double)T.l;
+          if (all3) T = df_mul(T, df{0.16666667f, -4.967054e-09f});  // 1/6 as a float pair
+          else if (two) T = df{T.h * 0.5f, T.l * 0.5f};
+          acc = fma((double)T.h, r1, acc);
+          acc = fma((double)T.l, r1, acc);
         } else {
-          const float w1 = w_dev<CW, 1>(cube, l), w2 = w_dev<CW, 2>(cube, l), w3 = w_dev<CW, 3>(cube, l);
-          const float w4 = w_dev<CW, 4>(cube, l), w5 = w_dev<CW, 5>(cube, l);
-          const float y0 = y_at<0>(ovsS, t1S, l);
-          const float v1 = w1 + (y_at<1>(ovsS, t1S, l) - y0), v2 = w2 + (y_at<2>(ovsS, t1S, l) - y0);
-          const float v3 = w3 + (y_at<3>(ovsS, t1S, l) - y0), v4 = w4 + (y_at<4>(ovsS, t1S, l) - y0);
-          const float v5 = w5 + (y_at<5>(ovsS, t1S, l) - y0);
+          const float w1 = w_dev<CW, 1>(cube, la, lb, lc), w2 = w_dev<CW, 2>(cube, la, lb, lc);
+          const float w3 = w_dev<CW, 3>(cube, la, lb, lc), w4 = w_dev<CW, 4>(cube, la, lb, lc);
+          const float w5 = w_dev<CW, 5>(cube, la, lb, lc);
+          const float y0 = y_at<0>(ovsS, t1S, la, lb, lc);
+          const float v1 = w1 + (y_at<1>(ovsS, t1S, la, lb, lc) - y0), v2 = w2 + (y_at<2>(ovsS, t1S, la, lb, lc) - y0);
+          const float v3 = w3 + (y_at<3>(ovsS, t1S, la, lb, lc) - y0), v4 = w4 + (y_at<4>(ovsS, t1S, la, lb, lc) - y0);
+          const float v5 = w5 + (y_at<5>(ovsS, t1S, la, lb, lc) - y0);
           const float Ae = w3 + w4, Ao = w1 + w2 + w5;
           const float Se = v3 + v4, So = v1 + v2 + v5;
           const float dot = w1 * v1 + w2 * v2 + w3 * v3 + w4 * v4 + w5 * v5;
-          Td = (double)(3.f * dot + Ae * Se + Ao * So - 2.f * (Ae * So + Ao * Se));
+          const float T = 3.f * dot + Ae * Se + Ao * So - 2.f * (Ae * So + Ao * Se);
+          const double Tw = all3 ? (double)T * (1.0 / 6.0) : (double)(two ? 0.5f * T : T);
+          acc = fma(Tw, r1, acc);
         }
-        const double D = eo - epsS[la] - epsS[16 + lb] - epsS[32 + lc];
-        const double r0 = (double)__frcp_rn((float)D);
-        const double r1 = fma(r0, fma(-D, r0, 1.0), r0);
-        const double wA = (a == bb && bb == c) ? (1.0 / 6.0) : ((a == bb || bb == c) ? 0.5 : 1.0);
-        acc = (wA * Td) * r1;
-      }
-      // fixed-order warp reduction; the producer sums the 16 warp partials in order
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) {
-        red[b * WARPS + warp] = acc;
-        ptx::mbar_arrive(&empty[b]);  // release: red[] and the buffer reads happen before
       }
       __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty[b]);  // release: this warp's reads of buffer b are done
+    }
+    if (cur_slot >= 0) {
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) P.partials[((int64_t)cur_slot * gridDim.x + blockIdx.x) * WARPS + warp] = acc;
     }
   }
   __syncthreads();
@@ -373,16 +382,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
 
 }  // namespace
 
+int64_t energy_tc_grid(int num_sms, int64_t items) { return std::min<int64_t>(items, (int64_t)num_sms); }
+
 size_t energy_tc_smem(int cw) {
   const size_t buf = cw == 2 ? Layout<2>::buf : Layout<1>::buf;
-  return 2 * buf + 128 + 512;
+  return 2 * buf + 128 + 512;  // + eps staging, added by the launcher
 }
 
 cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   EnergyMaps M;
   M.ovs = *e.map_ovs;
   M.t1 = *e.map_t1;
-  M.eps = *e.map_eps;
   EnergyParams P;
   P.o = e.o;
   P.v = e.v;
@@ -394,12 +404,14 @@ cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   P.t0 = e.t0;
   P.triples = e.triples;
   P.eps_o = e.eps_o;
+  P.eps_v = e.eps_v;
   P.partials = e.partials;
   P.err = e.err;
   P.wait_ns = e.wait_ns;
-  const size_t smem = energy_tc_smem(e.cw);
-  const int64_t grid = std::min<int64_t>(P.items, (int64_t)e.num_sms);
-  cudaError_t err;
+  const size_t smem = energy_tc_smem(e.cw) + sizeof(double) * (size_t)(e.v + e.o);
+  const int64_t grid = energy_tc_grid(e.num_sms, P.items);
+  cudaError_t err = cudaMemsetAsync(P.partials, 0, sizeof(double) * (size_t)e.nslots * grid * WARPS, s);
+  if (err != cudaSuccess) return err;
   if (e.cw == 2) {
     err = cudaFuncSetAttribute(k_energy_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

@@ -14,10 +14,10 @@ struct EnergyLaunch {
   const float* gbuf;           // cube-major G: [slot][g][X][Y][Z][cw planes][512 swizzled], X,Y,Z < ceil(v/8)
   const CUtensorMap* map_ovs;  // ovs32 [o][v][o][vq], 4D (b, j, a, i), box (8, 1, 8, 1)
   const CUtensorMap* map_t1;   // t1 [o][vq], 2D (a, i), box (8, 1)
-  const CUtensorMap* map_eps;  // eps_v copy [v], 1D FP64, box 8
   const Triple* triples;
   const double* eps_o;
-  double* partials;
+  const double* eps_v;
+  double* partials;  // [nslots][energy_tc_grid(num_sms, nslots*nbt)][ENERGY_TC_WARPS], zeroed by the launch
   unsigned int* err;
   unsigned long long wait_ns;
 };
@@ -33,6 +33,8 @@ __host__ __device__ __forceinline__ int cube_row(int u, int w) { return u * 64 +
 __host__ __device__ __forceinline__ int cube_zx(int u, int w) { return (u & 3) | ((((w ^ u) >> 2) & 1) << 2); }
 __host__ __device__ __forceinline__ int cube_off(int u, int w, int z) { return cube_row(u, w) + (z ^ cube_zx(u, w)); }
 
+constexpr int ENERGY_TC_WARPS = 16;
+int64_t energy_tc_grid(int num_sms, int64_t items);
 size_t energy_tc_smem(int cw);
 cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s);
 

@@ -743,7 +743,7 @@ static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64
   b->eps_copy = static_cast<double*>(take((size_t)v * 8));
   const size_t nbk = (size_t)((v + 7) / 8);
   b->gbuf = static_cast<float*>(take((size_t)pl.nslots * 3 * nbk * nbk * nbk * 512 * 4 * pl.cw));
-  b->partials = static_cast<double*>(take((size_t)pl.nslots * nbt * 8));
+  b->partials = static_cast<double*>(take((size_t)pl.nslots * ENERGY_TC_WARPS * 1024 * 8));
   b->etri = static_cast<double*>(take((size_t)std::max<int64_t>(1, ntri) * 8));
   b->maxbits = static_cast<unsigned long long*>(take(4 * 8));
   b->exps = static_cast<int*>(take(8 * 4));
@@ -814,7 +814,7 @@ static te_status build_maps(TcState* st, const TcPlan& pl, int o, int v, const T
 }
 
 struct EnergyMapsHost {
-  CUtensorMap ovs, t1, eps;
+  CUtensorMap ovs, t1;
 };
 
 static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, int nslots, const TcBuffers& b,
@@ -836,13 +836,6 @@ static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, 
     const uint32_t box[2] = {8, 1};
     if ((s = encode(st, &E->t1, b.t1_32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d, sn, box,
                     CU_TENSOR_MAP_SWIZZLE_NONE, "t1")) != TE_OK)
-      return s;
-  }
-  {  // eps_v copy [v] FP64
-    const uint64_t d[1] = {V};
-    const uint32_t box[1] = {8};
-    if ((s = encode(st, &E->eps, b.eps_copy, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 1, d, nullptr, box,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, "eps")) != TE_OK)
       return s;
   }
   return TE_OK;
@@ -970,9 +963,9 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   EL.gbuf = b.gbuf;
   EL.map_ovs = &EM.ovs;
   EL.map_t1 = &EM.t1;
-  EL.map_eps = &EM.eps;
   EL.triples = h->d_triples;
   EL.eps_o = c->eps_o;
+  EL.eps_v = b.eps_copy;
   EL.partials = b.partials;
   EL.err = h->d_err;
   EL.wait_ns = h->wait_limit_ns;
@@ -999,7 +992,8 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
       prof_end(h, pm, s);
     }
     if (e == cudaSuccess)
-      e = launch_reduce_triples(b.partials, nbt, h->d_triples, t0, ns, out + (t0 - t_begin), s);
+      e = launch_reduce_triples(b.partials, energy_tc_grid(h->num_sms, (int64_t)ns * nbt) * ENERGY_TC_WARPS,
+                                h->d_triples, t0, ns, out + (t0 - t_begin), s);
     h->n_launches += 3;
     if (e != cudaSuccess) return fail(TE_ECUDA, "tensor-core path launch: %s", cudaGetErrorString(e));
   }
