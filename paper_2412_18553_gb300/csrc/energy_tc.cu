@@ -48,6 +48,8 @@ struct Layout {
   static constexpr uint32_t t1 = 9 * 128;
   static constexpr uint32_t eps = 640;  // dAB[64] = e_ijk - e_a - e_b, epsC[8] (FP64, written by the producer)
   static constexpr uint32_t buf = cubes + ovs + t1 + eps;
+  // W~ (CW planes) and Y (one plane) of the item's 6 block orders, assembled once per item
+  static constexpr uint32_t asm_bytes = 6 * 512 * 4 * (CW + 1);
   static constexpr uint32_t tx = 18 * cube_bytes + 27 * TB * TB * 4 + 9 * TB * 4;
 };
 
@@ -190,7 +192,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                                          ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * L::buf);  // [2]
+  float* asmW = reinterpret_cast<float*>(smem + 2 * L::buf);           // [CW planes][6][512] then Y [6][512]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * L::buf + L::asm_bytes);  // [2]
   uint64_t* empty = full + 2;                                         // [2], one arrival per compute warp
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + 2);
   int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][4]: X, Y, Z, slot
@@ -287,9 +290,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
         if (((pending >> q) & 1u) && !ok) ptx::mbar_wait(&full[q], ((fphase >> q) & 1u) ^ 1u, P.wait_ns);
   } else {
     // ---------------- compute warps ----------------
+    // Each item in two phases.  A: every thread forms, at its own local point
+    // (la, lb, lc) of each of the 6 block orders P, W~ = G0 + G1 + G2 (as an FP32
+    // pair for CW = 2) and Y, into the assembled area; the G buffer is then
+    // released to the producer.  B: every thread takes the orbit (a,b,c) =
+    // its local point in block order 0 and reads W~ and Y at its 6 positions.
     uint32_t phase = 0u;  // one bit per buffer
     int b = 0;
     const int la = (tid >> 6), lb = (tid >> 3) & 7, lc = tid & 7;
+    const int o_own = cube_off(la, lb, lc), o_g1 = cube_off(lb, lc, la), o_g2 = cube_off(lc, la, lb);
+    int pos_off[6];
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+      const int u = n <= 1 ? la : (n <= 3 ? lb : lc);
+      const int w = (n == 0 || n == 5) ? lb : ((n == 1 || n == 3) ? lc : la);
+      const int z = 3 * 0 + ((n == 0 || n == 2) ? lc : ((n == 1 || n == 4) ? lb : la));
+      pos_off[n] = n * 512 + cube_off(u, w, z);
+    }
+    float* asmY = asmW + CW * 6 * 512;
     double acc = 0.0;  // this thread's sum over the items of the current triple slot
     int cur_slot = -1;
     for (int64_t it = blockIdx.x; it < P.items; it += gridDim.x, b ^= 1) {
@@ -321,25 +339,60 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
       const float* ovsS = reinterpret_cast<const float*>(base + L::cubes);
       const float* t1S = reinterpret_cast<const float*>(base + L::cubes + L::ovs);
       const double* dAB = reinterpret_cast<const double*>(base + L::cubes + L::ovs + L::t1);
+      const double D = dAB[la * 8 + lb] - dAB[64 + lc];
 
+      // ---- phase A ----
+#pragma unroll
+      for (int Pn = 0; Pn < 6; ++Pn) {
+        const int r1 = Pn == 0 ? 3 : Pn == 1 ? 5 : Pn == 2 ? 1 : Pn == 3 ? 4 : Pn == 4 ? 0 : 2;
+        const int r2 = Pn == 0 ? 4 : Pn == 1 ? 2 : Pn == 2 ? 5 : Pn == 3 ? 0 : Pn == 4 ? 3 : 1;
+        const int s0 = Pn <= 1 ? 0 : (Pn <= 3 ? 1 : 2);
+        const int s1 = Pn == 0 ? 1 : Pn == 1 ? 2 : Pn == 2 ? 0 : Pn == 3 ? 2 : Pn == 4 ? 0 : 1;
+        const int s2 = 3 - s0 - s1;
+        const float* g0 = cube + (0 * 6 + Pn) * 512 * CW;
+        const float* g1 = cube + (1 * 6 + r1) * 512 * CW;
+        const float* g2 = cube + (2 * 6 + r2) * 512 * CW;
+        const int wo = Pn * 512 + o_own;
+        if constexpr (CW == 2) {
+          df wv = df_two_sum(g0[o_own], g1[o_g1]);
+          wv = df_add(wv, df{g2[o_g2], 0.f});
+          wv = df_norm(wv.h, __fadd_rn(wv.l, __fadd_rn(__fadd_rn(g0[512 + o_own], g1[512 + o_g1]), g2[512 + o_g2])));
+          asmW[wo] = wv.h;
+          asmW[6 * 512 + wo] = wv.l;
+        } else {
+          asmW[wo] = (g0[o_own] + g1[o_g1]) + g2[o_g2];
+        }
+        // Y at (x, y, z) = (la, lb, lc) of blocks (s0, s1, s2):
+        //   ovs(i,x,j,y) t1(k,z) + ovs(j,y,k,z) t1(i,x) + ovs(i,x,k,z) t1(j,y)
+        asmY[wo] = ovsS[((0 * 3 + s0) * 3 + s1) * 64 + la * 8 + lb] * t1S[(2 * 3 + s2) * 32 + lc] +
+                   ovsS[((1 * 3 + s1) * 3 + s2) * 64 + lb * 8 + lc] * t1S[(0 * 3 + s0) * 32 + la] +
+                   ovsS[((2 * 3 + s0) * 3 + s2) * 64 + la * 8 + lc] * t1S[(1 * 3 + s1) * 32 + lb];
+      }
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty[b]);  // this warp no longer reads buffer b
+      asm volatile("bar.sync 1, %0;" ::"n"(WARPS * 32) : "memory");
+
+      // ---- phase B ----
       const int a = bx * TB + la, bb = by * TB + lb, c = bz * TB + lc;
       const bool valid = a < P.v && bb < P.v && c < P.v && !(bx == by && la < lb) && !(by == bz && lb < lc);
       if (valid) {
         // orbit weight A (Eq. E_corr_CCSD_T): 1, 1/2 or 1/6
         const bool all3 = (a == bb && bb == c), two = (a == bb || bb == c);
-        const double D = dAB[la * 8 + lb] - dAB[64 + lc];
         const double r0 = (double)__frcp_rn((float)D);
         const double r1 = fma(r0, fma(-D, r0, 1.0), r0);  // 1/D to ~1e-14 (one Newton step)
+        const float y0 = asmY[pos_off[0]];
         if constexpr (CW == 2) {
-          const df w1 = w_dev_df<1>(cube, la, lb, lc), w2 = w_dev_df<2>(cube, la, lb, lc);
-          const df w3 = w_dev_df<3>(cube, la, lb, lc), w4 = w_dev_df<4>(cube, la, lb, lc);
-          const df w5 = w_dev_df<5>(cube, la, lb, lc);
-          const float y0 = y_at<0>(ovsS, t1S, la, lb, lc);
-          const df v1 = df_add(w1, df{__fsub_rn(y_at<1>(ovsS, t1S, la, lb, lc), y0), 0.f});
-          const df v2 = df_add(w2, df{__fsub_rn(y_at<2>(ovsS, t1S, la, lb, lc), y0), 0.f});
-          const df v3 = df_add(w3, df{__fsub_rn(y_at<3>(ovsS, t1S, la, lb, lc), y0), 0.f});
-          const df v4 = df_add(w4, df{__fsub_rn(y_at<4>(ovsS, t1S, la, lb, lc), y0), 0.f});
-          const df v5 = df_add(w5, df{__fsub_rn(y_at<5>(ovsS, t1S, la, lb, lc), y0), 0.f});
+          const float h0 = asmW[pos_off[0]], l0 = asmW[6 * 512 + pos_off[0]];
+          df wd[5], vd[5];
+#pragma unroll
+          for (int n = 1; n < 6; ++n) {
+            df d = df_two_sum(asmW[pos_off[n]], -h0);
+            d = df_norm(d.h, __fadd_rn(d.l, __fsub_rn(asmW[6 * 512 + pos_off[n]], l0)));
+            wd[n - 1] = d;
+            vd[n - 1] = df_add(d, df{__fsub_rn(asmY[pos_off[n]], y0), 0.f});
+          }
+          const df w1 = wd[0], w2 = wd[1], w3 = wd[2], w4 = wd[3], w5 = wd[4];
+          const df v1 = vd[0], v2 = vd[1], v3 = vd[2], v4 = vd[3], v5 = vd[4];
           const df Ae = df_add(w3, w4), Ao = df_add(df_add(w1, w2), w5);
           const df Se = df_add(v3, v4), So = df_add(df_add(v1, v2), v5);
           df dot = df_mul(w1, v1);
@@ -354,23 +407,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
           acc = fma((double)T.h, r1, acc);
           acc = fma((double)T.l, r1, acc);
         } else {
-          const float w1 = w_dev<CW, 1>(cube, la, lb, lc), w2 = w_dev<CW, 2>(cube, la, lb, lc);
-          const float w3 = w_dev<CW, 3>(cube, la, lb, lc), w4 = w_dev<CW, 4>(cube, la, lb, lc);
-          const float w5 = w_dev<CW, 5>(cube, la, lb, lc);
-          const float y0 = y_at<0>(ovsS, t1S, la, lb, lc);
-          const float v1 = w1 + (y_at<1>(ovsS, t1S, la, lb, lc) - y0), v2 = w2 + (y_at<2>(ovsS, t1S, la, lb, lc) - y0);
-          const float v3 = w3 + (y_at<3>(ovsS, t1S, la, lb, lc) - y0), v4 = w4 + (y_at<4>(ovsS, t1S, la, lb, lc) - y0);
-          const float v5 = w5 + (y_at<5>(ovsS, t1S, la, lb, lc) - y0);
-          const float Ae = w3 + w4, Ao = w1 + w2 + w5;
-          const float Se = v3 + v4, So = v1 + v2 + v5;
-          const float dot = w1 * v1 + w2 * v2 + w3 * v3 + w4 * v4 + w5 * v5;
+          const float W0 = asmW[pos_off[0]];
+          float w[5], vv[5];
+#pragma unroll
+          for (int n = 1; n < 6; ++n) {
+            w[n - 1] = asmW[pos_off[n]] - W0;
+            vv[n - 1] = w[n - 1] + (asmY[pos_off[n]] - y0);
+          }
+          const float Ae = w[2] + w[3], Ao = w[0] + w[1] + w[4];
+          const float Se = vv[2] + vv[3], So = vv[0] + vv[1] + vv[4];
+          const float dot = w[0] * vv[0] + w[1] * vv[1] + w[2] * vv[2] + w[3] * vv[3] + w[4] * vv[4];
           const float T = 3.f * dot + Ae * Se + Ao * So - 2.f * (Ae * So + Ao * Se);
           const double Tw = all3 ? (double)T * (1.0 / 6.0) : (double)(two ? 0.5f * T : T);
           acc = fma(Tw, r1, acc);
         }
       }
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&empty[b]);  // release: this warp's reads of buffer b are done
+      asm volatile("bar.sync 1, %0;" ::"n"(WARPS * 32) : "memory");  // assembled area free
     }
     if (cur_slot >= 0) {
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -385,7 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
 int64_t energy_tc_grid(int num_sms, int64_t items) { return std::min<int64_t>(items, (int64_t)num_sms); }
 
 size_t energy_tc_smem(int cw) {
-  const size_t buf = cw == 2 ? Layout<2>::buf : Layout<1>::buf;
+  const size_t buf = cw == 2 ? Layout<2>::buf + Layout<2>::asm_bytes / 2 : Layout<1>::buf + Layout<1>::asm_bytes / 2;
   return 2 * buf + 128 + 512;  // + eps staging, added by the launcher
 }
 
