@@ -42,6 +42,11 @@ std::vector<Triple> unique_triples(int nocc) {
 
 int64_t num_unique_triples(int64_t nocc) { return nocc * (nocc + 1) * (nocc + 2) / 6 - nocc; }
 
+void drop_graphs(Handle* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
   int prev = -1;
@@ -71,6 +76,8 @@ struct Carver {
 
 static te_status ensure_workspace(Handle* h, size_t bytes) {
   if (h->ws_bytes >= bytes) return TE_OK;
+  if (h->capturing) return fail(TE_EUNSUPPORTED, "workspace growth inside a graph capture");
+  drop_graphs(h);  // captured graphs hold the old workspace's addresses
   if (h->ws) {
     cudaDeviceSynchronize();  // no launch may still read the old workspace
     cudaFree(h->ws);
@@ -93,8 +100,12 @@ static te_status ensure_workspace(Handle* h, size_t bytes) {
   return TE_OK;
 }
 
+// The canonical order is prefix-closed (the triples of nocc = n are the first
+// ones of any larger nocc), so one table for the largest nocc serves all.
 static te_status ensure_triples(Handle* h, int nocc) {
-  if (h->triples_nocc == nocc) return TE_OK;
+  if (h->triples_nocc >= nocc) return TE_OK;
+  if (h->capturing) return fail(TE_EUNSUPPORTED, "triple table growth inside a graph capture");
+  drop_graphs(h);
   std::vector<Triple> t = unique_triples(nocc);
   const size_t need = std::max<size_t>(1, t.size());
   if (h->triples_cap < need) {
@@ -121,7 +132,7 @@ static te_status ensure_triples(Handle* h, int nocc) {
   return TE_OK;
 }
 
-static te_status validate(const Handle* h, const te_cluster* c, te_precision p, cudaStream_t s) {
+static te_status host_check(const Handle* h, const te_cluster* c, te_precision p) {
   if (!h) return fail(TE_EINVAL, "null handle");
   if (!c) return fail(TE_EINVAL, "null cluster descriptor");
   if (c->nocc < 1 || c->nvir < 1) return fail(TE_EINVAL, "nocc and nvir must be >= 1 (got %lld, %lld)",
@@ -132,23 +143,44 @@ static te_status validate(const Handle* h, const te_cluster* c, te_precision p, 
     return fail(TE_EINVAL, "null array pointer in cluster descriptor");
   if (p != TE_FP64 && p != TE_TF32 && p != TE_BF16X3 && p != TE_TF32X3 && p != TE_OZAKI)
     return fail(TE_EINVAL, "unknown precision mode %d", (int)p);
-  // every denominator must be negative: max eps_o < min eps_v
-  std::vector<double> eo(c->nocc), ev(c->nvir);
-  if (cudaMemcpyAsync(eo.data(), c->eps_o, c->nocc * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(ev.data(), c->eps_v, c->nvir * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return fail(TE_ECUDA, "reading orbital energies failed: %s", cudaGetErrorString(cudaGetLastError()));
-  double mo = -1e300, mv = 1e300;
-  for (double x : eo) {
-    if (!(x == x) || x > 1e300 || x < -1e300) return fail(TE_EINVAL, "non-finite eps_o");
-    mo = std::max(mo, x);
-  }
-  for (double x : ev) {
-    if (!(x == x) || x > 1e300 || x < -1e300) return fail(TE_EINVAL, "non-finite eps_v");
-    mv = std::min(mv, x);
-  }
-  if (!(mo < mv)) return fail(TE_EINVAL, "max(eps_o) = %g must be below min(eps_v) = %g", mo, mv);
   return TE_OK;
+}
+
+// Every denominator must be negative: max eps_o < min eps_v.  Reads all
+// clusters' orbital energies back with one synchronisation of s.
+static te_status check_eps(const te_cluster* cs, int64_t n, cudaStream_t s) {
+  std::vector<std::vector<double>> eo(n), ev(n);
+  for (int64_t x = 0; x < n; ++x) {
+    eo[x].resize(cs[x].nocc);
+    ev[x].resize(cs[x].nvir);
+    if (cudaMemcpyAsync(eo[x].data(), cs[x].eps_o, cs[x].nocc * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(ev[x].data(), cs[x].eps_v, cs[x].nvir * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess)
+      return fail(TE_ECUDA, "reading orbital energies failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(TE_ECUDA, "reading orbital energies failed: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int64_t x = 0; x < n; ++x) {
+    double mo = -1e300, mv = 1e300;
+    for (double e : eo[x]) {
+      if (!(e == e) || e > 1e300 || e < -1e300) return fail(TE_EINVAL, "non-finite eps_o (cluster %lld)", (long long)x);
+      mo = std::max(mo, e);
+    }
+    for (double e : ev[x]) {
+      if (!(e == e) || e > 1e300 || e < -1e300) return fail(TE_EINVAL, "non-finite eps_v (cluster %lld)", (long long)x);
+      mv = std::min(mv, e);
+    }
+    if (!(mo < mv))
+      return fail(TE_EINVAL, "cluster %lld: max(eps_o) = %g must be below min(eps_v) = %g", (long long)x, mo, mv);
+  }
+  return TE_OK;
+}
+
+static te_status validate(const Handle* h, const te_cluster* c, te_precision p, cudaStream_t s) {
+  te_status st = host_check(h, c, p);
+  if (st != TE_OK) return st;
+  return check_eps(c, 1, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -237,7 +269,7 @@ static te_status run_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64
 size_t prof_begin(Handle* h, int kind, cudaStream_t s) {
   if (kind == 0) ++h->n_gemm;
   else ++h->n_energy;
-  if (!h->profiling) return SIZE_MAX;
+  if (!h->profiling || h->capturing) return SIZE_MAX;
   while (h->ev_pool.size() < h->ev_used + 2) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) {
@@ -310,6 +342,8 @@ te_status te_destroy(te_handle hh) {
   if (h->d_triples) cudaFree(h->d_triples);
   if (h->d_err) cudaFree(h->d_err);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   destroy_tc_state(h);
   delete h;
   return TE_OK;
@@ -352,18 +386,96 @@ te_status t_energy(te_handle hh, const te_cluster* c, te_precision p, double* e_
 te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_precision p,
                            double* e_out, te_stream_t ss) {
   Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
   if (!h) return fail(TE_EINVAL, "null handle");
   if (n < 0) return fail(TE_EINVAL, "negative batch size");
   if (n == 0) return TE_OK;
   if (!cs || !e_out) return fail(TE_EINVAL, "null cluster array or e_out");
+  DeviceGuard g(h->device);
   for (int64_t x = 0; x < n; ++x) {
-    te_status st = t_energy(hh, cs + x, p, e_out + x, ss);
+    te_status st = host_check(h, cs + x, p);
     if (st != TE_OK) {
       char msg[512];
       snprintf(msg, sizeof(msg), "cluster %lld: %s", (long long)x, te_last_error());
       return fail(st, "%s", msg);
     }
   }
+  // a replay of a captured batch needs no further checks of the descriptors
+  for (auto& ge : h->graphs) {
+    if (ge.precision != (int)p || ge.e_out != e_out || (int64_t)ge.clusters.size() != n) continue;
+    if (std::memcmp(ge.clusters.data(), cs, sizeof(te_cluster) * n) != 0) continue;
+    te_status st = check_eps(cs, n, s);
+    if (st != TE_OK) return st;
+    if (cudaGraphLaunch(ge.exec, s) != cudaSuccess)
+      return fail(TE_ECUDA, "graph launch: %s", cudaGetErrorString(cudaGetLastError()));
+    h->n_launches += ge.launches;
+    return TE_OK;
+  }
+  te_status st = check_eps(cs, n, s);
+  if (st != TE_OK) return st;
+  // one workspace and one triple table for the whole batch
+  size_t maxb = 0;
+  int64_t maxo = 1;
+  for (int64_t x = 0; x < n; ++x) {
+    size_t b = 0;
+    st = te_workspace_bytes(hh, cs + x, p, &b);
+    if (st != TE_OK) return st;
+    maxb = std::max(maxb, b);
+    maxo = std::max<int64_t>(maxo, cs[x].nocc);
+  }
+  st = ensure_workspace(h, maxb);
+  if (st != TE_OK) return st;
+  st = ensure_triples(h, (int)maxo);
+  if (st != TE_OK) return st;
+  if (p != TE_FP64) {  // tile shapes tuned per (nocc, nvir) before the capture
+    for (int64_t x = 0; x < n; ++x) {
+      st = tc_autotune(h, cs + x, p, s);
+      if (st != TE_OK) return st;
+    }
+  }
+  // capture the batch's launches into one CUDA graph on an internal stream
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(TE_ECUDA, "stream creation failed");
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TE_ECUDA, "stream synchronise failed");
+  if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(TE_ECUDA, "begin capture: %s", cudaGetErrorString(cudaGetLastError()));
+  h->capturing = true;
+  const int64_t l0 = h->n_launches;
+  for (int64_t x = 0; x < n && st == TE_OK; ++x) {
+    const int64_t nt = num_unique_triples(cs[x].nocc);
+    if (nt == 0) {
+      if (cudaMemsetAsync(e_out + x, 0, sizeof(double), h->cap_stream) != cudaSuccess)
+        st = fail(TE_ECUDA, "memset failed");
+      ++h->n_launches;
+    } else {
+      st = run_any(h, cs + x, p, 0, nt, nullptr, e_out + x, h->cap_stream);
+    }
+  }
+  h->capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (st != TE_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ec != cudaSuccess || !graph) return fail(TE_ECUDA, "end capture: %s", cudaGetErrorString(ec));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return fail(TE_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+  if (h->graphs.size() >= 4) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  Handle::GraphEntry ge;
+  ge.clusters.assign(cs, cs + n);
+  ge.precision = (int)p;
+  ge.e_out = e_out;
+  ge.exec = exec;
+  ge.launches = h->n_launches - l0;
+  h->graphs.push_back(ge);
+  if (cudaGraphLaunch(exec, s) != cudaSuccess)
+    return fail(TE_ECUDA, "graph launch: %s", cudaGetErrorString(cudaGetLastError()));
   return TE_OK;
 }
 

@@ -655,7 +655,8 @@ struct TcPlan {
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri) {
+static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, int force_tb = 0,
+                        int force_nnt = 0) {
   TcPlan pl{};
   pl.mode = mode;
   pl.es = (mode == TC_BF16X3 || mode == TC_OZAKI) ? 2 : 4;
@@ -676,12 +677,21 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri) {
       bestTB = TB;
     }
   }
+  if (!force_tb) {
+    auto it = h->tuned.find(std::make_tuple(o, v, mode));
+    if (it != h->tuned.end()) {
+      force_tb = it->second.first;
+      force_nnt = it->second.second;
+    }
+  }
+  if (force_tb) bestTB = force_tb;
   pl.TB = bestTB;
   pl.TA = 128 / bestTB;
   pl.n_mx = (v + pl.TA - 1) / pl.TA;
   pl.n_my = (v + pl.TB - 1) / pl.TB;
   const int ntmax = std::min(256, (512 / (nacc * nbuf)) / 16 * 16);
   pl.n_nt = (v + ntmax - 1) / ntmax;
+  if (force_nnt >= pl.n_nt) pl.n_nt = force_nnt;
   pl.NT = round_up((v + pl.n_nt - 1) / pl.n_nt, 16);
   pl.cbw = mode == TC_OZAKI ? 64 : 128;
   pl.kw_elems = pl.cbw / pl.es;
@@ -885,6 +895,105 @@ te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, siz
 te_status ensure_workspace_public(Handle* h, size_t bytes);
 te_status ensure_triples_public(Handle* h, int nocc);
 
+te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream_t s) {
+  const int o = (int)c->nocc, v = (int)c->nvir, mode = tc_mode_of(p);
+  const auto key = std::make_tuple(o, v, mode);
+  if (h->tuned.count(key)) return TE_OK;
+  if (mode == TC_OZAKI && 2 * (v + o) > 1024) return TE_OK;  // run_tc reports it
+  const int64_t nt = num_unique_triples(o);
+  if (nt == 0) return TE_OK;
+  // candidate M tiles: padding within 15% of the least; candidate N splits: the fewest and one more
+  std::vector<std::pair<int, int>> cand;
+  int64_t best_rows = -1;
+  for (int TB = 128; TB >= 16; TB /= 2) {
+    const int TA = 128 / TB;
+    const int64_t rows = (int64_t)round_up(v, TA) * round_up(v, TB);
+    if (best_rows < 0 || rows < best_rows) best_rows = rows;
+  }
+  const TcPlan base = make_plan(h, o, v, mode, nt, 128, 0);
+  for (int TB = 128; TB >= 16; TB /= 2) {
+    const int TA = 128 / TB;
+    const int64_t rows = (int64_t)round_up(v, TA) * round_up(v, TB);
+    if (rows * 100 > best_rows * 115) continue;
+    cand.emplace_back(TB, base.n_nt);
+    if (round_up((v + base.n_nt) / (base.n_nt + 1), 16) >= 64) cand.emplace_back(TB, base.n_nt + 1);
+  }
+  if (cand.size() <= 1) {
+    if (!cand.empty()) h->tuned[key] = cand[0];
+    return TE_OK;
+  }
+  TcState* st = tc_state(h);
+  te_status rs = get_encoder(st);
+  if (rs != TE_OK) return rs;
+  rs = ensure_triples_public(h, o);
+  if (rs != TE_OK) return rs;
+  const int64_t nbt = energy_num_block_triples(v);
+  size_t need = 0;
+  for (const auto& cd : cand) {
+    const TcPlan pl = make_plan(h, o, v, mode, nt, cd.first, cd.second);
+    TcBuffers b;
+    need = std::max(need, tc_carve(nullptr, pl, o, v, nbt, num_unique_triples(o), &b));
+  }
+  rs = ensure_workspace_public(h, need);
+  if (rs != TE_OK) return rs;
+  char* wbase = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(TE_ECUDA, "event creation failed");
+  float best_ms = 1e30f;
+  std::pair<int, int> best = cand[0];
+  bool prepped = false;
+  for (const auto& cd : cand) {
+    const TcPlan pl = make_plan(h, o, v, mode, nt, cd.first, cd.second);
+    if (pl.stages < 2) continue;
+    TcBuffers b;
+    tc_carve(wbase, pl, o, v, nbt, num_unique_triples(o), &b);
+    cudaError_t e = cudaSuccess;
+    if (!prepped) {  // the operand planes sit first in the workspace for every candidate
+      if (mode == TC_BF16X3) e = launch_prep_tc<TC_BF16X3>(c, pl, b, s);
+      else if (mode == TC_TF32X3) e = launch_prep_tc<TC_TF32X3>(c, pl, b, s);
+      else if (mode == TC_TF32) e = launch_prep_tc<TC_TF32>(c, pl, b, s);
+      else e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
+      prepped = true;
+    }
+    TcMaps M;
+    if (e != cudaSuccess || build_maps(st, pl, o, v, b, &M) != TE_OK) continue;
+    TcParams P{};
+    P.o = o; P.v = v; P.TA = pl.TA; P.TB = pl.TB; P.NT = pl.NT;
+    P.n_mx = pl.n_mx; P.n_my = pl.n_my; P.n_nt = pl.n_nt;
+    P.kw_chunks = pl.kw_chunks; P.ko_chunks = pl.ko_chunks; P.kw_elems = pl.kw_elems; P.ko_elems = pl.ko_elems;
+    P.cbw = pl.cbw; P.cbo = pl.cbo; P.stages = pl.stages; P.stage_bytes = pl.stage_bytes;
+    P.a_part_bytes = pl.a_part_bytes; P.b_part_bytes = pl.b_part_bytes; P.tmem_cols = pl.tmem_cols;
+    P.triples = h->d_triples; P.gbuf = b.gbuf; P.ldz = pl.ldz; P.exps = b.exps; P.err = h->d_err;
+    P.wait_ns = h->wait_limit_ns; P.t0 = 0;
+    const int ns = (int)std::min<int64_t>(pl.nslots, nt);
+    P.total_tiles = 3LL * ns * pl.n_mx * pl.n_my * pl.n_nt;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, s);
+      if (mode == TC_BF16X3) e = launch_gemm_tc<TC_BF16X3>(h, M, P, pl.smem, s);
+      else if (mode == TC_TF32X3) e = launch_gemm_tc<TC_TF32X3>(h, M, P, pl.smem, s);
+      else if (mode == TC_TF32) e = launch_gemm_tc<TC_TF32>(h, M, P, pl.smem, s);
+      else e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
+      cudaEventRecord(e1, s);
+      h->n_launches += 1;
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = std::min(ms, t / (float)ns);  // per triple
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cd;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) return fail(TE_ECUDA, "autotune launch failed");
+  h->tuned[key] = best;
+  return TE_OK;
+}
+
 te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin, int64_t t_end,
                  double* e_tri_out, double* e_total_out, cudaStream_t s) {
   if (h->cc_major != 10 && h->cc_major != 11)
@@ -900,8 +1009,9 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   const TcPlan pl = make_plan(h, o, v, mode, nt);
   if (pl.stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
   // exact level-2/3 sums: K * 2^14 (two products per level-3 term, each < 2^13) below 2^24
-  if (mode == TC_OZAKI && 2 * (pl.kw_chunks * pl.kw_elems + pl.ko_chunks * pl.ko_elems) > 1024)
-    return fail(TE_EUNSUPPORTED, "OZAKI mode needs 2 (nvir + nocc) <= 1024 (padded) for exact accumulation");
+  // exact level-2/3 sums: 2 (v + o) nonzero terms of at most 2^14 stay below 2^24
+  if (mode == TC_OZAKI && 2 * (v + o) > 1024)
+    return fail(TE_EUNSUPPORTED, "OZAKI mode needs 2 (nvir + nocc) <= 1024 for exact accumulation");
   const int64_t nbt = energy_num_block_triples(v);
   TcBuffers b;
   const size_t bytes = tc_carve(nullptr, pl, o, v, nbt, ntri, &b);

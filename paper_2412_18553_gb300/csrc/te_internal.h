@@ -6,7 +6,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/tenergy.h"
@@ -63,7 +65,22 @@ struct Handle {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, size_t>> ev_marks;  // (kind 0 gemm / 1 energy, start event index)
+  bool capturing = false;                         // inside a CUDA graph capture (no profiling events)
+  // CUDA graphs of whole batches, keyed by the batch signature
+  struct GraphEntry {
+    std::vector<te_cluster> clusters;
+    int precision;
+    double* e_out;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  // autotuned tile shapes: (nocc, nvir, mode) -> (TB, n_nt)
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
 };
+
+void drop_graphs(Handle* h);
 
 // Profiling helpers: begin/end a timed launch of `kind` on stream s.
 size_t prof_begin(Handle* h, int kind, cudaStream_t s);
