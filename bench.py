@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--check-triples", type=int, default=8,
                     help="triples checked against the FP64 GPU path for |dE|")
     ap.add_argument("--cpu-triples", type=int, default=2)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched measurement (16 clusters, nocc 8..20, nvir = 8 nocc)")
     return ap.parse_args()
 
 
@@ -264,6 +266,35 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
         del keep, host
 
+    # batched: 16 independent clusters (nocc ~ [8,20], nvir = 8 nocc) per step, one CUDA graph
+    batch = None
+    if not args.no_batch:
+        import tegen
+        cls = tegen.make_batch(range(16), rule="v8o")
+        bdev = [{n: torch.as_tensor(x).to(torch.device("cuda", local)) for n, x in c.arrays().items()}
+                for c in cls]
+        Fb = sum(te.flop_count(c.nocc, c.nvir) for c in cls)
+        for _ in range(max(1, args.warmup)):
+            te.t_energy_batched(bdev, prec, handle=h)
+        torch.cuda.synchronize()
+        barrier()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record()
+        for _ in range(args.steps):
+            eb = te.t_energy_batched(bdev, prec, handle=h)
+        b1.record()
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / args.steps
+        bt = torch.tensor([bms], device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(bt, op=torch.distributed.ReduceOp.MAX)
+        bms = float(bt.item())
+        batch = {"workload": "16 clusters, seeds 0..15, nocc ~ U[8,20], nvir = 8 nocc, naux = 4(o+v)",
+                 "clusters_per_s": world * 16 / (bms / 1e3), "gflops": world * Fb / (bms / 1e3) / 1e9,
+                 "ms_per_batch": bms, "graph": True}
+        del bdev
+
     pk, pk_src = peaks()
     if prec == "fp64":
         roof = None
@@ -300,6 +331,7 @@ def main():
                "dE_sampled": [{"triple": tt, "share": a, "share_fp64": b} for tt, a, b in d_sh],
                "gpu_launches": prof["launches"],
                "profile": prof,
+               "batch16": batch,
                "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
         print(json.dumps(out))
     if world > 1:
