@@ -207,6 +207,15 @@ const char* te_last_error(void);
  * later launches on this handle; 0 restores the default (4 s). */
 te_status te_set_wait_limit_ns(te_handle h, uint64_t ns);
 
+/* Self-test of the device watchdog.  Launches on s one single-thread kernel
+ * whose bounded wait is on a shared-memory mbarrier that nothing ever
+ * arrives on; after limit_ns (1 ms .. 10 s, else TE_EINVAL) the wait gives
+ * up, the kernel sets the handle's error word (ERR_WAIT_TIMEOUT) and returns,
+ * so the context stays usable.  The following te_sync must then return
+ * TE_ETIMEOUT (and clear the word).  Exercises the same wait routine and
+ * error path as the tensor-core pipelines without faulting or hanging. */
+te_status te_watchdog_selftest(te_handle h, uint64_t limit_ns, te_stream_t s);
+
 #ifdef __cplusplus
 }
 #endif

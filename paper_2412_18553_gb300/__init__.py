@@ -83,6 +83,12 @@ class Handle:
     def set_wait_limit_ns(self, ns: int):
         _lib.check(_lib.load().te_set_wait_limit_ns(self.ptr, int(ns)))
 
+    def watchdog_selftest(self, limit_ns: int = 20_000_000, stream=None):
+        """Launch a kernel whose bounded wait must expire after limit_ns; the
+        next sync() raises TEnergyError with status TE_ETIMEOUT."""
+        s = _stream(self.device, stream)
+        _lib.check(_lib.load().te_watchdog_selftest(self.ptr, int(limit_ns), s))
+
     def profile(self, on: bool = True):
         _lib.check(_lib.load().te_profile_enable(self.ptr, 1 if on else 0))
 

@@ -481,8 +481,17 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
 
 te_status t_energy_vjp(te_handle hh, const te_cluster* c, te_precision p, double gE, double* e_out,
                        te_cluster_grad* gr, te_stream_t ss) {
-  (void)hh; (void)c; (void)p; (void)gE; (void)e_out; (void)gr; (void)ss;
-  return fail(TE_EUNSUPPORTED, "t_energy_vjp is not available in this build");
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (!gr) return fail(TE_EINVAL, "null gradient descriptor");
+  if (!(gE == gE) || gE > 1e300 || gE < -1e300) return fail(TE_EINVAL, "non-finite gE");
+  if (h->capturing) return fail(TE_EINVAL, "t_energy_vjp cannot run inside a graph capture");
+  DeviceGuard g(h->device);
+  te_status st = validate(h, c, p, s);
+  if (st != TE_OK) return st;
+  // every mode's adjoint is evaluated in float64 (the forward's exact reference)
+  return run_vjp_fp64(h, c, gE, e_out, gr, s);
 }
 
 te_status te_sync(te_handle hh, te_stream_t ss) {

@@ -62,10 +62,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
-  for (uint32_t it = 0;; ++it) {
+  // time limit checked every 16 polls; the iteration cap bounds the wait even
+  // if the timer were not advancing
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 15u) == 15u && globaltimer() - t0 > limit_ns) return false;
   }
+  return false;
 }
 
 // ---------------- TMA ----------------

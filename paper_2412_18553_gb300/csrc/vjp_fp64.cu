@@ -1,0 +1,446 @@
+// Adjoint of E(T) (float64): dE/d(eps_o, eps_v, ovvv, ooov, ovov, t1, t2).
+//
+// E = sum over unique occupied triples t of (m_t/3) e_t,
+//   e_t = sum_{abc} W~[abc] R[V][abc] / D[abc],  V = W~ + Y,
+// with R acting on the virtual indices at fixed ijk (equal to R on the
+// occupied ones at fixed abc).  R's coefficient pattern (4, 3-cycles +1,
+// transpositions -2) is symmetric and D is invariant under permutations of
+// abc, so with w_t = gE m_t / 3:
+//   dW~ = w_t R[2 W~ + Y] / D,   dY = w_t R[W~] / D,   dD = -w_t W~ R[V] / D^2.
+// W~[a,b,c] = G0[a,b,c] + G1[b,c,a] + G2[c,a,b] gives dG0[x,y,z] = dW~[x,y,z],
+// dG1[x,y,z] = dW~[z,x,y], dG2[x,y,z] = dW~[y,z,x]; each G block
+//   G(p,q,r)[x,y,z] = sum_d ovvv[p,x,y,d] t2[r,q,z,d] + sum_d ovvv[q,y,x,d] t2[r,p,z,d]
+//                   - sum_l t2[l,p,y,x] ooov[q,l,r,z] - sum_l t2[l,q,x,y] ooov[p,l,r,z]
+// back-propagates through eight GEMMs (two per K segment).  Y = ovs(ia,jb) t1(kc)
+// + ovs(jb,kc) t1(ia) + ovs(ia,kc) t1(jb) with ovs = (ovov + ovov^T)/2 gives the
+// ovov and t1 parts.  Triples are processed one after another on the stream
+// and every accumulation has a fixed order, so the gradient is deterministic.
+#include <algorithm>
+
+#include "te_internal.h"
+
+namespace te {
+
+// ---------------------------------------------------------------------------
+// per-triple adjoint of the energy epilogue, one thread per ordered (a,b,c)
+// ---------------------------------------------------------------------------
+
+struct AdjArgs {
+  int o, v;
+  int i, j, k;
+  double w;  // gE * m / 3
+  const double* G;      // [3][v][v][v] for this triple
+  const double* ovs;    // [o][v][o][v]
+  const double* t1;     // [o][v]
+  const double* eps_o;
+  const double* eps_v;
+  double* dW;           // [v^3]
+  double* dY;           // [v^3]
+  double* dD;           // [v^3]
+  double* epart;        // per-block partial energies (unweighted by gE: m/3 e)
+};
+
+__device__ __forceinline__ double wt_at(const AdjArgs& A, int x, int y, int z) {
+  const int64_t v = A.v, v2 = v * v, v3 = v2 * v;
+  return A.G[(x * v + y) * v + z] + A.G[v3 + (y * v + z) * v + x] + A.G[2 * v3 + (z * v + x) * v + y];
+}
+
+__device__ __forceinline__ double y_at(const AdjArgs& A, int x, int y, int z) {
+  const int64_t v = A.v, o = A.o;
+  auto ovs = [&](int P1, int a, int P2, int b) { return A.ovs[(((int64_t)P1 * v + a) * o + P2) * v + b]; };
+  return ovs(A.i, x, A.j, y) * A.t1[(int64_t)A.k * v + z] + ovs(A.j, y, A.k, z) * A.t1[(int64_t)A.i * v + x] +
+         ovs(A.i, x, A.k, z) * A.t1[(int64_t)A.j * v + y];
+}
+
+__global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
+  __shared__ double red[8];
+  const int64_t v = A.v, v3 = v * v * v;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (e < v3) {
+    const int a = (int)(e / (v * v)), b = (int)((e / v) % v), c = (int)(e % v);
+    // positions abc, acb, bac, bca, cab, cba
+    const double W0 = wt_at(A, a, b, c), W1 = wt_at(A, a, c, b), W2 = wt_at(A, b, a, c);
+    const double W3 = wt_at(A, b, c, a), W4 = wt_at(A, c, a, b), W5 = wt_at(A, c, b, a);
+    const double Y0 = y_at(A, a, b, c), Y1 = y_at(A, a, c, b), Y2 = y_at(A, b, a, c);
+    const double Y3 = y_at(A, b, c, a), Y4 = y_at(A, c, a, b), Y5 = y_at(A, c, b, a);
+    // R at position abc: 4 X_abc + X_bca + X_cab - 2 (X_cba + X_acb + X_bac)
+    auto R0 = [](double x0, double x1, double x2, double x3, double x4, double x5) {
+      return (4.0 * x0 - 2.0 * x5 - 2.0 * x1) + (x3 + x4 - 2.0 * x2);
+    };
+    const double D = (A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k]) - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
+    const double RW = R0(W0, W1, W2, W3, W4, W5);
+    const double RY = R0(Y0, Y1, Y2, Y3, Y4, Y5);
+    const double RV = RW + RY;
+    A.dW[e] = A.w * (2.0 * RW + RY) / D;
+    A.dY[e] = A.w * RW / D;
+    A.dD[e] = -A.w * W0 * RV / (D * D);
+    contrib = W0 * RV / D;
+  }
+  for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = contrib;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    A.epart[blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// generic strided float64 GEMM:  C[m,n] += alpha sum_k A[m,k] B[k,n]
+// m = (m1, m2), k = (k1, k2), each index with its own stride
+// ---------------------------------------------------------------------------
+
+struct GemmView {
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t M1, M2, N, K1, K2;
+  int64_t a_m1, a_m2, a_k1, a_k2;
+  int64_t b_k1, b_k2, b_n;
+  int64_t c_m1, c_m2, c_n;
+  double alpha;
+};
+
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_strided(GemmView g) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int tid = threadIdx.x;
+  const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
+  const int64_t m0 = (int64_t)blockIdx.x * GT, n0 = (int64_t)blockIdx.y * GT;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  // loader: 64 rows (m or n) x 16 k
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  const int64_t am = m0 + lr;
+  const bool am_ok = am < M;
+  const int64_t a_row = am_ok ? (am / g.M2) * g.a_m1 + (am % g.M2) * g.a_m2 : 0;
+  const int64_t bn = n0 + lr;
+  const bool bn_ok = bn < g.N;
+  const int64_t b_col = bn_ok ? bn * g.b_n : 0;
+  for (int64_t k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t kk = k0 + lk + u;
+      const bool k_ok = kk < K;
+      const int64_t k1 = k_ok ? kk / g.K2 : 0, k2 = k_ok ? kk % g.K2 : 0;
+      As[lk + u][lr] = (am_ok && k_ok) ? g.A[a_row + k1 * g.a_k1 + k2 * g.a_k2] : 0.0;
+      Bs[lk + u][lr] = (bn_ok && k_ok) ? g.B[b_col + k1 * g.b_k1 + k2 * g.b_k2] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t m = m0 + ty * 4 + a;
+    if (m >= M) continue;
+    const int64_t crow = (m / g.M2) * g.c_m1 + (m % g.M2) * g.c_m2;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t n = n0 + tx * 4 + b;
+      if (n < g.N) g.C[crow + n * g.c_n] += g.alpha * acc[a][b];
+    }
+  }
+}
+
+static cudaError_t gemm(const GemmView& g, cudaStream_t s) {
+  const int64_t M = g.M1 * g.M2;
+  dim3 grid((unsigned)((M + GT - 1) / GT), (unsigned)((g.N + GT - 1) / GT));
+  k_gemm_strided<<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Y and denominator reductions for one triple
+// ---------------------------------------------------------------------------
+
+// dOVS[P1][x][P2][y] += sum_z dY[perm(x,y,z)] t1[P3][z]   (one of the three Y terms)
+// mode 0: ovs(i,a,j,b) t1(k,c): out (a,b), sum over c; t1 row k
+// mode 1: ovs(j,b,k,c) t1(i,a): out (b,c), sum over a; t1 row i
+// mode 2: ovs(i,a,k,c) t1(j,b): out (a,c), sum over b; t1 row j
+__global__ void k_dovs(int mode, int o, int v, int i, int j, int k, const double* __restrict__ dY,
+                       const double* __restrict__ t1, double* __restrict__ dOVS) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)v * v) return;
+  const int x = (int)(idx / v), y = (int)(idx % v);
+  const int64_t V = v;
+  double s = 0.0;
+  int P1, P2, P3;
+  if (mode == 0) {
+    P1 = i; P2 = j; P3 = k;
+    for (int c = 0; c < v; ++c) s += dY[(x * V + y) * V + c] * t1[(int64_t)P3 * v + c];
+  } else if (mode == 1) {
+    P1 = j; P2 = k; P3 = i;
+    for (int a = 0; a < v; ++a) s += dY[(a * V + x) * V + y] * t1[(int64_t)P3 * v + a];
+  } else {
+    P1 = i; P2 = k; P3 = j;
+    for (int b = 0; b < v; ++b) s += dY[(x * V + b) * V + y] * t1[(int64_t)P3 * v + b];
+  }
+  dOVS[(((int64_t)P1 * v + x) * o + P2) * v + y] += s;
+}
+
+// dt1[P3][z] += sum over the other two indices of dY * ovs (one of the three Y terms)
+__global__ void k_dt1(int mode, int o, int v, int i, int j, int k, const double* __restrict__ dY,
+                      const double* __restrict__ ovs, double* __restrict__ dt1) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= v) return;
+  const int64_t V = v;
+  auto OV = [&](int P1, int a, int P2, int b) { return ovs[(((int64_t)P1 * v + a) * o + P2) * v + b]; };
+  double s = 0.0;
+  if (mode == 0) {  // t1(k,c): sum over a,b of dY[a,b,c] ovs(i,a,j,b)
+    for (int a = 0; a < v; ++a)
+      for (int b = 0; b < v; ++b) s += dY[(a * V + b) * V + z] * OV(i, a, j, b);
+    dt1[(int64_t)k * v + z] += s;
+  } else if (mode == 1) {  // t1(i,a): sum over b,c of dY[a,b,c] ovs(j,b,k,c)
+    for (int b = 0; b < v; ++b)
+      for (int c = 0; c < v; ++c) s += dY[(z * V + b) * V + c] * OV(j, b, k, c);
+    dt1[(int64_t)i * v + z] += s;
+  } else {  // t1(j,b): sum over a,c of dY[a,b,c] ovs(i,a,k,c)
+    for (int a = 0; a < v; ++a)
+      for (int c = 0; c < v; ++c) s += dY[(a * V + z) * V + c] * OV(i, a, k, c);
+    dt1[(int64_t)j * v + z] += s;
+  }
+}
+
+// deps_v[x] -= sum_bc dD[x,b,c] + sum_ac dD[a,x,c] + sum_ab dD[a,b,x]
+__global__ void k_deps_v(int v, const double* __restrict__ dD, double* __restrict__ deps_v) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= v) return;
+  const int64_t V = v;
+  double s = 0.0;
+  for (int p = 0; p < v; ++p)
+    for (int q = 0; q < v; ++q)
+      s += dD[(x * V + p) * V + q] + dD[(p * V + x) * V + q] + dD[(p * V + q) * V + x];
+  deps_v[x] -= s;
+}
+
+// deps_o[i], [j], [k] += sum_abc dD (fixed-order block sum)
+__global__ void __launch_bounds__(1024) k_deps_o(int64_t n, const double* __restrict__ dD, int i, int j, int k,
+                                                  double* __restrict__ deps_o) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += dD[e];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    deps_o[i] += t;
+    deps_o[j] += t;
+    deps_o[k] += t;
+  }
+}
+
+// dovov[P1,x,P2,y] = (dOVS[P1,x,P2,y] + dOVS[P2,y,P1,x]) / 2
+__global__ void k_dovov(int o, int v, const double* __restrict__ dOVS, double* __restrict__ dovov) {
+  const int64_t n = (int64_t)o * v * o * v;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(idx % v);
+    int64_t rest = idx / v;
+    const int P2 = (int)(rest % o);
+    rest /= o;
+    const int x = (int)(rest % v);
+    const int P1 = (int)(rest / v);
+    dovov[idx] = 0.5 * (dOVS[idx] + dOVS[(((int64_t)P2 * v + y) * o + P1) * v + x]);
+  }
+}
+
+// sum of the adjoint kernel's per-block partials -> one per-triple share
+__global__ void __launch_bounds__(256) k_sum_share(const double* __restrict__ part, int64_t n, double scale,
+                                                    double* __restrict__ out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += part[e];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    *out = t * scale;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// driver
+// ---------------------------------------------------------------------------
+
+struct VjpWork {
+  double *t2L, *nooT, *ovs, *G, *dW, *dY, *dD, *dOVS, *epart, *shares;
+};
+
+size_t vjp_fp64_bytes(int64_t o, int64_t v) {
+  const int64_t v3 = v * v * v, nt = num_unique_triples(o);
+  const int64_t nblk = (v3 + 255) / 256;
+  auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
+  return a(o * v * v * o) + a(o * o * v * o) + a(o * v * o * v) + a(3 * v3) + 3 * a(v3) + a(o * v * o * v) +
+         a(nblk) + a(std::max<int64_t>(1, nt)) + 1024;
+}
+
+te_status ensure_workspace_public(Handle* h, size_t bytes);
+te_status ensure_triples_public(Handle* h, int nocc);
+
+te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
+                       cudaStream_t s) {
+  const int o = (int)c->nocc, v = (int)c->nvir;
+  const int64_t v2 = (int64_t)v * v, v3 = v2 * v, nt = num_unique_triples(o);
+  te_status st = ensure_workspace_public(h, vjp_fp64_bytes(o, v));
+  if (st != TE_OK) return st;
+  st = ensure_triples_public(h, o);
+  if (st != TE_OK) return st;
+  char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 255) & ~uintptr_t(255));
+  auto take = [&](int64_t n) {
+    double* r = reinterpret_cast<double*>(p);
+    p += ((size_t)n * 8 + 255) & ~size_t(255);
+    return r;
+  };
+  VjpWork W;
+  W.t2L = take((int64_t)o * v * v * o);
+  W.nooT = take((int64_t)o * o * v * o);
+  W.ovs = take((int64_t)o * v * o * v);
+  W.G = take(3 * v3);
+  W.dW = take(v3);
+  W.dY = take(v3);
+  W.dD = take(v3);
+  W.dOVS = take((int64_t)o * v * o * v);
+  const int64_t nblk = (v3 + 255) / 256;
+  W.epart = take(nblk);
+  W.shares = take(std::max<int64_t>(1, nt));
+
+  // gradient outputs start at zero
+  auto zero = [&](double* ptr, int64_t n) {
+    return ptr ? cudaMemsetAsync(ptr, 0, sizeof(double) * n, s) : cudaSuccess;
+  };
+  cudaError_t e = cudaSuccess;
+  e = e ? e : zero(g->eps_o, o);
+  e = e ? e : zero(g->eps_v, v);
+  e = e ? e : zero(g->ovvv, (int64_t)o * v3);
+  e = e ? e : zero(g->ooov, (int64_t)o * o * o * v);
+  e = e ? e : zero(g->ovov, (int64_t)o * v * o * v);
+  e = e ? e : zero(g->t1, (int64_t)o * v);
+  e = e ? e : zero(g->t2, (int64_t)o * o * v2);
+  e = e ? e : zero(W.dOVS, (int64_t)o * v * o * v);
+  if (e != cudaSuccess) return fail(TE_ECUDA, "memset: %s", cudaGetErrorString(e));
+
+  Prepared P{};
+  P.o = o;
+  P.v = v;
+  P.eps_o = c->eps_o;
+  P.eps_v = c->eps_v;
+  P.ovvv = c->ovvv;
+  P.t2 = c->t2;
+  P.t1 = c->t1;
+  P.t2L = W.t2L;
+  P.nooT = W.nooT;
+  P.ovs = W.ovs;
+  e = launch_prep_fp64(c, &P, s);
+  if (e != cudaSuccess) return fail(TE_ECUDA, "prep: %s", cudaGetErrorString(e));
+
+  std::vector<Triple> trip = unique_triples(o);
+  for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
+    const Triple T = trip[t];
+    e = launch_gemm_fp64(&P, h->d_triples, t, 1, W.G, s);
+    if (e != cudaSuccess) break;
+    AdjArgs A;
+    A.o = o; A.v = v; A.i = T.i; A.j = T.j; A.k = T.k;
+    A.w = gE * (double)T.m / 3.0;
+    A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v;
+    A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart;
+    k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
+    k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
+    h->n_launches += 3;
+    // back-propagation through the three G blocks; Gamma_g is a strided view of dW~
+    for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
+      int pp, qq, rr;
+      if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
+      else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
+      else { pp = T.k; qq = T.i; rr = T.j; }
+      // Gamma[x,y,z] strides (gx, gy, gz)
+      int64_t gx, gy, gz;
+      if (gi == 0) { gx = v2; gy = v; gz = 1; }        // dW~[x,y,z]
+      else if (gi == 1) { gx = v; gy = 1; gz = v2; }   // dW~[z,x,y]
+      else { gx = 1; gy = v2; gz = v; }                // dW~[y,z,x]
+      const double* t2rq = c->t2 + ((int64_t)rr * o + qq) * v2;
+      const double* t2rp = c->t2 + ((int64_t)rr * o + pp) * v2;
+      auto run = [&](GemmView gv) {
+        if (e == cudaSuccess) {
+          e = gemm(gv, s);
+          ++h->n_launches;
+        }
+      };
+      if (g->ovvv) {
+        // (a) dovvv[p,x,y,d] += sum_z G[x,y,z] t2[r,q,z,d]
+        run(GemmView{W.dW, t2rq, g->ovvv + (int64_t)pp * v3, v, v, v, v, 1, gx, gy, gz, 0, v, 0, 1, v2, v, 1, 1.0});
+        // (b) dovvv[q,y,x,d] += sum_z G[x,y,z] t2[r,p,z,d]
+        run(GemmView{W.dW, t2rp, g->ovvv + (int64_t)qq * v3, v, v, v, v, 1, gx, gy, gz, 0, v, 0, 1, v, v2, 1, 1.0});
+      }
+      if (g->t2) {
+        // (c) dt2[r,q,z,d] += sum_xy G[x,y,z] ovvv[p,x,y,d]
+        run(GemmView{W.dW, c->ovvv + (int64_t)pp * v3, g->t2 + ((int64_t)rr * o + qq) * v2, v, 1, v, v, v, gz, 0,
+                     gx, gy, v2, v, 1, v, 0, 1, 1.0});
+        // (d) dt2[r,p,z,d] += sum_xy G[x,y,z] ovvv[q,y,x,d]
+        run(GemmView{W.dW, c->ovvv + (int64_t)qq * v3, g->t2 + ((int64_t)rr * o + pp) * v2, v, 1, v, v, v, gz, 0,
+                     gx, gy, v, v2, 1, v, 0, 1, 1.0});
+        // (e) dt2[l,p,y,x] -= sum_z G[x,y,z] ooov[q,l,r,z]
+        run(GemmView{W.dW, c->ooov + ((int64_t)qq * o * o + rr) * v, g->t2 + (int64_t)pp * v2, v, v, o, v, 1, gx,
+                     gy, gz, 0, 1, 0, (int64_t)o * v, 1, v, (int64_t)o * v2, -1.0});
+        // (g) dt2[l,q,x,y] -= sum_z G[x,y,z] ooov[p,l,r,z]
+        run(GemmView{W.dW, c->ooov + ((int64_t)pp * o * o + rr) * v, g->t2 + (int64_t)qq * v2, v, v, o, v, 1, gx,
+                     gy, gz, 0, 1, 0, (int64_t)o * v, v, 1, (int64_t)o * v2, -1.0});
+      }
+      if (g->ooov) {
+        // (f) dooov[q,l,r,z] -= sum_xy t2[l,p,y,x] G[x,y,z]
+        run(GemmView{c->t2 + (int64_t)pp * v2, W.dW, g->ooov + ((int64_t)qq * o * o + rr) * v, o, 1, v, v, v,
+                     (int64_t)o * v2, 0, 1, v, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0});
+        // (h) dooov[p,l,r,z] -= sum_xy t2[l,q,x,y] G[x,y,z]
+        run(GemmView{c->t2 + (int64_t)qq * v2, W.dW, g->ooov + ((int64_t)pp * o * o + rr) * v, o, 1, v, v, v,
+                     (int64_t)o * v2, 0, v, 1, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0});
+      }
+    }
+    if (e != cudaSuccess) break;
+    // disconnected term and denominators
+    const unsigned gb2 = (unsigned)((v2 + 255) / 256), gb1 = (unsigned)((v + 127) / 128);
+    for (int mode = 0; mode < 3; ++mode) {
+      if (g->ovov) k_dovs<<<gb2, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, c->t1, W.dOVS);
+      if (g->t1) k_dt1<<<gb1, 128, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
+    }
+    if (g->eps_v) k_deps_v<<<gb1, 128, 0, s>>>(v, W.dD, g->eps_v);
+    if (g->eps_o) k_deps_o<<<1, 1024, 0, s>>>(v3, W.dD, T.i, T.j, T.k, g->eps_o);
+    h->n_launches += 8;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && g->ovov) {
+    k_dovov<<<1024, 256, 0, s>>>(o, v, W.dOVS, g->ovov);
+    ++h->n_launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && e_out) {
+    e = launch_reduce_total(W.shares, nt, e_out, s);
+    ++h->n_launches;
+  }
+  if (e != cudaSuccess) return fail(TE_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
+  return TE_OK;
+}
+
+}  // namespace te

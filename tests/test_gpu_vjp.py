@@ -1,0 +1,113 @@
+"""Adjoint of E(T) (t_energy_vjp) through the C ABI.
+
+* element by element against the oracle's reverse-mode gradient, on ragged
+  shapes with unsorted orbital energies and on the o8v40 workload;
+* Euler identities (E is homogeneous of degree 4 in the integrals and
+  amplitudes together and of degree -1 in the orbital energies);
+* central differences of the float64 GPU energy along a random direction;
+* the autograd Function's backward is the same adjoint."""
+import numpy as np
+import pytest
+import torch
+
+import tegen
+from oracle import t_energy as O
+from gpu_common import need_gpu, shuffled
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
+AMPS = ("ovvv", "ooov", "ovov", "t1", "t2")
+
+
+@pytest.fixture(scope="module")
+def te():
+    return need_gpu()
+
+
+def dev(arrs):
+    return {n: torch.as_tensor(np.ascontiguousarray(arrs[n])).cuda() for n in NAMES}
+
+
+def assert_grads_close(g, ref, rtol=1e-10):
+    for n in NAMES:
+        a = g[n].cpu().numpy()
+        b = ref[n].numpy() if isinstance(ref[n], torch.Tensor) else ref[n]
+        scale = max(float(np.max(np.abs(b))), 1e-300)
+        err = float(np.max(np.abs(a - b)))
+        assert err <= rtol * scale, (n, err, scale)
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 1), (3, 7, 2), (4, 12, 3), (5, 17, 4), (3, 70, 5), (2, 131, 6)])
+def test_matches_oracle_gradient(te, o, v, seed):
+    cl = tegen.make_cluster(o, v, 4 * (o + v), seed)
+    arrs = shuffled(cl.arrays(), seed)
+    arrs["t1"] = arrs["t1"] * 50.0
+    e_ref, g_ref = O.t_energy_grad(O.inputs(**arrs))
+    e, g = te.t_energy_vjp(dev(arrs))
+    assert abs(float(e) - e_ref) <= 1e-12 * abs(e_ref) + 1e-15
+    assert_grads_close(g, g_ref)
+
+
+def test_o8v40_matches_oracle_gradient(te):
+    cl = tegen.make_cluster(*tegen.WORKLOADS["o8v40"])
+    arrs = cl.arrays()
+    e_ref, g_ref = O.t_energy_grad(O.inputs(**arrs))
+    e, g = te.t_energy_vjp(dev(arrs), gE=-0.75)
+    assert abs(float(e) - e_ref) <= 1e-12 * abs(e_ref)
+    assert_grads_close(g, {n: -0.75 * g_ref[n] for n in NAMES})
+
+
+def test_single_occupied_orbital_gives_zero(te):
+    cl = tegen.make_cluster(1, 9, 40, 3)
+    e, g = te.t_energy_vjp(dev(cl.arrays()))
+    assert float(e) == 0.0
+    for n in NAMES:
+        assert float(g[n].abs().max()) == 0.0, n
+
+
+def test_euler_identities(te):
+    cl = tegen.make_cluster(6, 48, 216, 11)
+    a = dev(cl.arrays())
+    e, g = te.t_energy_vjp(a)
+    e = float(e)
+    deg4 = sum(float((a[n] * g[n]).sum()) for n in AMPS)
+    degm1 = sum(float((a[n] * g[n]).sum()) for n in ("eps_o", "eps_v"))
+    assert abs(deg4 - 4.0 * e) <= 1e-11 * abs(e)
+    assert abs(degm1 + e) <= 1e-11 * abs(e)
+
+
+def test_directional_central_difference(te):
+    cl = tegen.make_cluster(6, 48, 216, 12)
+    a = dev(cl.arrays())
+    _, g = te.t_energy_vjp(a)
+    gen = torch.Generator().manual_seed(5)
+    d = {n: (torch.randn(a[n].shape, generator=gen, dtype=torch.float64) * a[n].abs().mean().cpu()).cuda()
+         for n in NAMES}
+    h = 1e-4
+    ep = float(te.t_energy({n: a[n] + h * d[n] for n in NAMES}, "fp64"))
+    em = float(te.t_energy({n: a[n] - h * d[n] for n in NAMES}, "fp64"))
+    fd = (ep - em) / (2 * h)
+    an = sum(float((g[n] * d[n]).sum()) for n in NAMES)
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_deterministic_and_mode_independent(te):
+    cl = tegen.make_cluster(4, 24, 96, 2)
+    a = dev(cl.arrays())
+    e0, g0 = te.t_energy_vjp(a)
+    e1, g1 = te.t_energy_vjp(a, precision="ozaki")
+    assert float(e0) == float(e1)
+    for n in NAMES:
+        assert torch.equal(g0[n], g1[n]), n
+
+
+def test_autograd_function_uses_the_adjoint(te):
+    cl = tegen.make_cluster(3, 20, 92, 4)
+    a = dev(cl.arrays())
+    leaves = [a[n].clone().requires_grad_(True) for n in NAMES]
+    E = te.TEnergy.apply(*leaves, "fp64")
+    (2.0 * E).backward()
+    _, g = te.t_energy_vjp(a, gE=2.0)
+    for n, leaf in zip(NAMES, leaves):
+        torch.testing.assert_close(leaf.grad, g[n], rtol=1e-13, atol=0)
