@@ -80,10 +80,13 @@ def test_matches_slice_model_o16v120(te):
     sh = te.t_energy_triples(a, precision="ozaki").cpu().numpy()
     ref64 = te.t_energy_triples(a, precision="fp64").cpu().numpy()
     picks = list(np.argsort(np.abs(ref64))[-4:]) + [0, 137, 401]
+    # the approximate level-4/5 accumulator and the float32 Y carry errors
+    # relative to the largest products, hence the absolute floor
+    floor = 1e-12 * float(np.max(np.abs(ref64)))
     worst_scheme = 0.0
     for t in picks:
         m = model_share(arrs, *tri[t])
-        assert abs(sh[t] - m) <= 1e-9 * abs(m) + 1e-16, (t, tri[t], sh[t], m)
+        assert abs(sh[t] - m) <= 1e-9 * abs(m) + floor, (t, tri[t], sh[t], m)
         worst_scheme = max(worst_scheme, abs(m - ref64[t]) / abs(ref64[t]))
     # the model is not the float64 value: the comparison above is not vacuous
     assert worst_scheme > 1e-9
