@@ -207,6 +207,17 @@ const char* te_last_error(void);
  * later launches on this handle; 0 restores the default (4 s). */
 te_status te_set_wait_limit_ns(te_handle h, uint64_t ns);
 
+/* Slice width of TE_OZAKI for later calls on this handle.  bits = 0
+ * (default): 7-bit slices (four slices, ten slice products) when the K axis
+ * K = 2 (nvir + nocc) <= 1024, else 6-bit slices (five slices, fifteen
+ * products; K <= 4096).  bits = 7 or 6 forces one width (7 with K > 1024
+ * then fails with TE_EUNSUPPORTED).  6-bit slicing carries 30 bits of each
+ * operand instead of 28 and keeps one more level of slice products: about
+ * ten times more accurate, about 1.5 times the tensor work.  Sums of the
+ * level-0 and level-1 products are exact in either width: K products of at
+ * most 2^(2 bits) units stay below 2^24. */
+te_status te_set_ozaki_bits(te_handle h, int bits);
+
 /* Self-test of the device watchdog.  Launches on s one single-thread kernel
  * whose bounded wait is on a shared-memory mbarrier that nothing ever
  * arrives on; after limit_ns (1 ms .. 10 s, else TE_EINVAL) the wait gives

@@ -83,6 +83,11 @@ class Handle:
     def set_wait_limit_ns(self, ns: int):
         _lib.check(_lib.load().te_set_wait_limit_ns(self.ptr, int(ns)))
 
+    def set_ozaki_bits(self, bits: int):
+        """Slice width of the "ozaki" mode: 0 automatic (7-bit slices while
+        2 (nvir + nocc) <= 1024, else 6-bit), or 6 / 7 forced."""
+        _lib.check(_lib.load().te_set_ozaki_bits(self.ptr, int(bits)))
+
     def watchdog_selftest(self, limit_ns: int = 20_000_000, stream=None):
         """Launch a kernel whose bounded wait must expire after limit_ns; the
         next sync() raises TEnergyError with status TE_ETIMEOUT."""

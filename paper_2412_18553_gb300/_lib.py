@@ -49,6 +49,7 @@ SIGNATURES = [
     ("te_last_error", ctypes.c_char_p, []),
     ("te_set_wait_limit_ns", ctypes.c_int, [c_void_p, ctypes.c_uint64]),
     ("te_watchdog_selftest", ctypes.c_int, [c_void_p, ctypes.c_uint64, c_void_p]),
+    ("te_set_ozaki_bits", ctypes.c_int, [c_void_p, ctypes.c_int]),
     ("te_profile_enable", ctypes.c_int, [c_void_p, ctypes.c_int]),
     ("te_profile_read", ctypes.c_int, [c_void_p, ctypes.POINTER(TeProfile), ctypes.c_int]),
     ("t_energy_fp64_noalloc", ctypes.c_int, [ctypes.POINTER(TeCluster), c_void_p, c_void_p]),

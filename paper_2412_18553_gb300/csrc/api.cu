@@ -567,6 +567,18 @@ te_status te_profile_read(te_handle hh, te_profile* out, int reset) {
   return TE_OK;
 }
 
+te_status te_set_ozaki_bits(te_handle hh, int bits) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (bits != 0 && bits != 6 && bits != 7) return fail(TE_EINVAL, "slice width must be 0, 6 or 7 (got %d)", bits);
+  if (bits != h->ozaki_bits) {
+    DeviceGuard g(h->device);
+    drop_graphs(h);  // captured batches bake in the slice width
+    h->ozaki_bits = bits;
+  }
+  return TE_OK;
+}
+
 te_status te_set_wait_limit_ns(te_handle hh, uint64_t ns) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return fail(TE_EINVAL, "null handle");

@@ -37,27 +37,39 @@
 
 namespace te {
 
-enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2, TC_OZAKI = 3 };
+// TC_OZAKI: four 7-bit slices, ten slice products (K = 2 (v + o) <= 1024).
+// TC_OZAKI6: five 6-bit slices, fifteen slice products (K <= 4096); chosen
+// for the same user mode when the K axis is too long for 7-bit slices.
+enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2, TC_OZAKI = 3, TC_OZAKI6 = 4 };
 
-static int tc_mode_of(te_precision p) {
+constexpr int OZ_K_MAX7 = 1024;  // K * 2^14 < 2^24: exact level-2/3 sums with 7-bit slices
+constexpr int OZ_K_MAX6 = 4096;  // K * 2^12 < 2^24 with 6-bit slices
+
+// ozaki_bits: 0 = 7-bit slices when K allows, else 6-bit; 6 or 7 forces one.
+static int tc_mode_of(te_precision p, int o, int v, int ozaki_bits) {
   switch (p) {
     case TE_TF32: return TC_TF32;
     case TE_BF16X3: return TC_BF16X3;
     case TE_TF32X3: return TC_TF32X3;
-    default: return TC_OZAKI;
+    default:
+      if (ozaki_bits == 6) return TC_OZAKI6;
+      if (ozaki_bits == 7) return TC_OZAKI;
+      return 2 * (v + o) <= OZ_K_MAX7 ? TC_OZAKI : TC_OZAKI6;
   }
 }
+
+__host__ __device__ constexpr bool is_ozaki(int mode) { return mode == TC_OZAKI || mode == TC_OZAKI6; }
 
 template <int MODE>
 struct ModeTraits {
   static constexpr bool tf32 = (MODE == TC_TF32 || MODE == TC_TF32X3);
-  static constexpr int nparts = (MODE == TC_TF32) ? 1 : (MODE == TC_OZAKI ? 4 : 2);
-  static constexpr int nacc = (MODE == TC_OZAKI) ? 3 : 1;   // accumulators per tile
-  static constexpr int nbuf = (MODE == TC_OZAKI) ? 1 : 2;   // TMEM buffering
+  static constexpr int nparts = (MODE == TC_TF32) ? 1 : (MODE == TC_OZAKI ? 4 : (MODE == TC_OZAKI6 ? 5 : 2));
+  static constexpr int nacc = is_ozaki(MODE) ? 3 : 1;   // accumulators per tile
+  static constexpr int nbuf = is_ozaki(MODE) ? 1 : 2;   // TMEM buffering
+  static constexpr int beta = MODE == TC_OZAKI6 ? 6 : 7;  // bits per slice
 };
 
-constexpr int OZ_BETA = 7;    // bits per slice
-constexpr int OZ_SLICES = 4;
+constexpr int MAX_PARTS = 5;
 
 // ---------------------------------------------------------------------------
 // operand preparation
@@ -72,7 +84,7 @@ __device__ __forceinline__ double round_sig(double x) {
 }
 
 struct Parts {
-  void* p[4];
+  void* p[MAX_PARTS];
 };
 
 // Element `idx` of every part plane.  For OZAKI, `scale` is 2^-s of the array.
@@ -83,16 +95,17 @@ __device__ __forceinline__ void split_store(double x, const Parts& parts, int64_
     const double l = round_sig<8>(x - h);
     reinterpret_cast<__nv_bfloat16*>(parts.p[0])[idx] = __float2bfloat16_rn((float)h);
     reinterpret_cast<__nv_bfloat16*>(parts.p[1])[idx] = __float2bfloat16_rn((float)l);
-  } else if (MODE == TC_OZAKI) {
+  } else if (is_ozaki(MODE)) {
+    constexpr int BETA = ModeTraits<MODE>::beta, NS = ModeTraits<MODE>::nparts;
     double t = x * scale;  // |t| < 1, exact power-of-two scaling
 #pragma unroll
-    for (int k = 0; k < OZ_SLICES; ++k) {
-      t = t * (double)(1 << OZ_BETA);
+    for (int k = 0; k < NS; ++k) {
+      t = t * (double)(1 << BETA);
       const double m = rint(t);
       t = t - m;
-      // m 2^-7(k+1) is exact in BF16 (|m| <= 128)
+      // m 2^-BETA(k+1) is exact in BF16 (|m| <= 2^BETA)
       reinterpret_cast<__nv_bfloat16*>(parts.p[k])[idx] =
-          __float2bfloat16_rn((float)(m * (1.0 / (double)(1ull << (OZ_BETA * (k + 1))))));
+          __float2bfloat16_rn((float)(m * (1.0 / (double)(1ull << (BETA * (k + 1))))));
     }
   } else {
     const double h = round_sig<11>(x);
@@ -234,12 +247,12 @@ static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1,
 // ---------------------------------------------------------------------------
 
 struct TcMaps {
-  CUtensorMap a_nat[4];  // ovvv parts, dims (Kp, y, x, p): rows (x,y) of ovvv[p]
-  CUtensorMap a_tr[4];   // ovvv parts, dims (Kp, y, x, q) with strides swapped: ovvv[q,y,x,:]
-  CUtensorMap l_nat[4];  // t2L parts natural
-  CUtensorMap l_tr[4];   // t2L parts transposed
-  CUtensorMap b_t2[4];   // t2 parts, dims (Kp, z, q, r)
-  CUtensorMap b_noo[4];  // nooT parts, dims (Kp, z, r, p)
+  CUtensorMap a_nat[MAX_PARTS];  // ovvv parts, dims (Kp, y, x, p): rows (x,y) of ovvv[p]
+  CUtensorMap a_tr[MAX_PARTS];   // ovvv parts, dims (Kp, y, x, q) with strides swapped: ovvv[q,y,x,:]
+  CUtensorMap l_nat[MAX_PARTS];  // t2L parts natural
+  CUtensorMap l_tr[MAX_PARTS];   // t2L parts transposed
+  CUtensorMap b_t2[MAX_PARTS];   // t2 parts, dims (Kp, z, q, r)
+  CUtensorMap b_noo[MAX_PARTS];  // nooT parts, dims (Kp, z, r, p)
 };
 
 struct TcParams {
@@ -476,18 +489,21 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
                 bd[k] = ptx::smem_desc(b0 + k * P.b_part_bytes + ks * 32, sbo, lay);
               }
               const uint32_t acc_in = first ? 0u : 1u;
-              if constexpr (MODE == TC_OZAKI) {
+              if constexpr (is_ozaki(MODE)) {
+                // slice products a_i b_j with i + j <= NPART - 1: level i + j = 0 and
+                // level 1 each in an exact accumulator, the higher levels in a third
                 const uint32_t d2 = d_tmem, d3 = d_tmem + P.NT, dr = d_tmem + 2 * P.NT;
-                ptx::mma<false>(d2, ad[0], bd[0], idesc, acc_in);  // level 2
-                ptx::mma<false>(d3, ad[0], bd[1], idesc, acc_in);  // level 3
+                ptx::mma<false>(d2, ad[0], bd[0], idesc, acc_in);
+                ptx::mma<false>(d3, ad[0], bd[1], idesc, acc_in);
                 ptx::mma<false>(d3, ad[1], bd[0], idesc, 1);
-                ptx::mma<false>(dr, ad[0], bd[2], idesc, acc_in);  // levels 4 and 5
-                ptx::mma<false>(dr, ad[1], bd[1], idesc, 1);
-                ptx::mma<false>(dr, ad[2], bd[0], idesc, 1);
-                ptx::mma<false>(dr, ad[0], bd[3], idesc, 1);
-                ptx::mma<false>(dr, ad[1], bd[2], idesc, 1);
-                ptx::mma<false>(dr, ad[2], bd[1], idesc, 1);
-                ptx::mma<false>(dr, ad[3], bd[0], idesc, 1);
+                uint32_t rin = acc_in;
+#pragma unroll
+                for (int lev = 2; lev < NPART; ++lev)
+#pragma unroll
+                  for (int i = 0; i <= lev; ++i) {
+                    ptx::mma<false>(dr, ad[i], bd[lev - i], idesc, rin);
+                    rin = 1;
+                  }
               } else {
                 ptx::mma<TF32>(d_tmem, ad[0], bd[0], idesc, acc_in);
                 if constexpr (NPART == 2) {
@@ -526,7 +542,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
     const int row = quad * 32 + lane;
     const int64_t v2 = (int64_t)P.v * P.v;
     float gscale = 1.f;
-    if (MODE == TC_OZAKI) gscale = ldexpf(1.f, P.exps[4]);
+    if (is_ozaki(MODE)) gscale = ldexpf(1.f, P.exps[4]);
     uint32_t acc = 0, acc_phase = 0;
     for (int64_t tt = blockIdx.x; tt < P.total_tiles; tt += gridDim.x) {
       const TileCoord c = decode_tile(P, tt);
@@ -544,14 +560,14 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
       // cube-major G: [slot][g][X][Y][Z][CW planes][512], swizzled rows (see energy_tc.h);
       // this row is (x, y) = (X*8 + xl, Y*8 + yl)
       const int nb = (P.v + 7) >> 3;
-      constexpr int CWF = (MODE == TC_OZAKI) ? 2 : 1;
+      constexpr int CWF = is_ozaki(MODE) ? 2 : 1;
       const int64_t cubebase = (((int64_t)(c.slot * 3 + c.g) * nb + (x >> 3)) * nb + (y >> 3)) * nb;
       const int roff = cube_row(x & 7, y & 7);
       const int zx = cube_zx(x & 7, y & 7);
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)(NACC * P.NT);
       for (int c0 = 0; c0 < P.NT; c0 += 16) {
         const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
-        if constexpr (MODE == TC_OZAKI) {
+        if constexpr (is_ozaki(MODE)) {
           float a2[16], a3[16], ar[16];
           ptx::tmem_ld16(tbase + c0, a2);
           ptx::tmem_ld16(tbase + P.NT + c0, a3);
@@ -659,10 +675,11 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
                         int force_nnt = 0) {
   TcPlan pl{};
   pl.mode = mode;
-  pl.es = (mode == TC_BF16X3 || mode == TC_OZAKI) ? 2 : 4;
-  pl.nparts = mode == TC_TF32 ? 1 : (mode == TC_OZAKI ? 4 : 2);
-  pl.cw = mode == TC_OZAKI ? 2 : 1;
-  const int nacc = mode == TC_OZAKI ? 3 : 1, nbuf = mode == TC_OZAKI ? 1 : 2;
+  const bool oz = is_ozaki(mode);
+  pl.es = (mode == TC_BF16X3 || oz) ? 2 : 4;
+  pl.nparts = mode == TC_TF32 ? 1 : (mode == TC_OZAKI ? 4 : (mode == TC_OZAKI6 ? 5 : 2));
+  pl.cw = oz ? 2 : 1;
+  const int nacc = oz ? 3 : 1, nbuf = oz ? 1 : 2;
   pl.vp = round_up(v, 16);
   pl.op = round_up(o, 16);
   pl.vq = round_up(v, 4);
@@ -693,7 +710,7 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.n_nt = (v + ntmax - 1) / ntmax;
   if (force_nnt >= pl.n_nt) pl.n_nt = force_nnt;
   pl.NT = round_up((v + pl.n_nt - 1) / pl.n_nt, 16);
-  pl.cbw = mode == TC_OZAKI ? 64 : 128;
+  pl.cbw = oz ? 64 : 128;
   pl.kw_elems = pl.cbw / pl.es;
   pl.kw_chunks = (pl.vp + pl.kw_elems - 1) / pl.kw_elems;
   const int obytes = pl.op * pl.es;
@@ -722,7 +739,7 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
 }
 
 struct TcBuffers {
-  void *a[4], *b[4], *l[4], *n[4];
+  void *a[MAX_PARTS], *b[MAX_PARTS], *l[MAX_PARTS], *n[MAX_PARTS];
   float *ovs32, *t1_32, *gbuf;
   double *eps_copy, *partials, *etri;
   unsigned long long* maxbits;
@@ -741,7 +758,7 @@ static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64
   const size_t es = (size_t)pl.es;
   const size_t na = (size_t)o * v * v * pl.vp, nb = (size_t)o * o * v * pl.vp;
   const size_t nl = (size_t)o * v * v * pl.op, nn = (size_t)o * o * v * pl.op;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < MAX_PARTS; ++k) {
     const bool use = k < pl.nparts;
     b->a[k] = use ? take(na * es) : nullptr;
     b->b[k] = use ? take(nb * es) : nullptr;
@@ -855,15 +872,15 @@ template <int MODE>
 static cudaError_t launch_prep_tc(const te_cluster* c, const TcPlan& pl, const TcBuffers& b, cudaStream_t s) {
   const int o = (int)c->nocc, v = (int)c->nvir;
   const int* ex = nullptr;
-  if (MODE == TC_OZAKI) {
+  if (is_ozaki(MODE)) {
     cudaMemsetAsync(b.maxbits, 0, 4 * 8, s);
     k_maxabs<<<1024, 256, 0, s>>>(c->ovvv, (int64_t)o * v * v * v, c->t2, (int64_t)o * o * v * v, c->ooov,
                                   (int64_t)o * o * o * v, b.maxbits);
     k_exponents<<<1, 1, 0, s>>>(b.maxbits, b.exps);
     ex = b.exps;
   }
-  const Parts A{{b.a[0], b.a[1], b.a[2], b.a[3]}}, B{{b.b[0], b.b[1], b.b[2], b.b[3]}};
-  const Parts Lp{{b.l[0], b.l[1], b.l[2], b.l[3]}}, N{{b.n[0], b.n[1], b.n[2], b.n[3]}};
+  const Parts A{{b.a[0], b.a[1], b.a[2], b.a[3], b.a[4]}}, B{{b.b[0], b.b[1], b.b[2], b.b[3], b.b[4]}};
+  const Parts Lp{{b.l[0], b.l[1], b.l[2], b.l[3], b.l[4]}}, N{{b.n[0], b.n[1], b.n[2], b.n[3], b.n[4]}};
   k_split_rows<MODE><<<gridn((int64_t)o * v * v * pl.vp), 256, 0, s>>>(c->ovvv, A, (int64_t)o * v * v, v, pl.vp,
                                                                        ex, 0);
   k_split_rows<MODE><<<gridn((int64_t)o * o * v * pl.vp), 256, 0, s>>>(c->t2, B, (int64_t)o * o * v, v, pl.vp,
@@ -885,7 +902,8 @@ static cudaError_t launch_gemm_tc(const Handle* h, const TcMaps& M, const TcPara
 }
 
 te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, size_t* bytes) {
-  const TcPlan pl = make_plan(h, (int)c->nocc, (int)c->nvir, tc_mode_of(p), num_unique_triples(c->nocc));
+  const TcPlan pl = make_plan(h, (int)c->nocc, (int)c->nvir, tc_mode_of(p, (int)c->nocc, (int)c->nvir, h->ozaki_bits),
+                              num_unique_triples(c->nocc));
   TcBuffers b;
   *bytes = tc_carve(nullptr, pl, c->nocc, c->nvir, energy_num_block_triples(c->nvir),
                     num_unique_triples(c->nocc), &b);
@@ -896,10 +914,11 @@ te_status ensure_workspace_public(Handle* h, size_t bytes);
 te_status ensure_triples_public(Handle* h, int nocc);
 
 te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream_t s) {
-  const int o = (int)c->nocc, v = (int)c->nvir, mode = tc_mode_of(p);
+  const int o = (int)c->nocc, v = (int)c->nvir, mode = tc_mode_of(p, o, v, h->ozaki_bits);
   const auto key = std::make_tuple(o, v, mode);
   if (h->tuned.count(key)) return TE_OK;
-  if (mode == TC_OZAKI && 2 * (v + o) > 1024) return TE_OK;  // run_tc reports it
+  if ((mode == TC_OZAKI6 && 2 * (v + o) > OZ_K_MAX6) || (mode == TC_OZAKI && 2 * (v + o) > OZ_K_MAX7))
+    return TE_OK;  // run_tc reports it
   const int64_t nt = num_unique_triples(o);
   if (nt == 0) return TE_OK;
   // candidate M tiles: padding within 15% of the least; candidate N splits: the fewest and one more
@@ -953,7 +972,8 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
       if (mode == TC_BF16X3) e = launch_prep_tc<TC_BF16X3>(c, pl, b, s);
       else if (mode == TC_TF32X3) e = launch_prep_tc<TC_TF32X3>(c, pl, b, s);
       else if (mode == TC_TF32) e = launch_prep_tc<TC_TF32>(c, pl, b, s);
-      else e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
+      else if (mode == TC_OZAKI) e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
+      else e = launch_prep_tc<TC_OZAKI6>(c, pl, b, s);
       prepped = true;
     }
     TcMaps M;
@@ -974,7 +994,8 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
       if (mode == TC_BF16X3) e = launch_gemm_tc<TC_BF16X3>(h, M, P, pl.smem, s);
       else if (mode == TC_TF32X3) e = launch_gemm_tc<TC_TF32X3>(h, M, P, pl.smem, s);
       else if (mode == TC_TF32) e = launch_gemm_tc<TC_TF32>(h, M, P, pl.smem, s);
-      else e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
+      else if (mode == TC_OZAKI) e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
+      else e = launch_gemm_tc<TC_OZAKI6>(h, M, P, pl.smem, s);
       cudaEventRecord(e1, s);
       h->n_launches += 1;
       if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
@@ -1003,15 +1024,16 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   te_status rs = get_encoder(st);
   if (rs != TE_OK) return rs;
   const int o = (int)c->nocc, v = (int)c->nvir;
-  const int mode = tc_mode_of(p);
+  const int mode = tc_mode_of(p, o, v, h->ozaki_bits);
   const int64_t ntri = num_unique_triples(o);
   const int64_t nt = t_end - t_begin;
   const TcPlan pl = make_plan(h, o, v, mode, nt);
   if (pl.stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
-  // exact level-2/3 sums: K * 2^14 (two products per level-3 term, each < 2^13) below 2^24
-  // exact level-2/3 sums: 2 (v + o) nonzero terms of at most 2^14 stay below 2^24
-  if (mode == TC_OZAKI && 2 * (v + o) > 1024)
-    return fail(TE_EUNSUPPORTED, "OZAKI mode needs 2 (nvir + nocc) <= 1024 for exact accumulation");
+  // exact level-0/1 sums: K = 2 (v + o) products of at most 2^(2 beta) units stay below 2^24
+  if (mode == TC_OZAKI6 && 2 * (v + o) > OZ_K_MAX6)
+    return fail(TE_EUNSUPPORTED, "OZAKI mode needs 2 (nvir + nocc) <= %d for exact accumulation", OZ_K_MAX6);
+  if (mode == TC_OZAKI && 2 * (v + o) > OZ_K_MAX7)
+    return fail(TE_EUNSUPPORTED, "7-bit OZAKI slices need 2 (nvir + nocc) <= %d (use 6-bit slices)", OZ_K_MAX7);
   const int64_t nbt = energy_num_block_triples(v);
   TcBuffers b;
   const size_t bytes = tc_carve(nullptr, pl, o, v, nbt, ntri, &b);
@@ -1026,8 +1048,9 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   if (mode == TC_BF16X3) e = launch_prep_tc<TC_BF16X3>(c, pl, b, s);
   else if (mode == TC_TF32X3) e = launch_prep_tc<TC_TF32X3>(c, pl, b, s);
   else if (mode == TC_TF32) e = launch_prep_tc<TC_TF32>(c, pl, b, s);
-  else e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
-  h->n_launches += mode == TC_OZAKI ? 8 : 6;
+  else if (mode == TC_OZAKI) e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
+  else e = launch_prep_tc<TC_OZAKI6>(c, pl, b, s);
+  h->n_launches += is_ozaki(mode) ? 8 : 6;
   if (e != cudaSuccess) return fail(TE_ECUDA, "operand split launch: %s", cudaGetErrorString(e));
 
   TcMaps M;
@@ -1081,7 +1104,7 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   EL.wait_ns = h->wait_limit_ns;
 
   double* out = e_tri_out ? e_tri_out : b.etri;
-  const double nprod = (mode == TC_TF32) ? 1.0 : (mode == TC_OZAKI ? 10.0 : 3.0);
+  const double nprod = (mode == TC_TF32) ? 1.0 : (mode == TC_OZAKI ? 10.0 : (mode == TC_OZAKI6 ? 15.0 : 3.0));
   const double kpad = 2.0 * pl.kw_chunks * pl.kw_elems + 2.0 * pl.ko_chunks * pl.ko_elems;
   for (int64_t t0 = t_begin; t0 < t_end; t0 += pl.nslots) {
     const int ns = (int)std::min<int64_t>(pl.nslots, t_end - t0);
@@ -1091,7 +1114,8 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
     if (mode == TC_BF16X3) e = launch_gemm_tc<TC_BF16X3>(h, M, P, pl.smem, s);
     else if (mode == TC_TF32X3) e = launch_gemm_tc<TC_TF32X3>(h, M, P, pl.smem, s);
     else if (mode == TC_TF32) e = launch_gemm_tc<TC_TF32>(h, M, P, pl.smem, s);
-    else e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
+    else if (mode == TC_OZAKI) e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
+    else e = launch_gemm_tc<TC_OZAKI6>(h, M, P, pl.smem, s);
     prof_end(h, pm, s);
     h->gemm_flops += 2.0 * nprod * (double)P.total_tiles * 128.0 * pl.NT * kpad;
     if (e == cudaSuccess) {

@@ -49,6 +49,7 @@ struct Handle {
   int cc_major = 0, cc_minor = 0;
   size_t smem_optin = 0;
   uint64_t wait_limit_ns = 4000000000ull;
+  int ozaki_bits = 0;                // exact-slice width: 0 automatic, 6 or 7
   unsigned int* d_err = nullptr;     // device error word
   // workspace (grows, never shrinks until destroy)
   void* ws = nullptr;
