@@ -52,3 +52,42 @@ def test_ozaki_whole_cluster_sampled_and_summed(te, case):
     for t, ref in zip(g["triple_index"], g["shares"]):
         assert abs(s[t] - ref) <= 1e-7, (t, s[t], ref)
     assert abs(float(np.sum(s)) - e) <= 1e-10 * abs(e)
+
+
+class _OvvvRows:
+    """The rows ovvv[p] the oracle reads for one triple, copied from the
+    device tensor the GPU path uses (the full array is 67 GB)."""
+
+    def __init__(self, dev_ovvv, rows):
+        self._rows = {p: dev_ovvv[p].double().cpu() for p in set(rows)}
+
+    def __getitem__(self, p):
+        return self._rows[int(p)]
+
+
+def test_o48v560_sampled_triples():
+    """nocc=48 nvir=560 (seed 7): K = 2 (v + o) = 1216 > 1024, so the
+    exact-slice mode runs with 6-bit slices.  ovvv is formed on the GPU by
+    the generator; the oracle reads the same values (row copies) for two
+    triples: the largest share (47,47,46) and a distinct-index triple."""
+    from oracle import t_energy as O
+    te = need_gpu()
+    o, v, naux, seed = tegen.WORKLOADS["o48v560"]
+    cl = tegen.make_cluster(o, v, naux, seed, device="cuda")
+    torch.cuda.empty_cache()
+    arrs = cl.arrays()
+    a = {n: (x if isinstance(x, torch.Tensor) else torch.as_tensor(np.ascontiguousarray(x)).cuda())
+         for n, x in arrs.items()}
+    tri = [(i, j, k) for i in range(o) for j in range(i + 1) for k in range(j + 1) if not (i == j == k)]
+    h = te.Handle(0)
+    for (i, j, k) in [(47, 47, 46), (40, 25, 3)]:
+        t = tri.index((i, j, k))
+        small = O.inputs(arrs["eps_o"], arrs["eps_v"], np.zeros((1, 1, 1, 1)), arrs["ooov"], arrs["ovov"],
+                         arrs["t1"], arrs["t2"])
+        small.ovvv = _OvvvRows(a["ovvv"], (i, j, k))
+        ref = float(O.triple_share(small, i, j, k))
+        e64 = float(te.t_energy_triples(a, t, t + 1, precision="fp64", handle=h)[0])
+        eoz = float(te.t_energy_triples(a, t, t + 1, precision="ozaki", handle=h)[0])
+        h.sync()
+        assert abs(e64 - ref) <= 1e-12 * max(1.0, abs(ref)), ((i, j, k), e64, ref)
+        assert abs(eoz - ref) <= 1e-7, ((i, j, k), eoz, ref)
