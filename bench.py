@@ -182,7 +182,9 @@ def main():
     F = te.flop_count(o, v)
     h = te.Handle(local)
     prec = args.precision
-    nprod = {"fp64": 1, "tf32": 1, "bf16x3": 3, "tf32x3": 3}.get(prec, 10)
+    # slice products per output of the contraction: 10 for 7-bit exact slices,
+    # 15 for 6-bit (chosen when K = 2 (nvir + nocc) > 1024)
+    nprod = {"fp64": 1, "tf32": 1, "bf16x3": 3, "tf32x3": 3}.get(prec, 10 if 2 * (v + o) <= 1024 else 15)
 
     def barrier():
         if world > 1:
@@ -300,14 +302,14 @@ def main():
         roof = None
     else:
         bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        peak = bf16 if prec in ("bf16x3",) or nprod == 10 else bf16 * (1.1 / 2.25)
+        peak = bf16 if prec in ("bf16x3", "ozaki") else bf16 * (1.1 / 2.25)
         gemm_avg_ms = prof["gemm_ms"] / max(1, prof["gemm_launches"])
         alg_per_launch = nprod * F * args.steps / max(1, prof["gemm_launches"])
         achieved = alg_per_launch / (gemm_avg_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "k_gemm_tc", "peak_source": f"{pk_src} bf16 sustained"
-                + ("" if prec == "bf16x3" or nprod == 10 else " x 1.1/2.25 (tf32)"),
+                + ("" if prec in ("bf16x3", "ozaki") else " x 1.1/2.25 (tf32)"),
                 "gemm_share_of_step": prof["gemm_ms"] / max(1e-9, ms),
                 "energy_share_of_step": prof["energy_ms"] / max(1e-9, ms)}
 
