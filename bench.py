@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--check-triples", type=int, default=8,
                     help="triples checked against the FP64 GPU path for |dE|")
     ap.add_argument("--cpu-triples", type=int, default=2)
+    ap.add_argument("--no-vjp", action="store_true",
+                    help="skip the adjoint measurement (nocc=16 nvir=120, float64)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched measurement (16 clusters, nocc 8..20, nvir = 8 nocc)")
     return ap.parse_args()
@@ -297,6 +299,35 @@ def main():
                  "ms_per_batch": bms, "graph": True}
         del bdev
 
+    # adjoint: gradient of E(T) for the nocc=16 nvir=120 cluster (seed 3), float64
+    vjp = None
+    if not args.no_vjp:
+        import tegen
+        oq, vq, nq, sq = tegen.WORKLOADS["o16v120"]
+        cq = tegen.make_cluster(oq, vq, nq, sq)
+        qa = {n: torch.as_tensor(np.ascontiguousarray(x)).to(torch.device("cuda", local)) for n, x in cq.arrays().items()}
+        tiny = tegen.make_cluster(2, 8, 40, 0)
+        te.t_energy_vjp({n: torch.as_tensor(x).cuda(local) for n, x in tiny.arrays().items()}, handle=h)
+        torch.cuda.synchronize()
+        barrier()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        l0 = h.profile_read(reset=False)["launches"]
+        v0.record()
+        ev, _g = te.t_energy_vjp(qa, handle=h)
+        v1.record()
+        torch.cuda.synchronize()
+        vms = v0.elapsed_time(v1)
+        vt = torch.tensor([vms], device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(vt, op=torch.distributed.ReduceOp.MAX)
+        vms = float(vt.item())
+        Fq = te.flop_count(oq, vq)
+        vjp = {"workload": f"o16v120: nocc={oq} nvir={vq} naux={nq} seed={sq}", "precision": "fp64",
+               "ms": vms, "gflops_3F": world * 3 * Fq / (vms / 1e3) / 1e9, "e_t_ha": float(ev),
+               "launches": h.profile_read(reset=False)["launches"] - l0}
+        del qa, _g
+
     pk, pk_src = peaks()
     if prec == "fp64":
         roof = None
@@ -334,6 +365,7 @@ def main():
                "gpu_launches": prof["launches"],
                "profile": prof,
                "batch16": batch,
+               "vjp": vjp,
                "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
         print(json.dumps(out))
     if world > 1:

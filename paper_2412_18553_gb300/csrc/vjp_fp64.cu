@@ -89,7 +89,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
 
 // ---------------------------------------------------------------------------
 // generic strided float64 GEMM:  C[m,n] += alpha sum_k A[m,k] B[k,n]
-// m = (m1, m2), k = (k1, k2), each index with its own stride
+// m = (m1, m2), k = (k1, k2), each index with its own stride.  Outputs with
+// few tiles (the contractions over a virtual pair, K = v^2) split K over
+// blockIdx.z into fixed ranges; the partial tiles go to a scratch array and
+// are added in split order by k_splitk_add, so the result is deterministic.
 // ---------------------------------------------------------------------------
 
 struct GemmView {
@@ -105,34 +108,55 @@ struct GemmView {
 
 constexpr int GT = 64, GK = 16;
 
-__global__ void __launch_bounds__(256) k_gemm_strided(GemmView g) {
+// (k1, k2) of k = k1 K2 + k2, advanced by GK per step without division
+struct KCursor {
+  int k1, k2;
+  __device__ __forceinline__ void init(int k, int K2) {
+    k1 = k / K2;
+    k2 = k - k1 * K2;
+  }
+  __device__ __forceinline__ void step(int K2) {
+    k2 += GK;
+    while (k2 >= K2) {
+      k2 -= K2;
+      ++k1;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256) k_gemm_strided(GemmView g, int kchunk, double* __restrict__ part) {
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   const int tid = threadIdx.x;
-  const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
-  const int64_t m0 = (int64_t)blockIdx.x * GT, n0 = (int64_t)blockIdx.y * GT;
+  const int M = (int)(g.M1 * g.M2), K = (int)(g.K1 * g.K2), K2 = (int)g.K2;
+  const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
   const int tx = tid & 15, ty = tid >> 4;
   double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  // loader: 64 rows (m or n) x 16 k
+  // loader: 64 rows (m or n) x 16 k; thread (lr, lk .. lk+3)
   const int lr = tid >> 2, lk = (tid & 3) * 4;
-  const int64_t am = m0 + lr;
+  const int am = m0 + lr;
   const bool am_ok = am < M;
-  const int64_t a_row = am_ok ? (am / g.M2) * g.a_m1 + (am % g.M2) * g.a_m2 : 0;
-  const int64_t bn = n0 + lr;
-  const bool bn_ok = bn < g.N;
-  const int64_t b_col = bn_ok ? bn * g.b_n : 0;
-  for (int64_t k0 = 0; k0 < K; k0 += GK) {
+  const int64_t a_row = am_ok ? (int64_t)(am / (int)g.M2) * g.a_m1 + (int64_t)(am % (int)g.M2) * g.a_m2 : 0;
+  const int bn = n0 + lr;
+  const bool bn_ok = bn < (int)g.N;
+  const int64_t b_col = bn_ok ? (int64_t)bn * g.b_n : 0;
+  KCursor cur[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) cur[u].init(kb + lk + u, K2);
+  for (int k0 = kb; k0 < ke; k0 += GK) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int64_t kk = k0 + lk + u;
-      const bool k_ok = kk < K;
-      const int64_t k1 = k_ok ? kk / g.K2 : 0, k2 = k_ok ? kk % g.K2 : 0;
-      As[lk + u][lr] = (am_ok && k_ok) ? g.A[a_row + k1 * g.a_k1 + k2 * g.a_k2] : 0.0;
-      Bs[lk + u][lr] = (bn_ok && k_ok) ? g.B[b_col + k1 * g.b_k1 + k2 * g.b_k2] : 0.0;
+      const bool k_ok = k0 + lk + u < ke;
+      const int64_t ka = (int64_t)cur[u].k1 * g.a_k1 + (int64_t)cur[u].k2 * g.a_k2;
+      const int64_t kbo = (int64_t)cur[u].k1 * g.b_k1 + (int64_t)cur[u].k2 * g.b_k2;
+      As[lk + u][lr] = (am_ok && k_ok) ? g.A[a_row + ka] : 0.0;
+      Bs[lk + u][lr] = (bn_ok && k_ok) ? g.B[b_col + kbo] : 0.0;
+      cur[u].step(K2);
     }
     __syncthreads();
 #pragma unroll
@@ -151,21 +175,66 @@ __global__ void __launch_bounds__(256) k_gemm_strided(GemmView g) {
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const int64_t m = m0 + ty * 4 + a;
+    const int m = m0 + ty * 4 + a;
     if (m >= M) continue;
-    const int64_t crow = (m / g.M2) * g.c_m1 + (m % g.M2) * g.c_m2;
+    if (part) {  // split K: this split's tile, row-major [M][N]
+      double* prow = part + ((int64_t)blockIdx.z * M + m) * g.N;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int64_t n = n0 + tx * 4 + b;
-      if (n < g.N) g.C[crow + n * g.c_n] += g.alpha * acc[a][b];
+      for (int b = 0; b < 4; ++b) {
+        const int n = n0 + tx * 4 + b;
+        if (n < g.N) prow[n] = acc[a][b];
+      }
+    } else {
+      const int64_t crow = (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int n = n0 + tx * 4 + b;
+        if (n < g.N) g.C[crow + n * g.c_n] += g.alpha * acc[a][b];
+      }
     }
   }
 }
 
-static cudaError_t gemm(const GemmView& g, cudaStream_t s) {
-  const int64_t M = g.M1 * g.M2;
-  dim3 grid((unsigned)((M + GT - 1) / GT), (unsigned)((g.N + GT - 1) / GT));
-  k_gemm_strided<<<grid, 256, 0, s>>>(g);
+// C[m,n] += alpha sum_z part[z][m][n], z in order
+__global__ void k_splitk_add(GemmView g, int nsplit, const double* __restrict__ part) {
+  const int M = (int)(g.M1 * g.M2);
+  const int64_t MN = (int64_t)M * g.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += part[z * MN + e];
+    const int m = (int)(e / g.N), n = (int)(e % g.N);
+    const int64_t crow = (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2;
+    g.C[crow + n * g.c_n] += g.alpha * s;
+  }
+}
+
+// Split count for a GEMM of `tiles` output tiles and K steps: about two
+// blocks per SM, each split at least 8 K steps; the scratch holds `cap`
+// doubles.
+static int num_splits(int64_t tiles, int64_t K, int64_t MN, int num_sms, int64_t cap) {
+  const int64_t steps = (K + GK - 1) / GK;
+  int64_t want = (2LL * num_sms + tiles - 1) / tiles;
+  want = std::min<int64_t>(want, std::max<int64_t>(1, steps / 8));
+  want = std::min<int64_t>(want, std::max<int64_t>(1, cap / std::max<int64_t>(1, MN)));
+  return (int)std::max<int64_t>(1, want);
+}
+
+static cudaError_t gemm(const GemmView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
+                        int64_t* launches) {
+  const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
+  const int64_t tm = (M + GT - 1) / GT, tn = (g.N + GT - 1) / GT;
+  const int ns = num_splits(tm * tn, K, M * g.N, num_sms, scratch_cap);
+  const int64_t steps = (K + GK - 1) / GK;
+  const int kchunk = (int)(((steps + ns - 1) / ns) * GK);
+  const int nsplit = (int)((K + kchunk - 1) / kchunk);
+  dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)nsplit);
+  k_gemm_strided<<<grid, 256, 0, s>>>(g, kchunk, nsplit > 1 ? scratch : nullptr);
+  ++*launches;
+  if (nsplit > 1) {
+    const int64_t MN = M * g.N;
+    k_splitk_add<<<(unsigned)std::min<int64_t>((MN + 255) / 256, 4096), 256, 0, s>>>(g, nsplit, scratch);
+    ++*launches;
+  }
   return cudaGetLastError();
 }
 
@@ -198,39 +267,52 @@ __global__ void k_dovs(int mode, int o, int v, int i, int j, int k, const double
   dOVS[(((int64_t)P1 * v + x) * o + P2) * v + y] += s;
 }
 
-// dt1[P3][z] += sum over the other two indices of dY * ovs (one of the three Y terms)
-__global__ void k_dt1(int mode, int o, int v, int i, int j, int k, const double* __restrict__ dY,
-                      const double* __restrict__ ovs, double* __restrict__ dt1) {
-  const int z = blockIdx.x * blockDim.x + threadIdx.x;
-  if (z >= v) return;
-  const int64_t V = v;
+// fixed-order block sum of 256 threads' values; the result is valid in thread 0
+__device__ __forceinline__ double block_sum256(double s, double* red) {
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) t += red[w];
+  return t;
+}
+
+// dt1[P3][z] += sum over the other two indices of dY * ovs (one of the three
+// Y terms); one block per z
+__global__ void __launch_bounds__(256) k_dt1(int mode, int o, int v, int i, int j, int k,
+                                              const double* __restrict__ dY, const double* __restrict__ ovs,
+                                              double* __restrict__ dt1) {
+  __shared__ double red[8];
+  const int z = blockIdx.x;
+  const int64_t V = v, n = V * V;
   auto OV = [&](int P1, int a, int P2, int b) { return ovs[(((int64_t)P1 * v + a) * o + P2) * v + b]; };
   double s = 0.0;
-  if (mode == 0) {  // t1(k,c): sum over a,b of dY[a,b,c] ovs(i,a,j,b)
-    for (int a = 0; a < v; ++a)
-      for (int b = 0; b < v; ++b) s += dY[(a * V + b) * V + z] * OV(i, a, j, b);
-    dt1[(int64_t)k * v + z] += s;
-  } else if (mode == 1) {  // t1(i,a): sum over b,c of dY[a,b,c] ovs(j,b,k,c)
-    for (int b = 0; b < v; ++b)
-      for (int c = 0; c < v; ++c) s += dY[(z * V + b) * V + c] * OV(j, b, k, c);
-    dt1[(int64_t)i * v + z] += s;
-  } else {  // t1(j,b): sum over a,c of dY[a,b,c] ovs(i,a,k,c)
-    for (int a = 0; a < v; ++a)
-      for (int c = 0; c < v; ++c) s += dY[(a * V + z) * V + c] * OV(i, a, k, c);
-    dt1[(int64_t)j * v + z] += s;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const int p = (int)(e / v), q = (int)(e % v);
+    if (mode == 0) s += dY[(p * V + q) * V + z] * OV(i, p, j, q);       // t1(k,c): dY[a,b,c] ovs(i,a,j,b)
+    else if (mode == 1) s += dY[(z * V + p) * V + q] * OV(j, p, k, q);  // t1(i,a): dY[a,b,c] ovs(j,b,k,c)
+    else s += dY[(p * V + z) * V + q] * OV(i, p, k, q);                 // t1(j,b): dY[a,b,c] ovs(i,a,k,c)
+  }
+  const double t = block_sum256(s, red);
+  if (threadIdx.x == 0) {
+    const int row = mode == 0 ? k : (mode == 1 ? i : j);
+    dt1[(int64_t)row * v + z] += t;
   }
 }
 
-// deps_v[x] -= sum_bc dD[x,b,c] + sum_ac dD[a,x,c] + sum_ab dD[a,b,x]
-__global__ void k_deps_v(int v, const double* __restrict__ dD, double* __restrict__ deps_v) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= v) return;
-  const int64_t V = v;
+// deps_v[x] -= sum_bc dD[x,b,c] + sum_ac dD[a,x,c] + sum_ab dD[a,b,x]; one block per x
+__global__ void __launch_bounds__(256) k_deps_v(int v, const double* __restrict__ dD, double* __restrict__ deps_v) {
+  __shared__ double red[8];
+  const int x = blockIdx.x;
+  const int64_t V = v, n = V * V;
   double s = 0.0;
-  for (int p = 0; p < v; ++p)
-    for (int q = 0; q < v; ++q)
-      s += dD[(x * V + p) * V + q] + dD[(p * V + x) * V + q] + dD[(p * V + q) * V + x];
-  deps_v[x] -= s;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const int p = (int)(e / v), q = (int)(e % v);
+    s += dD[(x * V + p) * V + q] + dD[(p * V + x) * V + q] + dD[(p * V + q) * V + x];
+  }
+  const double t = block_sum256(s, red);
+  if (threadIdx.x == 0) deps_v[x] -= t;
 }
 
 // deps_o[i], [j], [k] += sum_abc dD (fixed-order block sum)
@@ -287,15 +369,18 @@ __global__ void __launch_bounds__(256) k_sum_share(const double* __restrict__ pa
 // ---------------------------------------------------------------------------
 
 struct VjpWork {
-  double *t2L, *nooT, *ovs, *G, *dW, *dY, *dD, *dOVS, *epart, *shares;
+  double *t2L, *nooT, *ovs, *G, *dW, *dY, *dD, *dOVS, *epart, *shares, *splitk;
 };
+
+// doubles of split-K scratch: room for the partial tiles of a v x v output
+static int64_t splitk_cap(int64_t o, int64_t v) { return 80 * std::max(v * v, o * v); }
 
 size_t vjp_fp64_bytes(int64_t o, int64_t v) {
   const int64_t v3 = v * v * v, nt = num_unique_triples(o);
   const int64_t nblk = (v3 + 255) / 256;
   auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
   return a(o * v * v * o) + a(o * o * v * o) + a(o * v * o * v) + a(3 * v3) + 3 * a(v3) + a(o * v * o * v) +
-         a(nblk) + a(std::max<int64_t>(1, nt)) + 1024;
+         a(nblk) + a(std::max<int64_t>(1, nt)) + a(splitk_cap(o, v)) + 1024;
 }
 
 te_status ensure_workspace_public(Handle* h, size_t bytes);
@@ -327,6 +412,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
   const int64_t nblk = (v3 + 255) / 256;
   W.epart = take(nblk);
   W.shares = take(std::max<int64_t>(1, nt));
+  W.splitk = take(splitk_cap(o, v));
 
   // gradient outputs start at zero
   auto zero = [&](double* ptr, int64_t n) {
@@ -384,10 +470,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
       const double* t2rq = c->t2 + ((int64_t)rr * o + qq) * v2;
       const double* t2rp = c->t2 + ((int64_t)rr * o + pp) * v2;
       auto run = [&](GemmView gv) {
-        if (e == cudaSuccess) {
-          e = gemm(gv, s);
-          ++h->n_launches;
-        }
+        if (e == cudaSuccess) e = gemm(gv, h->num_sms, W.splitk, splitk_cap(o, v), s, &h->n_launches);
       };
       if (g->ovvv) {
         // (a) dovvv[p,x,y,d] += sum_z G[x,y,z] t2[r,q,z,d]
@@ -420,12 +503,12 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
     }
     if (e != cudaSuccess) break;
     // disconnected term and denominators
-    const unsigned gb2 = (unsigned)((v2 + 255) / 256), gb1 = (unsigned)((v + 127) / 128);
+    const unsigned gb2 = (unsigned)((v2 + 255) / 256);
     for (int mode = 0; mode < 3; ++mode) {
       if (g->ovov) k_dovs<<<gb2, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, c->t1, W.dOVS);
-      if (g->t1) k_dt1<<<gb1, 128, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
+      if (g->t1) k_dt1<<<(unsigned)v, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
     }
-    if (g->eps_v) k_deps_v<<<gb1, 128, 0, s>>>(v, W.dD, g->eps_v);
+    if (g->eps_v) k_deps_v<<<(unsigned)v, 256, 0, s>>>(v, W.dD, g->eps_v);
     if (g->eps_o) k_deps_o<<<1, 1024, 0, s>>>(v3, W.dD, T.i, T.j, T.k, g->eps_o);
     h->n_launches += 8;
     e = cudaGetLastError();
