@@ -1,11 +1,12 @@
 // Energy epilogue of the tensor-core modes: a persistent kernel fed by TMA.
 //
 // Work item = (triple slot, block triple X >= Y >= Z of 8-wide virtual
-// blocks).  The G blocks are stored cube-major by the contraction kernel
-// ([X][Y][Z][8][8][8], each 8^3 cube contiguous), so each of the item's 18 G
-// cubes (3 G blocks x 6 block orders) arrives by one bulk copy; 27 8x8 blocks
-// of the symmetrised ovov, 9 t1 rows and 3 eps_v rows come by TMA.  Warp 0
-// issues the loads two items ahead into a double buffer; one thread per
+// blocks).  The contraction kernel stores G orbit-major (energy_tc.h): the
+// item's 18 G cubes (3 G blocks x 6 block orders) are contiguous and arrive
+// by one bulk copy; the 18 8x8 blocks of the symmetrised ovov the item uses
+// and 9 t1 rows come by TMA (few, large copies: the copy engine's per-copy
+// cost, not HBM, limited a layout that needed 54 copies per item).  A
+// producer warp issues the loads into a double buffer; one thread per
 // orbit candidate (a,b,c) of the 8^3 block triple.  G is either FP32 (BF16X3/TF32/TF32X3) or an FP32 pair
 // hi + lo (OZAKI), CW = 1 or 2 floats per element.
 //
@@ -29,8 +30,6 @@ constexpr int TB = 8;
 constexpr int WARPS = 16;                 // compute warps: one orbit candidate (a,b,c) of 8^3 per thread
 constexpr int THREADS = (WARPS + 1) * 32;  // + one producer warp
 
-__constant__ int c_perm_tc[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-
 template <int N>
 struct Pos {
   static constexpr int s0 = (N <= 1) ? 0 : (N <= 3) ? 1 : 2;
@@ -50,7 +49,7 @@ struct Layout {
   static constexpr uint32_t buf = cubes + ovs + t1 + eps;
   // W~ (CW planes) and Y (one plane) of the item's 6 block orders, assembled once per item
   static constexpr uint32_t asm_bytes = 6 * 512 * 4 * (CW + 1);
-  static constexpr uint32_t tx = 18 * cube_bytes + 27 * TB * TB * 4 + 9 * TB * 4;
+  static constexpr uint32_t tx = 18 * cube_bytes + 18 * TB * TB * 4 + 9 * TB * 4;
 };
 
 __device__ __forceinline__ void decode_bt(int64_t bt, int* blk) {
@@ -177,7 +176,7 @@ struct EnergyMaps {
 struct EnergyParams {
   int o, v, nslots, nb;
   int64_t nbt, items, t0;
-  const float* gbuf;  // cube-major G blocks: [slot][g][X][Y][Z][CW planes][512, swizzled]
+  const float* gbuf;  // orbit-major G: [slot][bt][g][pid][CW planes][512, swizzled]
   const Triple* triples;
   const double* eps_o;
   const double* eps_v;
@@ -248,21 +247,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
         pending |= 1u << b;
       }
       __syncwarp();
-      for (int q = lane; q < 54; q += 32) {
-        if (q < 18) {
-          const int g = q / 6, pid = q % 6;
-          const int64_t cube_idx =
-              (((int64_t)slot * 3 + g) * P.nb + blk[c_perm_tc[pid][0]]) * P.nb * P.nb +
-              (int64_t)blk[c_perm_tc[pid][1]] * P.nb + blk[c_perm_tc[pid][2]];
-          ptx::bulk_load(base + q * L::cube_bytes, P.gbuf + cube_idx * (TB * TB * TB * CW), L::cube_bytes,
-                         &full[b]);
-        } else if (q < 45) {
-          const int r = q - 18, pair = r / 9, sx = (r / 3) % 3, sy = r % 3;
+      for (int q = lane; q < 28; q += 32) {
+        if (q == 0) {  // the item's 18 cubes, contiguous ([g][pid] as in shared memory)
+          ptx::bulk_load(base, P.gbuf + it * (18 * TB * TB * TB * CW), 18 * L::cube_bytes, &full[b]);
+        } else if (q < 19) {
+          // ovs block (pair, sx, sy) with sx != sy: the only ones a permutation's Y reads
+          const int rr = q - 1, pair = rr / 6, od = rr % 6;
+          const int sx = od >> 1, sy = (od == 0) ? 1 : (od == 1) ? 2 : (od == 2) ? 0 : (od == 3) ? 2 : (od == 4) ? 0 : 1;
+          const int r = pair * 9 + sx * 3 + sy;
           const int P1 = (pair == 1) ? tr.j : tr.i;
           const int P2 = (pair == 0) ? tr.j : tr.k;
           ptx::tma_load_4d(base + L::cubes + r * 256, &M.ovs, &full[b], blk[sy] * TB, P2, blk[sx] * TB, P1);
         } else {
-          const int r = q - 45, which = r / 3, s2 = r % 3;
+          const int r = q - 19, which = r / 3, s2 = r % 3;
           const int occ = which == 0 ? tr.i : (which == 1 ? tr.j : tr.k);
           ptx::tma_load_2d(base + L::cubes + L::ovs + r * 128, &M.t1, &full[b], blk[s2] * TB, occ);
         }

@@ -11,7 +11,7 @@ namespace te {
 struct EnergyLaunch {
   int o, v, nslots, cw, num_sms;
   int64_t nbt, t0;
-  const float* gbuf;           // cube-major G: [slot][g][X][Y][Z][cw planes][512 swizzled], X,Y,Z < ceil(v/8)
+  const float* gbuf;           // orbit-major G: [slot][bt][g][pid][cw planes][512 swizzled]
   const CUtensorMap* map_ovs;  // ovs32 [o][v][o][vq], 4D (b, j, a, i), box (8, 1, 8, 1)
   const CUtensorMap* map_t1;   // t1 [o][vq], 2D (a, i), box (8, 1)
   const Triple* triples;
@@ -32,6 +32,36 @@ struct EnergyLaunch {
 __host__ __device__ __forceinline__ int cube_row(int u, int w) { return u * 64 + (w ^ (u & 3)) * 8; }
 __host__ __device__ __forceinline__ int cube_zx(int u, int w) { return (u & 3) | ((((w ^ u) >> 2) & 1) << 2); }
 __host__ __device__ __forceinline__ int cube_off(int u, int w, int z) { return cube_row(u, w) + (z ^ cube_zx(u, w)); }
+
+// Orbit-major placement of the G cubes.  The energy kernel's work item is a
+// block triple S0 >= S1 >= S2 of 8-wide virtual blocks; it needs, for each of
+// the 3 G blocks g, the cubes at the 6 block orders
+//   pid: (S0,S1,S2) (S0,S2,S1) (S1,S0,S2) (S1,S2,S0) (S2,S0,S1) (S2,S1,S0).
+// They are stored contiguously as [slot][bt][g][pid][CW planes][512], so one
+// bulk copy brings an item's 18 cubes.  A cube (X,Y,Z) whose indices repeat
+// serves several orders and is stored once per order.
+__host__ __device__ __forceinline__ int64_t block_triple_index(int s0, int s1, int s2) {
+  return (int64_t)s0 * (s0 + 1) * (s0 + 2) / 6 + (int64_t)s1 * (s1 + 1) / 2 + s2;
+}
+
+// bt of the sorted block triple of cube (X,Y,Z) and the set of orders pid
+// (bit pid) at which that cube appears
+__host__ __device__ __forceinline__ void orbit_slots(int X, int Y, int Z, int64_t* bt, unsigned* mask) {
+  int s0 = X, s1 = Y, s2 = Z, t;
+  if (s0 < s1) { t = s0; s0 = s1; s1 = t; }
+  if (s1 < s2) { t = s1; s1 = s2; s2 = t; }
+  if (s0 < s1) { t = s0; s0 = s1; s1 = t; }
+  *bt = block_triple_index(s0, s1, s2);
+  *mask = (unsigned)(s0 == X && s1 == Y && s2 == Z) | ((unsigned)(s0 == X && s2 == Y && s1 == Z) << 1) |
+          ((unsigned)(s1 == X && s0 == Y && s2 == Z) << 2) | ((unsigned)(s1 == X && s2 == Y && s0 == Z) << 3) |
+          ((unsigned)(s2 == X && s0 == Y && s1 == Z) << 4) | ((unsigned)(s2 == X && s1 == Y && s0 == Z) << 5);
+}
+
+// floats of the G buffer per triple slot
+__host__ __device__ __forceinline__ int64_t g_slot_floats(int v, int cw) {
+  const int64_t nb = (v + 7) / 8;
+  return nb * (nb + 1) * (nb + 2) / 6 * 18 * 512 * cw;
+}
 
 constexpr int ENERGY_TC_WARPS = 16;
 int64_t energy_tc_grid(int num_sms, int64_t items);

@@ -327,8 +327,7 @@ __device__ __forceinline__ void xor_permute8(float* v, int h) {
   }
 }
 
-__device__ __forceinline__ void store8(float* dst, float* v, int h) {
-  xor_permute8(v, h);
+__device__ __forceinline__ void store8(float* dst, const float* v) {
   float4* o4 = reinterpret_cast<float4*>(dst);
   o4[0] = make_float4(v[0], v[1], v[2], v[3]);
   o4[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -341,8 +340,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Warp roles: 0 TMA producer, 1 MMA issuer (and TMEM owner), 2..9 epilogue:
+// warp w drains TMEM lanes 32 (w % 4) .. +31 (the lane quarter its warp index
+// may access) and every other 16-column chunk, starting at chunk (w - 2) / 4.
+constexpr int GEMM_EPI_WARPS = 8;
+constexpr int GEMM_THREADS = (2 + GEMM_EPI_WARPS) * 32;
+
 template <int MODE>
-__global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMaps maps, const TcParams P) {
+__global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_constant__ TcMaps maps, const TcParams P) {
   using MT = ModeTraits<MODE>;
   constexpr bool TF32 = MT::tf32;
   constexpr int NPART = MT::nparts;
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
-      ptx::mbar_init(&tempty[a], 4);
+      ptx::mbar_init(&tempty[a], GEMM_EPI_WARPS);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -539,6 +544,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
   } else {
     // ---------------- epilogue: TMEM -> G buffer ----------------
     const int quad = warp & 3;
+    const int chunk0 = (warp - 2) >> 2;  // 0 or 1: this warp's first 16-column chunk
     const int row = quad * 32 + lane;
     const int64_t v2 = (int64_t)P.v * P.v;
     float gscale = 1.f;
@@ -557,15 +563,16 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
       const int x = c.x0 + row / P.TB;
       const int y = c.y0 + row % P.TB;
       const bool valid = x < P.v && y < P.v;
-      // cube-major G: [slot][g][X][Y][Z][CW planes][512], swizzled rows (see energy_tc.h);
-      // this row is (x, y) = (X*8 + xl, Y*8 + yl)
+      // orbit-major G: [slot][bt][g][pid][CW planes][512], swizzled rows (see
+      // energy_tc.h); this row is (x, y) = (X*8 + xl, Y*8 + yl)
       const int nb = (P.v + 7) >> 3;
       constexpr int CWF = is_ozaki(MODE) ? 2 : 1;
-      const int64_t cubebase = (((int64_t)(c.slot * 3 + c.g) * nb + (x >> 3)) * nb + (y >> 3)) * nb;
+      const int64_t slot_floats = g_slot_floats(P.v, CWF);
+      float* const gslot = P.gbuf + (int64_t)c.slot * slot_floats;
       const int roff = cube_row(x & 7, y & 7);
       const int zx = cube_zx(x & 7, y & 7);
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)(NACC * P.NT);
-      for (int c0 = 0; c0 < P.NT; c0 += 16) {
+      for (int c0 = 16 * chunk0; c0 < P.NT; c0 += 32) {
         const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
         if constexpr (is_ozaki(MODE)) {
           float a2[16], a3[16], ar[16];
@@ -587,9 +594,18 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
             for (int h2 = 0; h2 < 2; ++h2) {
               const int Z = (z >> 3) + h2;
               if (Z < nb) {
-                float* cube = P.gbuf + (cubebase + Z) * (512 * CWF);
-                store8(cube + roff, hv + 8 * h2, zx);
-                store8(cube + 512 + roff, lv + 8 * h2, zx);
+                int64_t bt;
+                unsigned mask;
+                orbit_slots(x >> 3, y >> 3, Z, &bt, &mask);
+                xor_permute8(hv + 8 * h2, zx);
+                xor_permute8(lv + 8 * h2, zx);
+                float* item = gslot + (bt * 18 + c.g * 6) * (512 * CWF);
+                for (int pid = 0; pid < 6; ++pid) {
+                  if (!((mask >> pid) & 1u)) continue;
+                  float* cube = item + pid * (512 * CWF);
+                  store8(cube + roff, hv + 8 * h2);
+                  store8(cube + 512 + roff, lv + 8 * h2);
+                }
               }
             }
           }
@@ -600,7 +616,15 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ TcMa
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
               const int Z = (z >> 3) + h2;
-              if (Z < nb) store8(P.gbuf + (cubebase + Z) * 512 + roff, vals + 8 * h2, zx);
+              if (Z < nb) {
+                int64_t bt;
+                unsigned mask;
+                orbit_slots(x >> 3, y >> 3, Z, &bt, &mask);
+                xor_permute8(vals + 8 * h2, zx);
+                float* item = gslot + (bt * 18 + c.g * 6) * 512;
+                for (int pid = 0; pid < 6; ++pid)
+                  if ((mask >> pid) & 1u) store8(item + pid * 512 + roff, vals + 8 * h2);
+              }
             }
           }
         }
@@ -730,8 +754,8 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   const int64_t tiles = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
   int64_t want = (4LL * std::max(1, h->num_sms) + tiles - 1) / tiles;
   const int64_t nbk = (v + 7) / 8;
-  const int64_t per_slot = 3LL * nbk * nbk * nbk * 512 * 4 * pl.cw;
-  const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(3LL << 30) / per_slot);
+  const int64_t per_slot = g_slot_floats(v, pl.cw) * 4;
+  const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(6LL << 30) / per_slot);
   want = std::max<int64_t>(want, 4);  // fewer launches per cluster
   want = std::min<int64_t>({want, mem_cap, 1024, std::max<int64_t>(1, ntri)});
   pl.nslots = (int)std::max<int64_t>(1, want);
@@ -768,8 +792,7 @@ static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64
   b->ovs32 = static_cast<float*>(take((size_t)o * v * o * pl.vq * 4));
   b->t1_32 = static_cast<float*>(take((size_t)o * pl.vq * 4));
   b->eps_copy = static_cast<double*>(take((size_t)v * 8));
-  const size_t nbk = (size_t)((v + 7) / 8);
-  b->gbuf = static_cast<float*>(take((size_t)pl.nslots * 3 * nbk * nbk * nbk * 512 * 4 * pl.cw));
+  b->gbuf = static_cast<float*>(take((size_t)pl.nslots * (size_t)g_slot_floats((int)v, pl.cw) * 4));
   b->partials = static_cast<double*>(take((size_t)pl.nslots * ENERGY_TC_WARPS * 1024 * 8));
   b->etri = static_cast<double*>(take((size_t)std::max<int64_t>(1, ntri) * 8));
   b->maxbits = static_cast<unsigned long long*>(take(4 * 8));
@@ -897,7 +920,7 @@ static cudaError_t launch_gemm_tc(const Handle* h, const TcMaps& M, const TcPara
   cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(P.total_tiles, h->num_sms);
-  k_gemm_tc<MODE><<<(unsigned)grid, 192, smem, s>>>(M, P);
+  k_gemm_tc<MODE><<<(unsigned)grid, GEMM_THREADS, smem, s>>>(M, P);
   return cudaGetLastError();
 }
 
