@@ -392,8 +392,13 @@ def main():
         gemm_avg_ms = prof["gemm_ms"] / max(1, prof["gemm_launches"])
         alg_per_launch = nprod * F * args.steps / max(1, prof["gemm_launches"])
         achieved = alg_per_launch / (gemm_avg_ms / 1e3) / 1e12
+        # DRAM bytes per launch: the ncu capture in profiles/k_gemm_tc_o8v320_ozaki.md
+        # measured 2.486 GB per triple at nvir = 320 (same tiles as this workload),
+        # scaled by the triples one launch processes; other shapes: not captured
+        tpl = te.num_unique_triples(o) * args.steps / max(1, prof["gemm_launches"])
+        traffic = 2.486e9 * tpl if (v == 320 and prec == "ozaki" and nprod == 10) else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_gemm_tc", "peak_source": f"{pk_src} bf16 sustained"
                 + ("" if prec in ("bf16x3", "ozaki") else " x 1.1/2.25 (tf32)"),
                 "gemm_share_of_step": prof["gemm_ms"] / max(1e-9, ms),
