@@ -118,9 +118,17 @@ __device__ __forceinline__ double scale_of(const int* exps, int which) {
   return exps ? ldexp(1.0, -exps[which]) : 1.0;
 }
 
-// dst[row][kp] = src[row][k] (k < K) or 0, rows x Kp
+// Slice-interleaved operand planes: rows come in groups of G (one occupied
+// index, or one occupied pair), and a group's slices are consecutive blocks,
+// [group][slice][G rows][Kp].  parts.p[s] points at slice s of group 0, so a
+// row's element for every slice sits at the same index from its part.
+__device__ __forceinline__ int64_t slice_index(int64_t row, int64_t k, int64_t G, int NS, int64_t Kp) {
+  return (row / G) * (NS * G * Kp) + (row % G) * Kp + k;
+}
+
+// dst[row][kp] = src[row][k] (k < K) or 0, rows x Kp, slice-interleaved by groups of G rows
 template <int MODE>
-__global__ void k_split_rows(const double* __restrict__ src, Parts parts, int64_t rows, int K, int Kp,
+__global__ void k_split_rows(const double* __restrict__ src, Parts parts, int64_t rows, int K, int Kp, int64_t G,
                              const int* exps, int which) {
   const double sc = scale_of(exps, which);
   const int64_t n = rows * Kp;
@@ -129,7 +137,7 @@ __global__ void k_split_rows(const double* __restrict__ src, Parts parts, int64_
     const int k = (int)(idx % Kp);
     const int64_t row = idx / Kp;
     const double x = k < K ? src[row * K + k] : 0.0;
-    split_store<MODE>(x, parts, idx, sc);
+    split_store<MODE>(x, parts, slice_index(row, k, G, ModeTraits<MODE>::nparts, Kp), sc);
   }
 }
 
@@ -148,7 +156,7 @@ __global__ void k_split_t2L(const double* __restrict__ t2, Parts parts, int o, i
     const int x = (int)(rest % v);
     const int q = (int)(rest / v);
     const double val = l < o ? t2[(((int64_t)l * o + q) * v + x) * v + y] : 0.0;
-    split_store<MODE>(val, parts, idx, sc);
+    split_store<MODE>(val, parts, slice_index(idx / op, l, (int64_t)v * v, ModeTraits<MODE>::nparts, op), sc);
   }
 }
 
@@ -167,7 +175,7 @@ __global__ void k_split_noo(const double* __restrict__ ooov, Parts parts, int o,
     const int r = (int)(rest % o);
     const int p = (int)(rest / o);
     const double val = l < o ? -ooov[(((int64_t)p * o + l) * o + r) * v + z] : 0.0;
-    split_store<MODE>(val, parts, idx, sc);
+    split_store<MODE>(val, parts, slice_index(idx / op, l, v, ModeTraits<MODE>::nparts, op), sc);
   }
 }
 
@@ -246,13 +254,16 @@ static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1,
 // the GEMM kernel
 // ---------------------------------------------------------------------------
 
+// One 5-D map per operand view; the slice is a box dimension, so one copy
+// brings every slice of a stage (the slices land part-contiguous in shared
+// memory, as the MMA descriptors expect).
 struct TcMaps {
-  CUtensorMap a_nat[MAX_PARTS];  // ovvv parts, dims (Kp, y, x, p): rows (x,y) of ovvv[p]
-  CUtensorMap a_tr[MAX_PARTS];   // ovvv parts, dims (Kp, y, x, q) with strides swapped: ovvv[q,y,x,:]
-  CUtensorMap l_nat[MAX_PARTS];  // t2L parts natural
-  CUtensorMap l_tr[MAX_PARTS];   // t2L parts transposed
-  CUtensorMap b_t2[MAX_PARTS];   // t2 parts, dims (Kp, z, q, r)
-  CUtensorMap b_noo[MAX_PARTS];  // nooT parts, dims (Kp, z, r, p)
+  CUtensorMap a_nat;  // ovvv slices [p][s][x][y][Kp], dims (Kp, y, x, s, p): rows (x,y) of ovvv[p]
+  CUtensorMap a_tr;   // the same with the y and x strides swapped: rows ovvv[q,y,x,:]
+  CUtensorMap l_nat;  // t2L slices [q][s][x][y][op], natural
+  CUtensorMap l_tr;   // t2L slices, transposed rows
+  CUtensorMap b_t2;   // t2 slices [r][q][s][z][Kp], dims (Kp, z, s, q, r)
+  CUtensorMap b_noo;  // nooT slices [p][r][s][z][op], dims (op, z, s, r, p)
 };
 
 struct TcParams {
@@ -381,14 +392,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
     ptx::fence_barrier_init();
   }
   if (warp == 0 && lane == 0) {
-    for (int k = 0; k < NPART; ++k) {
-      ptx::tma_prefetch_desc(&maps.a_nat[k]);
-      ptx::tma_prefetch_desc(&maps.a_tr[k]);
-      ptx::tma_prefetch_desc(&maps.l_nat[k]);
-      ptx::tma_prefetch_desc(&maps.l_tr[k]);
-      ptx::tma_prefetch_desc(&maps.b_t2[k]);
-      ptx::tma_prefetch_desc(&maps.b_noo[k]);
-    }
+    ptx::tma_prefetch_desc(&maps.a_nat);
+    ptx::tma_prefetch_desc(&maps.a_tr);
+    ptx::tma_prefetch_desc(&maps.l_nat);
+    ptx::tma_prefetch_desc(&maps.l_tr);
+    ptx::tma_prefetch_desc(&maps.b_t2);
+    ptx::tma_prefetch_desc(&maps.b_noo);
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, P.tmem_cols);
@@ -423,24 +432,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
             ptx::mbar_arrive_expect_tx(&full[stage], bytes);
             pending[stage] = (int)phase;
             unsigned char* sa = smem + (size_t)stage * P.stage_bytes;
+            unsigned char* sb = sa + NPART * P.a_part_bytes;
             const int kc = ch * ce;
-#pragma unroll
-            for (int k = 0; k < NPART; ++k) {
-              void* da = sa + k * P.a_part_bytes;
-              void* db = sa + NPART * P.a_part_bytes + k * P.b_part_bytes;
-              if (seg == 0) {
-                ptx::tma_load_4d(da, &maps.a_nat[k], &full[stage], kc, c.y0, c.x0, c.p);
-                ptx::tma_load_4d(db, &maps.b_t2[k], &full[stage], kc, c.z0, c.q, c.r);
-              } else if (seg == 1) {
-                ptx::tma_load_4d(da, &maps.a_tr[k], &full[stage], kc, c.y0, c.x0, c.q);
-                ptx::tma_load_4d(db, &maps.b_t2[k], &full[stage], kc, c.z0, c.p, c.r);
-              } else if (seg == 2) {
-                ptx::tma_load_4d(da, &maps.l_tr[k], &full[stage], kc, c.y0, c.x0, c.p);
-                ptx::tma_load_4d(db, &maps.b_noo[k], &full[stage], kc, c.z0, c.r, c.q);
-              } else {
-                ptx::tma_load_4d(da, &maps.l_nat[k], &full[stage], kc, c.y0, c.x0, c.q);
-                ptx::tma_load_4d(db, &maps.b_noo[k], &full[stage], kc, c.z0, c.r, c.p);
-              }
+            if (seg == 0) {
+              ptx::tma_load_5d(sa, &maps.a_nat, &full[stage], kc, c.y0, c.x0, 0, c.p);
+              ptx::tma_load_5d(sb, &maps.b_t2, &full[stage], kc, c.z0, 0, c.q, c.r);
+            } else if (seg == 1) {
+              ptx::tma_load_5d(sa, &maps.a_tr, &full[stage], kc, c.y0, c.x0, 0, c.q);
+              ptx::tma_load_5d(sb, &maps.b_t2, &full[stage], kc, c.z0, 0, c.p, c.r);
+            } else if (seg == 2) {
+              ptx::tma_load_5d(sa, &maps.l_tr, &full[stage], kc, c.y0, c.x0, 0, c.p);
+              ptx::tma_load_5d(sb, &maps.b_noo, &full[stage], kc, c.z0, 0, c.r, c.q);
+            } else {
+              ptx::tma_load_5d(sa, &maps.l_nat, &full[stage], kc, c.y0, c.x0, 0, c.q);
+              ptx::tma_load_5d(sb, &maps.b_noo, &full[stage], kc, c.z0, 0, c.r, c.p);
             }
             if (++stage == (uint32_t)P.stages) {
               stage = 0;
@@ -490,8 +495,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
               uint64_t ad[NPART], bd[NPART];
 #pragma unroll
               for (int k = 0; k < NPART; ++k) {
-                ad[k] = ptx::smem_desc(a0 + k * P.a_part_bytes + ks * 32, sbo, lay);
-                bd[k] = ptx::smem_desc(b0 + k * P.b_part_bytes + ks * 32, sbo, lay);
+                // one box per operand lands the slices back to back: 128 (A) or NT (B) rows of cb bytes each
+                ad[k] = ptx::smem_desc(a0 + k * (128u * (uint32_t)cb) + ks * 32, sbo, lay);
+                bd[k] = ptx::smem_desc(b0 + k * ((uint32_t)P.NT * (uint32_t)cb) + ks * 32, sbo, lay);
               }
               const uint32_t acc_in = first ? 0u : 1u;
               if constexpr (is_ozaki(MODE)) {
@@ -782,12 +788,20 @@ static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64
   const size_t es = (size_t)pl.es;
   const size_t na = (size_t)o * v * v * pl.vp, nb = (size_t)o * o * v * pl.vp;
   const size_t nl = (size_t)o * v * v * pl.op, nn = (size_t)o * o * v * pl.op;
+  // one slice-interleaved block per array; part k points at slice k of the
+  // first row group (groups: v^2 rows per occupied index for ovvv and t2L,
+  // v rows per occupied pair for t2 and nooT)
+  const size_t ns = (size_t)pl.nparts;
+  char* A = static_cast<char*>(take(ns * na * es));
+  char* B = static_cast<char*>(take(ns * nb * es));
+  char* Lb = static_cast<char*>(take(ns * nl * es));
+  char* Nb = static_cast<char*>(take(ns * nn * es));
   for (int k = 0; k < MAX_PARTS; ++k) {
-    const bool use = k < pl.nparts;
-    b->a[k] = use ? take(na * es) : nullptr;
-    b->b[k] = use ? take(nb * es) : nullptr;
-    b->l[k] = use ? take(nl * es) : nullptr;
-    b->n[k] = use ? take(nn * es) : nullptr;
+    const bool use = k < pl.nparts && base;
+    b->a[k] = use ? A + (size_t)k * v * v * pl.vp * es : nullptr;
+    b->b[k] = use ? B + (size_t)k * v * pl.vp * es : nullptr;
+    b->l[k] = use ? Lb + (size_t)k * v * v * pl.op * es : nullptr;
+    b->n[k] = use ? Nb + (size_t)k * v * pl.op * es : nullptr;
   }
   b->ovs32 = static_cast<float*>(take((size_t)o * v * o * pl.vq * 4));
   b->t1_32 = static_cast<float*>(take((size_t)o * pl.vq * 4));
@@ -827,38 +841,37 @@ static te_status build_maps(TcState* st, const TcPlan& pl, int o, int v, const T
   std::memset(M, 0, sizeof(*M));
   const CUtensorMapDataType dt = pl.es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const uint64_t es = (uint64_t)pl.es;
-  const uint64_t vp = pl.vp, op = pl.op, V = v, O = o;
-  for (int k = 0; k < pl.nparts; ++k) {
-    te_status s;
-    {  // ovvv[p][x][y][d]: dims (d, y, x, p)
-      const uint64_t d[4] = {vp, V, V, O};
-      const uint64_t sn[3] = {vp * es, V * vp * es, V * V * vp * es};
-      const uint32_t box[4] = {(uint32_t)pl.kw_elems, (uint32_t)pl.TB, (uint32_t)pl.TA, 1};
-      if ((s = encode(st, &M->a_nat[k], b.a[k], dt, 4, d, sn, box, swz_of(pl.cbw), "ovvv")) != TE_OK) return s;
-      // transposed rows: element (d, y, x, q) at ovvv[q][y][x][d]
-      const uint64_t stt[3] = {V * vp * es, vp * es, V * V * vp * es};
-      if ((s = encode(st, &M->a_tr[k], b.a[k], dt, 4, d, stt, box, swz_of(pl.cbw), "ovvv^T")) != TE_OK) return s;
-    }
-    {  // t2L[q][x][y][l]: dims (l, y, x, q)
-      const uint64_t d[4] = {op, V, V, O};
-      const uint64_t sn[3] = {op * es, V * op * es, V * V * op * es};
-      const uint32_t box[4] = {(uint32_t)pl.ko_elems, (uint32_t)pl.TB, (uint32_t)pl.TA, 1};
-      if ((s = encode(st, &M->l_nat[k], b.l[k], dt, 4, d, sn, box, swz_of(pl.cbo), "t2L")) != TE_OK) return s;
-      const uint64_t stt[3] = {V * op * es, op * es, V * V * op * es};
-      if ((s = encode(st, &M->l_tr[k], b.l[k], dt, 4, d, stt, box, swz_of(pl.cbo), "t2L^T")) != TE_OK) return s;
-    }
-    {  // t2[r][q][z][d]: dims (d, z, q, r)
-      const uint64_t d[4] = {vp, V, O, O};
-      const uint64_t sn[3] = {vp * es, V * vp * es, O * V * vp * es};
-      const uint32_t box[4] = {(uint32_t)pl.kw_elems, (uint32_t)pl.NT, 1, 1};
-      if ((s = encode(st, &M->b_t2[k], b.b[k], dt, 4, d, sn, box, swz_of(pl.cbw), "t2")) != TE_OK) return s;
-    }
-    {  // nooT[p][r][z][l]: dims (l, z, r, p)
-      const uint64_t d[4] = {op, V, O, O};
-      const uint64_t sn[3] = {op * es, V * op * es, O * V * op * es};
-      const uint32_t box[4] = {(uint32_t)pl.ko_elems, (uint32_t)pl.NT, 1, 1};
-      if ((s = encode(st, &M->b_noo[k], b.n[k], dt, 4, d, sn, box, swz_of(pl.cbo), "nooT")) != TE_OK) return s;
-    }
+  const uint64_t vp = pl.vp, op = pl.op, V = v, O = o, NS = (uint64_t)pl.nparts;
+  const uint32_t ns = (uint32_t)pl.nparts;
+  te_status s;
+  {  // ovvv slices [p][s][x][y][d]: dims (d, y, x, s, p)
+    const uint64_t d[5] = {vp, V, V, NS, O};
+    const uint64_t sn[4] = {vp * es, V * vp * es, V * V * vp * es, NS * V * V * vp * es};
+    const uint32_t box[5] = {(uint32_t)pl.kw_elems, (uint32_t)pl.TB, (uint32_t)pl.TA, ns, 1};
+    if ((s = encode(st, &M->a_nat, b.a[0], dt, 5, d, sn, box, swz_of(pl.cbw), "ovvv")) != TE_OK) return s;
+    // transposed rows: element (d, y, x, s, q) at ovvv[q][s][y][x][d]
+    const uint64_t stt[4] = {V * vp * es, vp * es, V * V * vp * es, NS * V * V * vp * es};
+    if ((s = encode(st, &M->a_tr, b.a[0], dt, 5, d, stt, box, swz_of(pl.cbw), "ovvv^T")) != TE_OK) return s;
+  }
+  {  // t2L slices [q][s][x][y][l]: dims (l, y, x, s, q)
+    const uint64_t d[5] = {op, V, V, NS, O};
+    const uint64_t sn[4] = {op * es, V * op * es, V * V * op * es, NS * V * V * op * es};
+    const uint32_t box[5] = {(uint32_t)pl.ko_elems, (uint32_t)pl.TB, (uint32_t)pl.TA, ns, 1};
+    if ((s = encode(st, &M->l_nat, b.l[0], dt, 5, d, sn, box, swz_of(pl.cbo), "t2L")) != TE_OK) return s;
+    const uint64_t stt[4] = {V * op * es, op * es, V * V * op * es, NS * V * V * op * es};
+    if ((s = encode(st, &M->l_tr, b.l[0], dt, 5, d, stt, box, swz_of(pl.cbo), "t2L^T")) != TE_OK) return s;
+  }
+  {  // t2 slices [r][q][s][z][d]: dims (d, z, s, q, r)
+    const uint64_t d[5] = {vp, V, NS, O, O};
+    const uint64_t sn[4] = {vp * es, V * vp * es, NS * V * vp * es, O * NS * V * vp * es};
+    const uint32_t box[5] = {(uint32_t)pl.kw_elems, (uint32_t)pl.NT, ns, 1, 1};
+    if ((s = encode(st, &M->b_t2, b.b[0], dt, 5, d, sn, box, swz_of(pl.cbw), "t2")) != TE_OK) return s;
+  }
+  {  // nooT slices [p][r][s][z][l]: dims (l, z, s, r, p)
+    const uint64_t d[5] = {op, V, NS, O, O};
+    const uint64_t sn[4] = {op * es, V * op * es, NS * V * op * es, O * NS * V * op * es};
+    const uint32_t box[5] = {(uint32_t)pl.ko_elems, (uint32_t)pl.NT, ns, 1, 1};
+    if ((s = encode(st, &M->b_noo, b.n[0], dt, 5, d, sn, box, swz_of(pl.cbo), "nooT")) != TE_OK) return s;
   }
   return TE_OK;
 }
@@ -904,9 +917,9 @@ static cudaError_t launch_prep_tc(const te_cluster* c, const TcPlan& pl, const T
   }
   const Parts A{{b.a[0], b.a[1], b.a[2], b.a[3], b.a[4]}}, B{{b.b[0], b.b[1], b.b[2], b.b[3], b.b[4]}};
   const Parts Lp{{b.l[0], b.l[1], b.l[2], b.l[3], b.l[4]}}, N{{b.n[0], b.n[1], b.n[2], b.n[3], b.n[4]}};
-  k_split_rows<MODE><<<gridn((int64_t)o * v * v * pl.vp), 256, 0, s>>>(c->ovvv, A, (int64_t)o * v * v, v, pl.vp,
+  k_split_rows<MODE><<<gridn((int64_t)o * v * v * pl.vp), 256, 0, s>>>(c->ovvv, A, (int64_t)o * v * v, v, pl.vp, (int64_t)v * v,
                                                                        ex, 0);
-  k_split_rows<MODE><<<gridn((int64_t)o * o * v * pl.vp), 256, 0, s>>>(c->t2, B, (int64_t)o * o * v, v, pl.vp,
+  k_split_rows<MODE><<<gridn((int64_t)o * o * v * pl.vp), 256, 0, s>>>(c->t2, B, (int64_t)o * o * v, v, pl.vp, (int64_t)v,
                                                                        ex, 1);
   k_split_t2L<MODE><<<gridn((int64_t)o * v * v * pl.op), 256, 0, s>>>(c->t2, Lp, o, v, pl.op, ex, 2);
   k_split_noo<MODE><<<gridn((int64_t)o * o * v * pl.op), 256, 0, s>>>(c->ooov, N, o, v, pl.op, ex, 3);
