@@ -582,9 +582,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
         const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
         if constexpr (is_ozaki(MODE)) {
           float a2[16], a3[16], ar[16];
-          ptx::tmem_ld16(tbase + c0, a2);
-          ptx::tmem_ld16(tbase + P.NT + c0, a3);
-          ptx::tmem_ld16(tbase + 2 * P.NT + c0, ar);
+          ptx::tmem_ld16x3(tbase + c0, tbase + P.NT + c0, tbase + 2 * P.NT + c0, a2, a3, ar);
           if (valid) {
             float hv[16], lv[16];
 #pragma unroll
