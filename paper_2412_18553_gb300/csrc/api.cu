@@ -490,8 +490,11 @@ te_status t_energy_vjp(te_handle hh, const te_cluster* c, te_precision p, double
   DeviceGuard g(h->device);
   te_status st = validate(h, c, p, s);
   if (st != TE_OK) return st;
-  // every mode's adjoint is evaluated in float64 (the forward's exact reference)
-  return run_vjp_fp64(h, c, gE, e_out, gr, s);
+  // float64: DFMA contractions; the tensor-core modes: exact-slice contractions
+  if (p == TE_FP64) return run_vjp_fp64(h, c, gE, e_out, gr, s);
+  if (h->cc_major != 10 && h->cc_major != 11)
+    return fail(TE_EUNSUPPORTED, "the tensor-core adjoint needs an sm_100-family GPU");
+  return run_vjp_tc(h, c, gE, e_out, gr, s);
 }
 
 te_status te_sync(te_handle hh, te_stream_t ss) {

@@ -442,7 +442,7 @@ cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   EnergyMaps M;
   M.ovs = *e.map_ovs;
   M.t1 = *e.map_t1;
-  EnergyParams P;
+  EnergyParams P{};
   P.o = e.o;
   P.v = e.v;
   P.nslots = e.nslots;

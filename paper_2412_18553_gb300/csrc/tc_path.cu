@@ -935,6 +935,71 @@ static cudaError_t launch_gemm_tc(const Handle* h, const TcMaps& M, const TcPara
   return cudaGetLastError();
 }
 
+size_t tc_slices_bytes(int o, int v) {
+  const size_t vp = (size_t)round_up(v, 16), op = (size_t)round_up(o, 16), NS = 4, es = 2;
+  const size_t na = (size_t)o * v * v * vp, nb = (size_t)o * o * v * vp;
+  const size_t nl = (size_t)o * v * v * op, nn = (size_t)o * o * v * op;
+  auto al = [](size_t b) { return (b + 1023) & ~size_t(1023); };
+  return al(NS * na * es) + al(NS * nb * es) + al(NS * nl * es) + al(NS * nn * es) + al(64) + al(64) + 1024;
+}
+
+te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, cudaStream_t s) {
+  const int o = (int)c->nocc, v = (int)c->nvir;
+  const int vp = round_up(v, 16), op = round_up(o, 16);
+  constexpr int NS = 4;
+  const size_t es = 2;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base_v) + 1023) & ~uintptr_t(1023));
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 1023) & ~size_t(1023);
+    char* p = base + off;
+    off += bytes;
+    return p;
+  };
+  const size_t na = (size_t)o * v * v * vp, nb = (size_t)o * o * v * vp;
+  const size_t nl = (size_t)o * v * v * op, nn = (size_t)o * o * v * op;
+  char* A = take(NS * na * es);
+  char* B = take(NS * nb * es);
+  char* L = take(NS * nl * es);
+  char* N = take(NS * nn * es);
+  auto* maxbits = reinterpret_cast<unsigned long long*>(take(64));
+  int* exps = reinterpret_cast<int*>(take(64));
+  Parts pa{}, pb{}, pL{}, pN{};
+  for (int k = 0; k < NS; ++k) {
+    pa.p[k] = A + (size_t)k * v * v * vp * es;
+    pb.p[k] = B + (size_t)k * v * vp * es;
+    pL.p[k] = L + (size_t)k * v * v * op * es;
+    pN.p[k] = N + (size_t)k * v * op * es;
+  }
+  cudaMemsetAsync(maxbits, 0, 4 * 8, s);
+  k_maxabs<<<1024, 256, 0, s>>>(c->ovvv, (int64_t)o * v * v * v, c->t2, (int64_t)o * o * v * v, c->ooov,
+                                (int64_t)o * o * o * v, maxbits);
+  k_exponents<<<1, 1, 0, s>>>(maxbits, exps);
+  k_split_rows<TC_OZAKI><<<gridn((int64_t)o * v * v * vp), 256, 0, s>>>(c->ovvv, pa, (int64_t)o * v * v, v, vp,
+                                                                        (int64_t)v * v, exps, 0);
+  k_split_rows<TC_OZAKI><<<gridn((int64_t)o * o * v * vp), 256, 0, s>>>(c->t2, pb, (int64_t)o * o * v, v, vp,
+                                                                        (int64_t)v, exps, 1);
+  k_split_t2L<TC_OZAKI><<<gridn((int64_t)o * v * v * op), 256, 0, s>>>(c->t2, pL, o, v, op, exps, 2);
+  k_split_noo<TC_OZAKI><<<gridn((int64_t)o * o * v * op), 256, 0, s>>>(c->ooov, pN, o, v, op, exps, 3);
+  if (cudaGetLastError() != cudaSuccess) return fail(TE_ECUDA, "slice preparation launch failed");
+  out->ovvv = A;
+  out->t2 = B;
+  out->t2L = L;
+  out->nooT = N;
+  out->ovvv_plane = (int64_t)v * v * vp;
+  out->t2_plane = (int64_t)v * vp;
+  out->t2L_plane = (int64_t)v * v * op;
+  out->nooT_plane = (int64_t)v * op;
+  out->ovvv_p = NS * (int64_t)v * v * vp;
+  out->t2_rq = NS * (int64_t)v * vp;
+  out->t2L_q = NS * (int64_t)v * v * op;
+  out->nooT_pr = NS * (int64_t)v * op;
+  out->vp = vp;
+  out->op = op;
+  out->exps = exps;
+  return TE_OK;
+}
+
 te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, size_t* bytes) {
   const TcPlan pl = make_plan(h, (int)c->nocc, (int)c->nvir, tc_mode_of(p, (int)c->nocc, (int)c->nvir, h->ozaki_bits),
                               num_unique_triples(c->nocc));

@@ -113,9 +113,12 @@ cudaError_t launch_reduce_triples(const double* partials, int64_t nbt, const Tri
 cudaError_t launch_reduce_total(const double* e_triples, int64_t n, double* e_out,
                                 cudaStream_t s);
 
-// adjoint of E(T) in float64 (vjp_fp64.cu)
+// adjoint of E(T) in float64 (vjp.cu)
 te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
                        cudaStream_t s);
+// the same with the contractions on the tensor cores in exact BF16 slices (vjp.cu)
+te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
+                     cudaStream_t s);
 
 constexpr int ENERGY_TB = 8;  // virtual block edge of the energy kernel
 inline int64_t energy_num_blocks(int64_t v) { return (v + ENERGY_TB - 1) / ENERGY_TB; }

@@ -1,4 +1,6 @@
-// Adjoint of E(T) (float64): dE/d(eps_o, eps_v, ovvv, ooov, ovov, t1, t2).
+// Adjoint of E(T): dE/d(eps_o, eps_v, ovvv, ooov, ovov, t1, t2), in float64
+// (DFMA contractions) or with the contractions on the tensor cores in exact
+// BF16 slices (the exact-slice mode's scheme), epilogue and sums in float64.
 //
 // E = sum over unique occupied triples t of (m_t/3) e_t,
 //   e_t = sum_{abc} W~[abc] R[V][abc] / D[abc],  V = W~ + Y,
@@ -15,8 +17,11 @@
 // + ovs(jb,kc) t1(ia) + ovs(ia,kc) t1(jb) with ovs = (ovov + ovov^T)/2 gives the
 // ovov and t1 parts.  Triples are processed one after another on the stream
 // and every accumulation has a fixed order, so the gradient is deterministic.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
+#include "tc_path.h"
 #include "te_internal.h"
 
 namespace te {
@@ -38,6 +43,7 @@ struct AdjArgs {
   double* dY;           // [v^3]
   double* dD;           // [v^3]
   double* epart;        // per-block partial energies (unweighted by gE: m/3 e)
+  unsigned long long* dwmax;  // if set: max |dW~| (bit pattern of a non-negative double)
 };
 
 __device__ __forceinline__ double wt_at(const AdjArgs& A, int x, int y, int z) {
@@ -79,6 +85,11 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
   }
   for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = contrib;
+  if (A.dwmax) {
+    double m = e < v3 ? fabs(A.dW[e]) : 0.0;
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(A.dwmax, (unsigned long long)__double_as_longlong(m));
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -236,6 +247,202 @@ static cudaError_t gemm(const GemmView& g, int num_sms, double* scratch, int64_t
     ++*launches;
   }
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// exact-slice strided GEMM on the tensor cores (mma.sync, BF16 -> FP32):
+//   C[m,n] (+)= alpha 2^(ea + eb) sum_k A[m,k] B[k,n]
+// A and B are four BF16 slice planes each (slice s at base + s * plane), read
+// through the same two-index strided views as the float64 kernel.  The ten
+// slice products a_i b_j with i + j <= 3 go to three FP32 accumulators:
+// level 0 and level 1 exactly (K <= 1024 per block keeps their partial sums
+// integer multiples of the level's unit below 2^24), the higher levels
+// approximately; each block's sums go to float64 once, at its end.
+// ---------------------------------------------------------------------------
+
+struct OzView {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int64_t a_ps, b_ps;  // slice plane strides (elements)
+  double* C;
+  int64_t M1, M2, N, K1, K2;
+  int64_t a_m1, a_m2, a_k1, a_k2;
+  int64_t b_k1, b_k2, b_n;
+  int64_t c_m1, c_m2, c_n;
+  double alpha;
+  const int* ea;  // device scale exponents of A's and B's slices
+  const int* eb;
+  int overwrite;  // store instead of accumulate (single K split only)
+};
+
+constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_KMAX = 1024, OZ_NS = 4;
+constexpr int OZ_LD = OZ_BK + 8;  // padded row (bf16): conflict-free fragment loads
+
+__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* __restrict__ part) {
+  __shared__ __align__(16) __nv_bfloat16 As[OZ_NS][OZ_BM][OZ_LD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[OZ_NS][OZ_BN][OZ_LD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int M = (int)(g.M1 * g.M2), N = (int)g.N, K = (int)(g.K1 * g.K2), K2 = (int)g.K2;
+  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  // loader: thread -> one row (A) / column (B) and 16 consecutive k of the 32
+  const int lr = tid >> 1, lk = (tid & 1) * 16;
+  const int am = m0 + lr, bn = n0 + lr;
+  const bool am_ok = am < M, bn_ok = bn < N;
+  const int64_t a_row = am_ok ? (int64_t)(am / (int)g.M2) * g.a_m1 + (int64_t)(am % (int)g.M2) * g.a_m2 : 0;
+  const int64_t b_col = bn_ok ? (int64_t)bn * g.b_n : 0;
+  // warp tile 32 x 32: 2 x 4 MMA tiles of 16 x 8
+  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  const int gq = lane >> 2, tq = lane & 3;
+  float acc[3][2][4][4];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[l][i][j][q] = 0.f;
+  int k1 = (kb + lk) / K2, k2 = (kb + lk) % K2;  // cursor of this thread's first k
+  for (int k0 = kb; k0 < ke; k0 += OZ_BK) {
+    int c1 = k1, c2 = k2;
+#pragma unroll 4
+    for (int u = 0; u < 16; ++u) {
+      const bool k_ok = k0 + lk + u < ke;
+      const int64_t ka = (int64_t)c1 * g.a_k1 + (int64_t)c2 * g.a_k2;
+      const int64_t kbo = (int64_t)c1 * g.b_k1 + (int64_t)c2 * g.b_k2;
+#pragma unroll
+      for (int sl = 0; sl < OZ_NS; ++sl) {
+        As[sl][lr][lk + u] = (am_ok && k_ok) ? g.A[a_row + ka + sl * g.a_ps] : __float2bfloat16_rn(0.f);
+        Bs[sl][lr][lk + u] = (bn_ok && k_ok) ? g.B[b_col + kbo + sl * g.b_ps] : __float2bfloat16_rn(0.f);
+      }
+      if (++c2 == K2) {
+        c2 = 0;
+        ++c1;
+      }
+    }
+    // advance the cursor by OZ_BK
+    k2 += OZ_BK;
+    while (k2 >= K2) {
+      k2 -= K2;
+      ++k1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < OZ_BK; kk += 16) {
+      uint32_t af[OZ_NS][2][4], bf[OZ_NS][4][2];
+#pragma unroll
+      for (int sl = 0; sl < OZ_NS; ++sl) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int r = wm + i * 16 + gq;
+          af[sl][i][0] = *reinterpret_cast<const uint32_t*>(&As[sl][r][kk + 2 * tq]);
+          af[sl][i][1] = *reinterpret_cast<const uint32_t*>(&As[sl][r + 8][kk + 2 * tq]);
+          af[sl][i][2] = *reinterpret_cast<const uint32_t*>(&As[sl][r][kk + 2 * tq + 8]);
+          af[sl][i][3] = *reinterpret_cast<const uint32_t*>(&As[sl][r + 8][kk + 2 * tq + 8]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int cidx = wn + j * 8 + gq;
+          bf[sl][j][0] = *reinterpret_cast<const uint32_t*>(&Bs[sl][cidx][kk + 2 * tq]);
+          bf[sl][j][1] = *reinterpret_cast<const uint32_t*>(&Bs[sl][cidx][kk + 2 * tq + 8]);
+        }
+      }
+#pragma unroll
+      for (int sa = 0; sa < OZ_NS; ++sa)
+#pragma unroll
+        for (int sb = 0; sb < OZ_NS - sa; ++sb) {
+          const int lev = sa + sb == 0 ? 0 : (sa + sb == 1 ? 1 : 2);
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[lev][i][j], af[sa][i], bf[sb][j]);
+        }
+    }
+    __syncthreads();
+  }
+  const double scale = ldexp(g.alpha, *g.ea + *g.eb);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
+        const int n = n0 + wn + j * 8 + 2 * tq + (q & 1);
+        if (m >= M || n >= N) continue;
+        const double val = scale * (((double)acc[0][i][j][q] + (double)acc[1][i][j][q]) + (double)acc[2][i][j][q]);
+        if (part) {
+          part[((int64_t)blockIdx.z * M + m) * N + n] = val;
+        } else {
+          double* cp = g.C + (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2 + n * g.c_n;
+          *cp = g.overwrite ? val : *cp + val;
+        }
+      }
+}
+
+// C[m,n] += sum_z part[z][m][n], z in order (alpha is already applied)
+__global__ void k_splitk_add_oz(OzView g, int nsplit, const double* __restrict__ part) {
+  const int M = (int)(g.M1 * g.M2);
+  const int64_t MN = (int64_t)M * g.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += part[z * MN + e];
+    const int m = (int)(e / g.N), n = (int)(e % g.N);
+    double* cp = g.C + (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2 + n * g.c_n;
+    *cp = g.overwrite ? s : *cp + s;
+  }
+}
+
+// K in splits of at most OZ_KMAX (exactness), more when the output has few tiles
+static cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
+                           int64_t* launches) {
+  const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
+  const int64_t tm = (M + OZ_BM - 1) / OZ_BM, tn = (g.N + OZ_BN - 1) / OZ_BN;
+  const int64_t steps = (K + OZ_BK - 1) / OZ_BK;
+  int64_t ns = std::max<int64_t>((K + OZ_KMAX - 1) / OZ_KMAX, (2LL * num_sms + tm * tn - 1) / (tm * tn));
+  ns = std::min<int64_t>(ns, std::max<int64_t>(1, steps / 4));
+  ns = std::max<int64_t>(ns, (K + OZ_KMAX - 1) / OZ_KMAX);
+  const int kchunk = (int)(((steps + ns - 1) / ns) * OZ_BK);
+  const int nsplit = (int)((K + kchunk - 1) / kchunk);
+  if (nsplit > 1 && (int64_t)nsplit * M * g.N > scratch_cap) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)nsplit);
+  k_gemm_oz<<<grid, 128, 0, s>>>(g, kchunk, nsplit > 1 ? scratch : nullptr);
+  ++*launches;
+  if (nsplit > 1) {
+    const int64_t MN = M * g.N;
+    k_splitk_add_oz<<<(unsigned)std::min<int64_t>((MN + 255) / 256, 4096), 256, 0, s>>>(g, nsplit, scratch);
+    ++*launches;
+  }
+  return cudaGetLastError();
+}
+
+// four BF16 slices of dW~ (same layout), scale 2^-e with 2^e > max |dW~|
+__global__ void k_slice_dw(const double* __restrict__ dW, int64_t n, const unsigned long long* __restrict__ dwmax,
+                           int* __restrict__ e_out, __nv_bfloat16* __restrict__ planes) {
+  const double mx = __longlong_as_double((long long)*dwmax);
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *e_out = ex;
+  const double sc = ldexp(1.0, -ex);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double t = dW[i] * sc;  // |t| < 1
+#pragma unroll
+    for (int k = 0; k < OZ_NS; ++k) {
+      t = t * 128.0;
+      const double m = rint(t);
+      t = t - m;
+      planes[k * n + i] = __float2bfloat16_rn((float)(m * (1.0 / (double)(1ull << (7 * (k + 1))))));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -448,7 +655,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
     const Triple T = trip[t];
     e = launch_gemm_fp64(&P, h->d_triples, t, 1, W.G, s);
     if (e != cudaSuccess) break;
-    AdjArgs A;
+    AdjArgs A{};  // value-initialised: optional pointers (dwmax) are null unless set
     A.o = o; A.v = v; A.i = T.i; A.j = T.j; A.k = T.k;
     A.w = gE * (double)T.m / 3.0;
     A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v;
@@ -503,6 +710,204 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
     }
     if (e != cudaSuccess) break;
     // disconnected term and denominators
+    const unsigned gb2 = (unsigned)((v2 + 255) / 256);
+    for (int mode = 0; mode < 3; ++mode) {
+      if (g->ovov) k_dovs<<<gb2, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, c->t1, W.dOVS);
+      if (g->t1) k_dt1<<<(unsigned)v, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
+    }
+    if (g->eps_v) k_deps_v<<<(unsigned)v, 256, 0, s>>>(v, W.dD, g->eps_v);
+    if (g->eps_o) k_deps_o<<<1, 1024, 0, s>>>(v3, W.dD, T.i, T.j, T.k, g->eps_o);
+    h->n_launches += 8;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && g->ovov) {
+    k_dovov<<<1024, 256, 0, s>>>(o, v, W.dOVS, g->ovov);
+    ++h->n_launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && e_out) {
+    e = launch_reduce_total(W.shares, nt, e_out, s);
+    ++h->n_launches;
+  }
+  if (e != cudaSuccess) return fail(TE_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
+  return TE_OK;
+}
+
+}  // namespace te
+
+namespace te {
+
+// ---------------------------------------------------------------------------
+// the adjoint with the contractions on the tensor cores (exact BF16 slices)
+// ---------------------------------------------------------------------------
+
+static int64_t oz_scratch_cap(int64_t o, int64_t v, int num_sms) {
+  const int64_t splits = std::max<int64_t>((v * v + OZ_KMAX - 1) / OZ_KMAX + 1, 2LL * num_sms);
+  return splits * std::max(v * v, o * v);
+}
+
+size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms) {
+  const int64_t v3 = v * v * v, nt = num_unique_triples(o);
+  const int64_t nblk = (v3 + 255) / 256;
+  auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
+  return tc_slices_bytes((int)o, (int)v) + 1024 + a(o * v * v * o) + a(o * o * v * o) + a(o * v * o * v) +
+         a(3 * v3) + 3 * a(v3) + a(v3) /* dW slices: 4 x 2 B */ + a(o * v * o * v) + a(nblk) +
+         a(std::max<int64_t>(1, nt)) + a(oz_scratch_cap(o, v, num_sms)) + a(4) + 1024;
+}
+
+te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
+                     cudaStream_t s) {
+  const int o = (int)c->nocc, v = (int)c->nvir;
+  const int64_t v2 = (int64_t)v * v, v3 = v2 * v, nt = num_unique_triples(o);
+  te_status st = ensure_workspace_public(h, vjp_tc_bytes(o, v, h->num_sms));
+  if (st != TE_OK) return st;
+  st = ensure_triples_public(h, o);
+  if (st != TE_OK) return st;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023));
+  SliceSet S;
+  st = tc_prepare_slices(c, base, &S, s);
+  if (st != TE_OK) return st;
+  char* p = base + ((tc_slices_bytes(o, v) + 1023) & ~size_t(1023));
+  auto take = [&](int64_t n) {
+    double* r = reinterpret_cast<double*>(p);
+    p += ((size_t)n * 8 + 255) & ~size_t(255);
+    return r;
+  };
+  VjpWork W;
+  W.t2L = take((int64_t)o * v * v * o);
+  W.nooT = take((int64_t)o * o * v * o);
+  W.ovs = take((int64_t)o * v * o * v);
+  W.G = take(3 * v3);
+  W.dW = take(v3);
+  W.dY = take(v3);
+  W.dD = take(v3);
+  __nv_bfloat16* dWs = reinterpret_cast<__nv_bfloat16*>(take(v3));  // 4 planes of v^3 BF16
+  W.dOVS = take((int64_t)o * v * o * v);
+  const int64_t nblk = (v3 + 255) / 256;
+  W.epart = take(nblk);
+  W.shares = take(std::max<int64_t>(1, nt));
+  const int64_t cap = oz_scratch_cap(o, v, h->num_sms);
+  W.splitk = take(cap);
+  // per-triple scalars: max |dW~| (bit pattern) and the exponent of its slices
+  unsigned long long* dwmax = reinterpret_cast<unsigned long long*>(take(4));
+  int* dwexp = reinterpret_cast<int*>(dwmax + 1);
+
+  auto zero = [&](double* ptr, int64_t n) {
+    return ptr ? cudaMemsetAsync(ptr, 0, sizeof(double) * n, s) : cudaSuccess;
+  };
+  cudaError_t e = cudaSuccess;
+  e = e ? e : zero(g->eps_o, o);
+  e = e ? e : zero(g->eps_v, v);
+  e = e ? e : zero(g->ovvv, (int64_t)o * v3);
+  e = e ? e : zero(g->ooov, (int64_t)o * o * o * v);
+  e = e ? e : zero(g->ovov, (int64_t)o * v * o * v);
+  e = e ? e : zero(g->t1, (int64_t)o * v);
+  e = e ? e : zero(g->t2, (int64_t)o * o * v2);
+  e = e ? e : zero(W.dOVS, (int64_t)o * v * o * v);
+  if (e != cudaSuccess) return fail(TE_ECUDA, "memset: %s", cudaGetErrorString(e));
+
+  Prepared P{};  // float64 ovs for the disconnected term
+  P.o = o;
+  P.v = v;
+  P.eps_o = c->eps_o;
+  P.eps_v = c->eps_v;
+  P.ovvv = c->ovvv;
+  P.t2 = c->t2;
+  P.t1 = c->t1;
+  P.t2L = W.t2L;
+  P.nooT = W.nooT;
+  P.ovs = W.ovs;
+  e = launch_prep_fp64(c, &P, s);
+  if (e != cudaSuccess) return fail(TE_ECUDA, "prep: %s", cudaGetErrorString(e));
+
+  using bf = __nv_bfloat16;
+  const bf* sO = static_cast<const bf*>(S.ovvv);
+  const bf* sT = static_cast<const bf*>(S.t2);
+  const bf* sL = static_cast<const bf*>(S.t2L);
+  const bf* sN = static_cast<const bf*>(S.nooT);
+  const int64_t vp = S.vp, op = S.op;
+  const int* EX = S.exps;  // 0 ovvv, 1 t2, 2 t2L, 3 nooT
+
+  std::vector<Triple> trip = unique_triples(o);
+  auto run = [&](const OzView& gv) {
+    if (e == cudaSuccess) e = gemm_oz(gv, h->num_sms, W.splitk, cap, s, &h->n_launches);
+  };
+  for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
+    const Triple T = trip[t];
+    // forward G blocks, natural [g][x][y][z], four K segments each
+    for (int gi = 0; gi < 3; ++gi) {
+      int pp, qq, rr;
+      if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
+      else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
+      else { pp = T.k; qq = T.i; rr = T.j; }
+      double* Gg = W.G + gi * v3;
+      // S1: sum_d ovvv[p,x,y,d] t2[r,q,z,d]
+      run(OzView{sO + pp * S.ovvv_p, sT + ((int64_t)rr * o + qq) * S.t2_rq, S.ovvv_plane, S.t2_plane, Gg, v, v, v, v,
+                 1, v * vp, vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, EX + 0, EX + 1, 1});
+      // S2: sum_d ovvv[q,y,x,d] t2[r,p,z,d]
+      run(OzView{sO + qq * S.ovvv_p, sT + ((int64_t)rr * o + pp) * S.t2_rq, S.ovvv_plane, S.t2_plane, Gg, v, v, v, v,
+                 1, vp, v * vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, EX + 0, EX + 1, 0});
+      // S3: -sum_l t2[l,p,y,x] ooov[q,l,r,z] = sum_l t2L[p][y][x][l] nooT[q][r][z][l]
+      run(OzView{sL + pp * S.t2L_q, sN + ((int64_t)qq * o + rr) * S.nooT_pr, S.t2L_plane, S.nooT_plane, Gg, v, v, v,
+                 o, 1, op, v * op, 1, 0, 1, 0, op, v2, v, 1, 1.0, EX + 2, EX + 3, 0});
+      // S4: -sum_l t2[l,q,x,y] ooov[p,l,r,z] = sum_l t2L[q][x][y][l] nooT[p][r][z][l]
+      run(OzView{sL + qq * S.t2L_q, sN + ((int64_t)pp * o + rr) * S.nooT_pr, S.t2L_plane, S.nooT_plane, Gg, v, v, v,
+                 o, 1, v * op, op, 1, 0, 1, 0, op, v2, v, 1, 1.0, EX + 2, EX + 3, 0});
+    }
+    if (e != cudaSuccess) break;
+    AdjArgs A{};  // value-initialised: optional pointers (dwmax) are null unless set
+    A.o = o; A.v = v; A.i = T.i; A.j = T.j; A.k = T.k;
+    A.w = gE * (double)T.m / 3.0;
+    A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v;
+    A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart; A.dwmax = dwmax;
+    cudaMemsetAsync(dwmax, 0, 8, s);
+    k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
+    k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
+    k_slice_dw<<<(unsigned)std::min<int64_t>((v3 + 255) / 256, 8192), 256, 0, s>>>(W.dW, v3, dwmax, dwexp, dWs);
+    h->n_launches += 4;
+    for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
+      int pp, qq, rr;
+      if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
+      else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
+      else { pp = T.k; qq = T.i; rr = T.j; }
+      int64_t gx, gy, gz;  // Gamma[x,y,z] strides in dW~ (and its slice planes)
+      if (gi == 0) { gx = v2; gy = v; gz = 1; }
+      else if (gi == 1) { gx = v; gy = 1; gz = v2; }
+      else { gx = 1; gy = v2; gz = v; }
+      const bf* t2rq = sT + ((int64_t)rr * o + qq) * S.t2_rq;
+      const bf* t2rp = sT + ((int64_t)rr * o + pp) * S.t2_rq;
+      if (g->ovvv) {
+        // (a) dovvv[p,x,y,d] += sum_z G[x,y,z] t2[r,q,z,d]
+        run(OzView{dWs, t2rq, v3, S.t2_plane, g->ovvv + (int64_t)pp * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
+                   v2, v, 1, 1.0, dwexp, EX + 1, 0});
+        // (b) dovvv[q,y,x,d] += sum_z G[x,y,z] t2[r,p,z,d]
+        run(OzView{dWs, t2rp, v3, S.t2_plane, g->ovvv + (int64_t)qq * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
+                   v, v2, 1, 1.0, dwexp, EX + 1, 0});
+      }
+      if (g->t2) {
+        // (c) dt2[r,q,z,d] += sum_xy G[x,y,z] ovvv[p,x,y,d]
+        run(OzView{dWs, sO + pp * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + qq) * v2, v, 1, v, v, v,
+                   gz, 0, gx, gy, v * vp, vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0});
+        // (d) dt2[r,p,z,d] += sum_xy G[x,y,z] ovvv[q,y,x,d]
+        run(OzView{dWs, sO + qq * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + pp) * v2, v, 1, v, v, v,
+                   gz, 0, gx, gy, vp, v * vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0});
+        // (e) dt2[l,p,y,x] -= sum_z G[x,y,z] ooov[q,l,r,z]; ooov[q,l,r,z] = -nooT[q][r][z][l]
+        run(OzView{dWs, sN + ((int64_t)qq * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)pp * v2, v, v,
+                   o, v, 1, gx, gy, gz, 0, op, 0, 1, 1, v, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0});
+        // (g) dt2[l,q,x,y] -= sum_z G[x,y,z] ooov[p,l,r,z]
+        run(OzView{dWs, sN + ((int64_t)pp * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)qq * v2, v, v,
+                   o, v, 1, gx, gy, gz, 0, op, 0, 1, v, 1, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0});
+      }
+      if (g->ooov) {
+        // (f) dooov[q,l,r,z] -= sum_xy t2[l,p,y,x] G[x,y,z]; t2[l,p,y,x] = t2L[p][y][x][l]
+        run(OzView{sL + pp * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)qq * o * o + rr) * v, o, 1, v, v,
+                   v, 1, 0, op, v * op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0});
+        // (h) dooov[p,l,r,z] -= sum_xy t2[l,q,x,y] G[x,y,z]; t2[l,q,x,y] = t2L[q][x][y][l]
+        run(OzView{sL + qq * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)pp * o * o + rr) * v, o, 1, v, v,
+                   v, 1, 0, v * op, op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0});
+      }
+    }
+    if (e != cudaSuccess) break;
     const unsigned gb2 = (unsigned)((v2 + 255) / 256);
     for (int mode = 0; mode < 3; ++mode) {
       if (g->ovov) k_dovs<<<gb2, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, c->t1, W.dOVS);

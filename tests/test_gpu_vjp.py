@@ -1,7 +1,10 @@
-"""Adjoint of E(T) (t_energy_vjp) through the C ABI.
+"""Adjoint of E(T) (t_energy_vjp) through the C ABI, float64 ("fp64") and
+with the contractions on the tensor cores in exact BF16 slices ("ozaki").
 
 * element by element against the oracle's reverse-mode gradient, on ragged
-  shapes with unsorted orbital energies and on the o8v40 workload;
+  shapes with unsorted orbital energies and on the o8v40 workload (float64:
+  1e-10 of each tensor's largest entry; exact-slice: 1e-6, the bar for
+  gradients);
 * Euler identities (E is homogeneous of degree 4 in the integrals and
   amplitudes together and of degree -1 in the orbital energies);
 * central differences of the float64 GPU energy along a random direction;
@@ -38,43 +41,62 @@ def assert_grads_close(g, ref, rtol=1e-10):
         assert err <= rtol * scale, (n, err, scale)
 
 
+RTOL = {"fp64": 1e-10, "ozaki": 1e-6}
+ETOL = {"fp64": 1e-12, "ozaki": 1e-7}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
 @pytest.mark.parametrize("o,v,seed", [(2, 3, 1), (3, 7, 2), (4, 12, 3), (5, 17, 4), (3, 70, 5), (2, 131, 6)])
-def test_matches_oracle_gradient(te, o, v, seed):
+def test_matches_oracle_gradient(te, o, v, seed, prec):
     cl = tegen.make_cluster(o, v, 4 * (o + v), seed)
     arrs = shuffled(cl.arrays(), seed)
     arrs["t1"] = arrs["t1"] * 50.0
     e_ref, g_ref = O.t_energy_grad(O.inputs(**arrs))
-    e, g = te.t_energy_vjp(dev(arrs))
-    assert abs(float(e) - e_ref) <= 1e-12 * abs(e_ref) + 1e-15
-    assert_grads_close(g, g_ref)
+    e, g = te.t_energy_vjp(dev(arrs), precision=prec)
+    assert abs(float(e) - e_ref) <= ETOL[prec] * abs(e_ref) + 1e-15
+    assert_grads_close(g, g_ref, RTOL[prec])
 
 
-def test_o8v40_matches_oracle_gradient(te):
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_o8v40_matches_oracle_gradient(te, prec):
     cl = tegen.make_cluster(*tegen.WORKLOADS["o8v40"])
     arrs = cl.arrays()
     e_ref, g_ref = O.t_energy_grad(O.inputs(**arrs))
-    e, g = te.t_energy_vjp(dev(arrs), gE=-0.75)
-    assert abs(float(e) - e_ref) <= 1e-12 * abs(e_ref)
-    assert_grads_close(g, {n: -0.75 * g_ref[n] for n in NAMES})
+    e, g = te.t_energy_vjp(dev(arrs), gE=-0.75, precision=prec)
+    assert abs(float(e) - e_ref) <= ETOL[prec] * abs(e_ref)
+    assert_grads_close(g, {n: -0.75 * g_ref[n] for n in NAMES}, RTOL[prec])
 
 
-def test_single_occupied_orbital_gives_zero(te):
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_single_occupied_orbital_gives_zero(te, prec):
     cl = tegen.make_cluster(1, 9, 40, 3)
-    e, g = te.t_energy_vjp(dev(cl.arrays()))
+    e, g = te.t_energy_vjp(dev(cl.arrays()), precision=prec)
     assert float(e) == 0.0
     for n in NAMES:
         assert float(g[n].abs().max()) == 0.0, n
 
 
-def test_euler_identities(te):
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("ozaki", 1e-6)])
+def test_euler_identities(te, prec, tol):
     cl = tegen.make_cluster(6, 48, 216, 11)
     a = dev(cl.arrays())
-    e, g = te.t_energy_vjp(a)
+    e, g = te.t_energy_vjp(a, precision=prec)
     e = float(e)
     deg4 = sum(float((a[n] * g[n]).sum()) for n in AMPS)
     degm1 = sum(float((a[n] * g[n]).sum()) for n in ("eps_o", "eps_v"))
-    assert abs(deg4 - 4.0 * e) <= 1e-11 * abs(e)
-    assert abs(degm1 + e) <= 1e-11 * abs(e)
+    assert abs(deg4 - 4.0 * e) <= tol * abs(e)
+    assert abs(degm1 + e) <= tol * abs(e)
+
+
+def test_exact_slice_gradient_against_float64_o16v120(te):
+    """The nocc=16 nvir=120 workload: the tensor-core adjoint against the
+    float64 adjoint, every tensor within 1e-6 of its largest entry."""
+    cl = tegen.make_cluster(*tegen.WORKLOADS["o16v120"])
+    a = dev(cl.arrays())
+    e64, g64 = te.t_energy_vjp(a, precision="fp64")
+    eoz, goz = te.t_energy_vjp(a, precision="ozaki")
+    assert abs(float(eoz) - float(e64)) <= 1e-7
+    assert_grads_close(goz, {n: g64[n].cpu().numpy() for n in NAMES}, 1e-6)
 
 
 def test_directional_central_difference(te):
@@ -92,22 +114,24 @@ def test_directional_central_difference(te):
     assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
 
 
-def test_deterministic_and_mode_independent(te):
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_deterministic(te, prec):
     cl = tegen.make_cluster(4, 24, 96, 2)
     a = dev(cl.arrays())
-    e0, g0 = te.t_energy_vjp(a)
-    e1, g1 = te.t_energy_vjp(a, precision="ozaki")
+    e0, g0 = te.t_energy_vjp(a, precision=prec)
+    e1, g1 = te.t_energy_vjp(a, precision=prec)
     assert float(e0) == float(e1)
     for n in NAMES:
         assert torch.equal(g0[n], g1[n]), n
 
 
-def test_autograd_function_uses_the_adjoint(te):
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_autograd_function_uses_the_adjoint(te, prec):
     cl = tegen.make_cluster(3, 20, 92, 4)
     a = dev(cl.arrays())
     leaves = [a[n].clone().requires_grad_(True) for n in NAMES]
-    E = te.TEnergy.apply(*leaves, "fp64")
+    E = te.TEnergy.apply(*leaves, prec)
     (2.0 * E).backward()
-    _, g = te.t_energy_vjp(a, gE=2.0)
+    _, g = te.t_energy_vjp(a, gE=2.0, precision=prec)
     for n, leaf in zip(NAMES, leaves):
         torch.testing.assert_close(leaf.grad, g[n], rtol=1e-13, atol=0)
