@@ -44,6 +44,7 @@ struct AdjArgs {
   double* dD;           // [v^3]
   double* epart;        // per-block partial energies (unweighted by gE: m/3 e)
   unsigned long long* dwmax;  // if set: max |dW~| (bit pattern of a non-negative double)
+  double* dpart;        // per-block sums of dD (the orbital-energy gradient of the triple's occupied indices)
 };
 
 __device__ __forceinline__ double wt_at(const AdjArgs& A, int x, int y, int z) {
@@ -59,10 +60,10 @@ __device__ __forceinline__ double y_at(const AdjArgs& A, int x, int y, int z) {
 }
 
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
-  __shared__ double red[8];
+  __shared__ double red[8], redd[8];
   const int64_t v = A.v, v3 = v * v * v;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double contrib = 0.0;
+  double contrib = 0.0, dsum = 0.0;
   if (e < v3) {
     const int a = (int)(e / (v * v)), b = (int)((e / v) % v), c = (int)(e % v);
     // positions abc, acb, bac, bca, cab, cba
@@ -78,13 +79,21 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
     const double RW = R0(W0, W1, W2, W3, W4, W5);
     const double RY = R0(Y0, Y1, Y2, Y3, Y4, Y5);
     const double RV = RW + RY;
-    A.dW[e] = A.w * (2.0 * RW + RY) / D;
-    A.dY[e] = A.w * RW / D;
-    A.dD[e] = -A.w * W0 * RV / (D * D);
-    contrib = W0 * RV / D;
+    const double rD = 1.0 / D, q = A.w * rD;
+    A.dW[e] = q * (2.0 * RW + RY);
+    A.dY[e] = q * RW;
+    dsum = -q * W0 * RV * rD;
+    A.dD[e] = dsum;
+    contrib = W0 * RV * rD;
   }
-  for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = contrib;
+  for (int off = 16; off > 0; off >>= 1) {
+    contrib += __shfl_down_sync(0xffffffffu, contrib, off);
+    dsum += __shfl_down_sync(0xffffffffu, dsum, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = contrib;
+    redd[threadIdx.x >> 5] = dsum;
+  }
   if (A.dwmax) {
     double m = e < v3 ? fabs(A.dW[e]) : 0.0;
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
@@ -92,9 +101,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += red[w];
+    double s = 0.0, sd = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      s += red[w];
+      sd += redd[w];
+    }
     A.epart[blockIdx.x] = s;
+    A.dpart[blockIdx.x] = sd;
   }
 }
 
@@ -311,22 +324,80 @@ __global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* _
       for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[l][i][j][q] = 0.f;
+  // operands contiguous along k (K2 = 1, unit stride) and 16-byte aligned load
+  // eight slices' worth of k per instruction; the others element by element
+  const bool a_vec = K2 == 1 && g.a_k1 == 1 && g.a_ps % 8 == 0 &&
+                     (reinterpret_cast<uintptr_t>(g.A + a_row) & 15) == 0;
+  const bool b_vec = K2 == 1 && g.b_k1 == 1 && g.b_ps % 8 == 0 &&
+                     (reinterpret_cast<uintptr_t>(g.B + b_col) & 15) == 0;
   int k1 = (kb + lk) / K2, k2 = (kb + lk) % K2;  // cursor of this thread's first k
   for (int k0 = kb; k0 < ke; k0 += OZ_BK) {
-    int c1 = k1, c2 = k2;
-#pragma unroll 4
-    for (int u = 0; u < 16; ++u) {
-      const bool k_ok = k0 + lk + u < ke;
-      const int64_t ka = (int64_t)c1 * g.a_k1 + (int64_t)c2 * g.a_k2;
-      const int64_t kbo = (int64_t)c1 * g.b_k1 + (int64_t)c2 * g.b_k2;
+    if (a_vec) {
 #pragma unroll
-      for (int sl = 0; sl < OZ_NS; ++sl) {
-        As[sl][lr][lk + u] = (am_ok && k_ok) ? g.A[a_row + ka + sl * g.a_ps] : __float2bfloat16_rn(0.f);
-        Bs[sl][lr][lk + u] = (bn_ok && k_ok) ? g.B[b_col + kbo + sl * g.b_ps] : __float2bfloat16_rn(0.f);
+      for (int u = 0; u < 16; u += 8) {
+        const int kk = k0 + lk + u;
+#pragma unroll
+        for (int sl = 0; sl < OZ_NS; ++sl) {
+          uint4 val = make_uint4(0u, 0u, 0u, 0u);
+          const __nv_bfloat16* src = g.A + a_row + kk + sl * g.a_ps;
+          if (am_ok && kk + 8 <= ke) {
+            val = *reinterpret_cast<const uint4*>(src);
+          } else if (am_ok) {
+            __align__(16) __nv_bfloat16 tmp[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tmp[q] = kk + q < ke ? src[q] : __float2bfloat16_rn(0.f);
+            val = *reinterpret_cast<const uint4*>(tmp);
+          }
+          *reinterpret_cast<uint4*>(&As[sl][lr][lk + u]) = val;
+        }
       }
-      if (++c2 == K2) {
-        c2 = 0;
-        ++c1;
+    } else {
+      int c1 = k1, c2 = k2;
+#pragma unroll 4
+      for (int u = 0; u < 16; ++u) {
+        const bool k_ok = k0 + lk + u < ke;
+        const int64_t ka = (int64_t)c1 * g.a_k1 + (int64_t)c2 * g.a_k2;
+#pragma unroll
+        for (int sl = 0; sl < OZ_NS; ++sl)
+          As[sl][lr][lk + u] = (am_ok && k_ok) ? g.A[a_row + ka + sl * g.a_ps] : __float2bfloat16_rn(0.f);
+        if (++c2 == K2) {
+          c2 = 0;
+          ++c1;
+        }
+      }
+    }
+    if (b_vec) {
+#pragma unroll
+      for (int u = 0; u < 16; u += 8) {
+        const int kk = k0 + lk + u;
+#pragma unroll
+        for (int sl = 0; sl < OZ_NS; ++sl) {
+          uint4 val = make_uint4(0u, 0u, 0u, 0u);
+          const __nv_bfloat16* src = g.B + b_col + kk + sl * g.b_ps;
+          if (bn_ok && kk + 8 <= ke) {
+            val = *reinterpret_cast<const uint4*>(src);
+          } else if (bn_ok) {
+            __align__(16) __nv_bfloat16 tmp[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tmp[q] = kk + q < ke ? src[q] : __float2bfloat16_rn(0.f);
+            val = *reinterpret_cast<const uint4*>(tmp);
+          }
+          *reinterpret_cast<uint4*>(&Bs[sl][lr][lk + u]) = val;
+        }
+      }
+    } else {
+      int c1 = k1, c2 = k2;
+#pragma unroll 4
+      for (int u = 0; u < 16; ++u) {
+        const bool k_ok = k0 + lk + u < ke;
+        const int64_t kbo = (int64_t)c1 * g.b_k1 + (int64_t)c2 * g.b_k2;
+#pragma unroll
+        for (int sl = 0; sl < OZ_NS; ++sl)
+          Bs[sl][lr][lk + u] = (bn_ok && k_ok) ? g.B[b_col + kbo + sl * g.b_ps] : __float2bfloat16_rn(0.f);
+        if (++c2 == K2) {
+          c2 = 0;
+          ++c1;
+        }
       }
     }
     // advance the cursor by OZ_BK
@@ -522,18 +593,19 @@ __global__ void __launch_bounds__(256) k_deps_v(int v, const double* __restrict_
   if (threadIdx.x == 0) deps_v[x] -= t;
 }
 
-// deps_o[i], [j], [k] += sum_abc dD (fixed-order block sum)
-__global__ void __launch_bounds__(1024) k_deps_o(int64_t n, const double* __restrict__ dD, int i, int j, int k,
-                                                  double* __restrict__ deps_o) {
-  __shared__ double red[32];
+// deps_o[i], [j], [k] += sum_abc dD, from the adjoint kernel's per-block sums
+// (fixed-order block sum)
+__global__ void __launch_bounds__(256) k_deps_o(int64_t n, const double* __restrict__ dpart, int i, int j, int k,
+                                                 double* __restrict__ deps_o) {
+  __shared__ double red[8];
   double s = 0.0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += dD[e];
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += dpart[e];
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int w = 0; w < 8; ++w) t += red[w];
     deps_o[i] += t;
     deps_o[j] += t;
     deps_o[k] += t;
@@ -576,7 +648,7 @@ __global__ void __launch_bounds__(256) k_sum_share(const double* __restrict__ pa
 // ---------------------------------------------------------------------------
 
 struct VjpWork {
-  double *t2L, *nooT, *ovs, *G, *dW, *dY, *dD, *dOVS, *epart, *shares, *splitk;
+  double *t2L, *nooT, *ovs, *G, *dW, *dY, *dD, *dOVS, *epart, *dpart, *shares, *splitk;
 };
 
 // doubles of split-K scratch: room for the partial tiles of a v x v output
@@ -587,7 +659,7 @@ size_t vjp_fp64_bytes(int64_t o, int64_t v) {
   const int64_t nblk = (v3 + 255) / 256;
   auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
   return a(o * v * v * o) + a(o * o * v * o) + a(o * v * o * v) + a(3 * v3) + 3 * a(v3) + a(o * v * o * v) +
-         a(nblk) + a(std::max<int64_t>(1, nt)) + a(splitk_cap(o, v)) + 1024;
+         2 * a(nblk) + a(std::max<int64_t>(1, nt)) + a(splitk_cap(o, v)) + 1024;
 }
 
 te_status ensure_workspace_public(Handle* h, size_t bytes);
@@ -618,6 +690,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
   W.dOVS = take((int64_t)o * v * o * v);
   const int64_t nblk = (v3 + 255) / 256;
   W.epart = take(nblk);
+  W.dpart = take(nblk);
   W.shares = take(std::max<int64_t>(1, nt));
   W.splitk = take(splitk_cap(o, v));
 
@@ -659,7 +732,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
     A.o = o; A.v = v; A.i = T.i; A.j = T.j; A.k = T.k;
     A.w = gE * (double)T.m / 3.0;
     A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v;
-    A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart;
+    A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart; A.dpart = W.dpart;
     k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
     k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
     h->n_launches += 3;
@@ -716,7 +789,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
       if (g->t1) k_dt1<<<(unsigned)v, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
     }
     if (g->eps_v) k_deps_v<<<(unsigned)v, 256, 0, s>>>(v, W.dD, g->eps_v);
-    if (g->eps_o) k_deps_o<<<1, 1024, 0, s>>>(v3, W.dD, T.i, T.j, T.k, g->eps_o);
+    if (g->eps_o) k_deps_o<<<1, 256, 0, s>>>(nblk, W.dpart, T.i, T.j, T.k, g->eps_o);
     h->n_launches += 8;
     e = cudaGetLastError();
   }
@@ -751,7 +824,7 @@ size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms) {
   const int64_t nblk = (v3 + 255) / 256;
   auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
   return tc_slices_bytes((int)o, (int)v) + 1024 + a(o * v * v * o) + a(o * o * v * o) + a(o * v * o * v) +
-         a(3 * v3) + 3 * a(v3) + a(v3) /* dW slices: 4 x 2 B */ + a(o * v * o * v) + a(nblk) +
+         a(3 * v3) + 3 * a(v3) + a(v3) /* dW slices: 4 x 2 B */ + a(o * v * o * v) + 2 * a(nblk) +
          a(std::max<int64_t>(1, nt)) + a(oz_scratch_cap(o, v, num_sms)) + a(4) + 1024;
 }
 
@@ -785,6 +858,7 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
   W.dOVS = take((int64_t)o * v * o * v);
   const int64_t nblk = (v3 + 255) / 256;
   W.epart = take(nblk);
+  W.dpart = take(nblk);
   W.shares = take(std::max<int64_t>(1, nt));
   const int64_t cap = oz_scratch_cap(o, v, h->num_sms);
   W.splitk = take(cap);
@@ -859,7 +933,7 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
     A.o = o; A.v = v; A.i = T.i; A.j = T.j; A.k = T.k;
     A.w = gE * (double)T.m / 3.0;
     A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v;
-    A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart; A.dwmax = dwmax;
+    A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart; A.dpart = W.dpart; A.dwmax = dwmax;
     cudaMemsetAsync(dwmax, 0, 8, s);
     k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
     k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
@@ -914,7 +988,7 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
       if (g->t1) k_dt1<<<(unsigned)v, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
     }
     if (g->eps_v) k_deps_v<<<(unsigned)v, 256, 0, s>>>(v, W.dD, g->eps_v);
-    if (g->eps_o) k_deps_o<<<1, 1024, 0, s>>>(v3, W.dD, T.i, T.j, T.k, g->eps_o);
+    if (g->eps_o) k_deps_o<<<1, 256, 0, s>>>(nblk, W.dpart, T.i, T.j, T.k, g->eps_o);
     h->n_launches += 8;
     e = cudaGetLastError();
   }
