@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--batch-stride", type=int, default=8,
                     help="with --workload batch96: time every s-th seed of the 96 (extrapolated by flop count)")
     ap.add_argument("--no-vjp", action="store_true",
-                    help="skip the adjoint measurement (nocc=16 nvir=120, float64)")
+                    help="skip the adjoint measurement (nocc=16 nvir=120, exact-slice and float64)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched measurement (16 clusters, nocc 8..20, nvir = 8 nocc)")
     return ap.parse_args()
@@ -362,26 +362,31 @@ def main():
         cq = tegen.make_cluster(oq, vq, nq, sq)
         qa = {n: torch.as_tensor(np.ascontiguousarray(x)).to(torch.device("cuda", local)) for n, x in cq.arrays().items()}
         tiny = tegen.make_cluster(2, 8, 40, 0)
-        te.t_energy_vjp({n: torch.as_tensor(x).cuda(local) for n, x in tiny.arrays().items()}, handle=h)
-        torch.cuda.synchronize()
-        barrier()
         v0 = torch.cuda.Event(enable_timing=True)
         v1 = torch.cuda.Event(enable_timing=True)
-        l0 = h.profile_read(reset=False)["launches"]
-        v0.record()
-        ev, _g = te.t_energy_vjp(qa, handle=h)
-        v1.record()
-        torch.cuda.synchronize()
-        vms = v0.elapsed_time(v1)
-        vt = torch.tensor([vms], device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(vt, op=torch.distributed.ReduceOp.MAX)
-        vms = float(vt.item())
         Fq = te.flop_count(oq, vq)
-        vjp = {"workload": f"o16v120: nocc={oq} nvir={vq} naux={nq} seed={sq}", "precision": "fp64",
-               "ms": vms, "gflops_3F": world * 3 * Fq / (vms / 1e3) / 1e9, "e_t_ha": float(ev),
-               "launches": h.profile_read(reset=False)["launches"] - l0}
-        del qa, _g
+        vjp = {"workload": f"o16v120: nocc={oq} nvir={vq} naux={nq} seed={sq}"}
+        for vprec in ("ozaki", "fp64"):
+            te.t_energy_vjp({n: torch.as_tensor(x).cuda(local) for n, x in tiny.arrays().items()},
+                            precision=vprec, handle=h)
+            torch.cuda.synchronize()
+            barrier()
+            l0 = h.profile_read(reset=False)["launches"]
+            v0.record()
+            ev, _g = te.t_energy_vjp(qa, precision=vprec, handle=h)
+            v1.record()
+            torch.cuda.synchronize()
+            vms = v0.elapsed_time(v1)
+            vt = torch.tensor([vms], device="cuda")
+            if world > 1:
+                torch.distributed.all_reduce(vt, op=torch.distributed.ReduceOp.MAX)
+            vms = float(vt.item())
+            vjp[vprec] = {"ms": vms, "gflops_3F": world * 3 * Fq / (vms / 1e3) / 1e9, "e_t_ha": float(ev),
+                          "launches": h.profile_read(reset=False)["launches"] - l0}
+            del _g
+        if "ozaki" in vjp and "fp64" in vjp:
+            vjp["speedup_vs_fp64"] = vjp["fp64"]["ms"] / vjp["ozaki"]["ms"]
+        del qa
 
     pk, pk_src = peaks()
     if prec == "fp64":

@@ -324,34 +324,100 @@ __global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* _
       for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[l][i][j][q] = 0.f;
-  // operands contiguous along k (K2 = 1, unit stride) and 16-byte aligned load
-  // eight slices' worth of k per instruction; the others element by element
-  const bool a_vec = K2 == 1 && g.a_k1 == 1 && g.a_ps % 8 == 0 &&
-                     (reinterpret_cast<uintptr_t>(g.A + a_row) & 15) == 0;
-  const bool b_vec = K2 == 1 && g.b_k1 == 1 && g.b_ps % 8 == 0 &&
-                     (reinterpret_cast<uintptr_t>(g.B + b_col) & 15) == 0;
+  // Loads: an operand that is contiguous along k (8 consecutive k in one k1
+  // row), or along its row index m / column index n, loads eight BF16 values
+  // per 16-byte instruction; others element by element.
+  auto aligned16 = [](const __nv_bfloat16* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; };
+  const bool a_kvec = g.a_ps % 8 == 0 && aligned16(g.A) &&
+                      ((K2 == 1 && g.a_k1 == 1) || (K2 % 8 == 0 && g.a_k2 == 1 && g.a_k1 % 8 == 0)) &&
+                      (g.a_m1 % 8 == 0 || g.M1 == 1) && (g.a_m2 % 8 == 0 || g.M2 == 1);
+  const bool b_kvec = g.b_ps % 8 == 0 && aligned16(g.B) &&
+                      ((K2 == 1 && g.b_k1 == 1) || (K2 % 8 == 0 && g.b_k2 == 1 && g.b_k1 % 8 == 0)) && g.b_n % 8 == 0;
+  const bool a_mvec = !a_kvec && g.a_ps % 8 == 0 && aligned16(g.A) &&
+                      ((g.M2 == 1 && g.a_m1 == 1) || (g.M2 % 8 == 0 && g.a_m2 == 1 && g.a_m1 % 8 == 0)) &&
+                      g.a_k1 % 8 == 0 && g.a_k2 % 8 == 0;
+  const bool b_nvec = !b_kvec && g.b_ps % 8 == 0 && aligned16(g.B) && g.b_n == 1 && g.b_k1 % 8 == 0 &&
+                      g.b_k2 % 8 == 0;
   int k1 = (kb + lk) / K2, k2 = (kb + lk) % K2;  // cursor of this thread's first k
   for (int k0 = kb; k0 < ke; k0 += OZ_BK) {
-    if (a_vec) {
+    if (a_kvec || b_kvec) {
 #pragma unroll
       for (int u = 0; u < 16; u += 8) {
         const int kk = k0 + lk + u;
+        const int q1 = kk / K2, q2 = kk % K2;
 #pragma unroll
-        for (int sl = 0; sl < OZ_NS; ++sl) {
-          uint4 val = make_uint4(0u, 0u, 0u, 0u);
-          const __nv_bfloat16* src = g.A + a_row + kk + sl * g.a_ps;
-          if (am_ok && kk + 8 <= ke) {
-            val = *reinterpret_cast<const uint4*>(src);
-          } else if (am_ok) {
-            __align__(16) __nv_bfloat16 tmp[8];
+        for (int op = 0; op < 2; ++op) {
+          const bool vec = op == 0 ? a_kvec : b_kvec;
+          if (!vec) continue;
+          const bool ok = op == 0 ? am_ok : bn_ok;
+          const __nv_bfloat16* src0 = op == 0 ? g.A + a_row + (int64_t)q1 * g.a_k1 + (int64_t)q2 * g.a_k2
+                                              : g.B + b_col + (int64_t)q1 * g.b_k1 + (int64_t)q2 * g.b_k2;
+          const int64_t ps = op == 0 ? g.a_ps : g.b_ps;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) tmp[q] = kk + q < ke ? src[q] : __float2bfloat16_rn(0.f);
-            val = *reinterpret_cast<const uint4*>(tmp);
+          for (int sl = 0; sl < OZ_NS; ++sl) {
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            const __nv_bfloat16* src = src0 + sl * ps;
+            if (ok && kk + 8 <= ke) {
+              val = *reinterpret_cast<const uint4*>(src);
+            } else if (ok) {
+              __align__(16) __nv_bfloat16 tmp[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) tmp[q] = kk + q < ke ? src[q] : __float2bfloat16_rn(0.f);
+              val = *reinterpret_cast<const uint4*>(tmp);
+            }
+            if (op == 0) *reinterpret_cast<uint4*>(&As[sl][lr][lk + u]) = val;
+            else *reinterpret_cast<uint4*>(&Bs[sl][lr][lk + u]) = val;
           }
-          *reinterpret_cast<uint4*>(&As[sl][lr][lk + u]) = val;
         }
       }
-    } else {
+    }
+    if (a_mvec || b_nvec) {
+      // item: 8 consecutive rows (columns) x one k; 8 groups x 32 k over 128 threads
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int grp = tid & 7, kq = (tid >> 3) + 16 * it;
+        const int kk = k0 + kq;
+        const bool k_ok = kk < ke;
+        const int q1 = k_ok ? kk / K2 : 0, q2 = k_ok ? kk % K2 : 0;
+#pragma unroll
+        for (int op = 0; op < 2; ++op) {
+          const bool vec = op == 0 ? a_mvec : b_nvec;
+          if (!vec) continue;
+          const int r0 = (op == 0 ? m0 : n0) + grp * 8;
+          const int lim = op == 0 ? M : N;
+          __nv_bfloat16(*dst)[OZ_BM][OZ_LD] = op == 0 ? As : Bs;
+          if (k_ok && r0 + 8 <= lim) {
+            const __nv_bfloat16* src0 =
+                op == 0 ? g.A + (int64_t)(r0 / (int)g.M2) * g.a_m1 + (int64_t)(r0 % (int)g.M2) * g.a_m2 +
+                              (int64_t)q1 * g.a_k1 + (int64_t)q2 * g.a_k2
+                        : g.B + (int64_t)r0 + (int64_t)q1 * g.b_k1 + (int64_t)q2 * g.b_k2;
+            const int64_t ps = op == 0 ? g.a_ps : g.b_ps;
+#pragma unroll
+            for (int sl = 0; sl < OZ_NS; ++sl) {
+              const uint4 val = *reinterpret_cast<const uint4*>(src0 + sl * ps);
+              const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&val);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) dst[sl][grp * 8 + q][kq] = e8[q];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int r = r0 + q;
+              const bool ok = k_ok && r < lim;
+              const int64_t off = !ok ? 0
+                                  : op == 0 ? (int64_t)(r / (int)g.M2) * g.a_m1 + (int64_t)(r % (int)g.M2) * g.a_m2 +
+                                                  (int64_t)q1 * g.a_k1 + (int64_t)q2 * g.a_k2
+                                            : (int64_t)r * g.b_n + (int64_t)q1 * g.b_k1 + (int64_t)q2 * g.b_k2;
+#pragma unroll
+              for (int sl = 0; sl < OZ_NS; ++sl)
+                dst[sl][grp * 8 + q][kq] =
+                    ok ? (op == 0 ? g.A[off + sl * g.a_ps] : g.B[off + sl * g.b_ps]) : __float2bfloat16_rn(0.f);
+            }
+          }
+        }
+      }
+    }
+    if (!a_kvec && !a_mvec) {
       int c1 = k1, c2 = k2;
 #pragma unroll 4
       for (int u = 0; u < 16; ++u) {
@@ -366,26 +432,7 @@ __global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* _
         }
       }
     }
-    if (b_vec) {
-#pragma unroll
-      for (int u = 0; u < 16; u += 8) {
-        const int kk = k0 + lk + u;
-#pragma unroll
-        for (int sl = 0; sl < OZ_NS; ++sl) {
-          uint4 val = make_uint4(0u, 0u, 0u, 0u);
-          const __nv_bfloat16* src = g.B + b_col + kk + sl * g.b_ps;
-          if (bn_ok && kk + 8 <= ke) {
-            val = *reinterpret_cast<const uint4*>(src);
-          } else if (bn_ok) {
-            __align__(16) __nv_bfloat16 tmp[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) tmp[q] = kk + q < ke ? src[q] : __float2bfloat16_rn(0.f);
-            val = *reinterpret_cast<const uint4*>(tmp);
-          }
-          *reinterpret_cast<uint4*>(&Bs[sl][lr][lk + u]) = val;
-        }
-      }
-    } else {
+    if (!b_kvec && !b_nvec) {
       int c1 = k1, c2 = k2;
 #pragma unroll 4
       for (int u = 0; u < 16; ++u) {
@@ -906,6 +953,22 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
   auto run = [&](const OzView& gv) {
     if (e == cudaSuccess) e = gemm_oz(gv, h->num_sms, W.splitk, cap, s, &h->n_launches);
   };
+  // The order of the two row indices (or of the two k indices) of a view is a
+  // free choice: put the unit-stride one second so the loads vectorise.
+  auto swapM = [](OzView gv) {
+    std::swap(gv.M1, gv.M2);
+    std::swap(gv.a_m1, gv.a_m2);
+    std::swap(gv.c_m1, gv.c_m2);
+    return gv;
+  };
+  auto swapK = [](OzView gv) {
+    std::swap(gv.K1, gv.K2);
+    std::swap(gv.a_k1, gv.a_k2);
+    std::swap(gv.b_k1, gv.b_k2);
+    return gv;
+  };
+  auto runI = [&](const OzView& gv, int gi) { run(gi == 2 ? swapM(gv) : gv); };   // rows (x, y) of Gamma
+  auto runII = [&](const OzView& gv, int gi) { run(gi == 2 ? swapK(gv) : gv); };  // k = (x, y) of Gamma
   for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
     const Triple T = trip[t];
     // forward G blocks, natural [g][x][y][z], four K segments each
@@ -952,33 +1015,33 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
       const bf* t2rp = sT + ((int64_t)rr * o + pp) * S.t2_rq;
       if (g->ovvv) {
         // (a) dovvv[p,x,y,d] += sum_z G[x,y,z] t2[r,q,z,d]
-        run(OzView{dWs, t2rq, v3, S.t2_plane, g->ovvv + (int64_t)pp * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
-                   v2, v, 1, 1.0, dwexp, EX + 1, 0});
+        runI(OzView{dWs, t2rq, v3, S.t2_plane, g->ovvv + (int64_t)pp * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
+                   v2, v, 1, 1.0, dwexp, EX + 1, 0}, gi);
         // (b) dovvv[q,y,x,d] += sum_z G[x,y,z] t2[r,p,z,d]
-        run(OzView{dWs, t2rp, v3, S.t2_plane, g->ovvv + (int64_t)qq * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
-                   v, v2, 1, 1.0, dwexp, EX + 1, 0});
+        runI(OzView{dWs, t2rp, v3, S.t2_plane, g->ovvv + (int64_t)qq * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
+                   v, v2, 1, 1.0, dwexp, EX + 1, 0}, gi);
       }
       if (g->t2) {
         // (c) dt2[r,q,z,d] += sum_xy G[x,y,z] ovvv[p,x,y,d]
-        run(OzView{dWs, sO + pp * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + qq) * v2, v, 1, v, v, v,
-                   gz, 0, gx, gy, v * vp, vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0});
+        runII(OzView{dWs, sO + pp * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + qq) * v2, v, 1, v, v, v,
+                   gz, 0, gx, gy, v * vp, vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0}, gi);
         // (d) dt2[r,p,z,d] += sum_xy G[x,y,z] ovvv[q,y,x,d]
-        run(OzView{dWs, sO + qq * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + pp) * v2, v, 1, v, v, v,
-                   gz, 0, gx, gy, vp, v * vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0});
+        runII(OzView{dWs, sO + qq * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + pp) * v2, v, 1, v, v, v,
+                   gz, 0, gx, gy, vp, v * vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0}, gi);
         // (e) dt2[l,p,y,x] -= sum_z G[x,y,z] ooov[q,l,r,z]; ooov[q,l,r,z] = -nooT[q][r][z][l]
-        run(OzView{dWs, sN + ((int64_t)qq * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)pp * v2, v, v,
-                   o, v, 1, gx, gy, gz, 0, op, 0, 1, 1, v, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0});
+        runI(OzView{dWs, sN + ((int64_t)qq * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)pp * v2, v, v,
+                   o, v, 1, gx, gy, gz, 0, op, 0, 1, 1, v, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0}, gi);
         // (g) dt2[l,q,x,y] -= sum_z G[x,y,z] ooov[p,l,r,z]
-        run(OzView{dWs, sN + ((int64_t)pp * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)qq * v2, v, v,
-                   o, v, 1, gx, gy, gz, 0, op, 0, 1, v, 1, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0});
+        runI(OzView{dWs, sN + ((int64_t)pp * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)qq * v2, v, v,
+                   o, v, 1, gx, gy, gz, 0, op, 0, 1, v, 1, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0}, gi);
       }
       if (g->ooov) {
         // (f) dooov[q,l,r,z] -= sum_xy t2[l,p,y,x] G[x,y,z]; t2[l,p,y,x] = t2L[p][y][x][l]
-        run(OzView{sL + pp * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)qq * o * o + rr) * v, o, 1, v, v,
-                   v, 1, 0, op, v * op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0});
+        runII(OzView{sL + pp * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)qq * o * o + rr) * v, o, 1, v, v,
+                   v, 1, 0, op, v * op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0}, gi);
         // (h) dooov[p,l,r,z] -= sum_xy t2[l,q,x,y] G[x,y,z]; t2[l,q,x,y] = t2L[q][x][y][l]
-        run(OzView{sL + qq * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)pp * o * o + rr) * v, o, 1, v, v,
-                   v, 1, 0, v * op, op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0});
+        runII(OzView{sL + qq * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)pp * o * o + rr) * v, o, 1, v, v,
+                   v, 1, 0, v * op, op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0}, gi);
       }
     }
     if (e != cudaSuccess) break;
