@@ -139,7 +139,10 @@ te_status t_energy_batched(te_handle h, const te_cluster* cs, int64_t n,
 /* Vector-Jacobian product of E(T): g.X = gE * dE/dX for every non-null member
  * of *g, every stored entry of every input treated as an independent variable
  * (no symmetrisation of t2 or of the integrals).  If e_out is non-null it
- * receives E(T) (one device double). */
+ * receives E(T) (one device double).  TE_FP64 runs every contraction in
+ * float64; the other modes run them on the tensor cores in exact 7-bit BF16
+ * slices (the TE_OZAKI scheme; gradients to ~1e-7 of each tensor's largest
+ * entry), with the epilogue and all sums in float64.  Deterministic. */
 te_status t_energy_vjp(te_handle h, const te_cluster* c, te_precision p,
                        double gE, double* e_out, te_cluster_grad* g,
                        te_stream_t s);
