@@ -103,8 +103,18 @@ typedef struct {
 typedef struct te_handle_s* te_handle;
 
 /* Create a handle bound to CUDA device `device`.  Allocates nothing on the
- * device until the first compute call.  *h is set to NULL on failure. */
-te_status te_create(te_handle* h, int device);
+ * device until the first compute call.  *h is set to NULL on failure.
+ *
+ * autotune_cache_path (nullable): a text file that keeps the tile shapes the
+ * autotuner picked (t_energy_batched tunes each new (nocc, nvir, mode) once)
+ * across handles and processes.  Read here if it exists: the first line names
+ * the format, the SM count and the compute capability, and entries written on
+ * another kind of GPU, malformed lines and shapes the tuner would not propose
+ * are ignored.  Rewritten (whole, through a temporary file and a rename) after
+ * every new tuning; a file that cannot be written is not an error, the tuning
+ * then only lasts for the handle.  A tile shape changes the speed, never the
+ * result beyond summation order inside a tile. */
+te_status te_create(te_handle* h, int device, const char* autotune_cache_path);
 
 /* Free the handle and its workspace (synchronises the device first). */
 te_status te_destroy(te_handle h);
@@ -155,6 +165,18 @@ te_status te_sync(te_handle h, te_stream_t s);
  * (before any call), so a caller can check memory up front. */
 te_status te_workspace_bytes(te_handle h, const te_cluster* c, te_precision p,
                              size_t* bytes);
+
+/* Allocate the handle's workspace (and its table of occupied triples) for a
+ * cluster of c->nocc, c->nvir in mode p now, instead of on the first call, so
+ * that later calls of that size or smaller allocate nothing.  Only nocc and
+ * nvir are read; the array pointers may be NULL.  what: TE_RESERVE_ENERGY for
+ * t_energy / t_energy_triples / t_energy_batched, TE_RESERVE_VJP for
+ * t_energy_vjp, or both.  TE_ENOMEM if the device cannot hold it (the handle
+ * keeps what it had); TE_EUNSUPPORTED inside a stream capture.  Synchronises
+ * the device when a smaller workspace is replaced. */
+#define TE_RESERVE_ENERGY 1
+#define TE_RESERVE_VJP 2
+te_status te_reserve(te_handle h, const te_cluster* c, te_precision p, int what);
 
 /* Launch accounting of one handle.  Kernel launches are always counted; with
  * profiling on, CUDA events are recorded on the caller's stream around every

@@ -14,6 +14,7 @@ Precision: "fp64", "tf32", "bf16x3", "tf32x3".
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
@@ -40,7 +41,9 @@ def flop_count(nocc: int, nvir: int) -> float:
 class Handle:
     """Owns the library handle (workspace) for one CUDA device."""
 
-    def __init__(self, device=None):
+    def __init__(self, device=None, autotune_cache=None):
+        """autotune_cache: optional path of a text file that keeps the tile
+        shapes the autotuner picks across handles and processes."""
         lib = _lib.load()
         if device is None:
             dev = torch.cuda.current_device()
@@ -49,7 +52,8 @@ class Handle:
         else:
             dev = torch.device(device).index or 0
         h = ctypes.c_void_p()
-        _lib.check(lib.te_create(ctypes.byref(h), dev))
+        path = None if autotune_cache is None else os.fsencode(autotune_cache)
+        _lib.check(lib.te_create(ctypes.byref(h), dev, path))
         self._h = h
         self.device = dev
 
@@ -101,6 +105,14 @@ class Handle:
         pr = _lib.TeProfile()
         _lib.check(_lib.load().te_profile_read(self.ptr, ctypes.byref(pr), 1 if reset else 0))
         return {f: getattr(pr, f) for f, _ in pr._fields_}
+
+    def reserve(self, nocc: int, nvir: int, precision="fp64", energy=True, vjp=False):
+        """Allocate the workspace for clusters up to (nocc, nvir) now, for the
+        energy calls and / or the adjoint, so that later calls allocate nothing."""
+        c = _lib.TeCluster()
+        c.nocc, c.nvir = int(nocc), int(nvir)
+        what = (1 if energy else 0) | (2 if vjp else 0)
+        _lib.check(_lib.load().te_reserve(self.ptr, ctypes.byref(c), _prec(precision), what))
 
     def workspace_bytes(self, cluster, precision="fp64") -> int:
         t = _tensors(cluster, self.device)

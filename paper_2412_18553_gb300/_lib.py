@@ -34,7 +34,8 @@ class TeProfile(ctypes.Structure):
 
 # (name, restype, argtypes) for every function of include/tenergy.h
 SIGNATURES = [
-    ("te_create", ctypes.c_int, [ctypes.POINTER(c_void_p), ctypes.c_int]),
+    ("te_create", ctypes.c_int, [ctypes.POINTER(c_void_p), ctypes.c_int, ctypes.c_char_p]),
+    ("te_reserve", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int, ctypes.c_int]),
     ("te_destroy", ctypes.c_int, [c_void_p]),
     ("t_energy", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int, c_void_p, c_void_p]),
     ("t_energy_triples", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int,

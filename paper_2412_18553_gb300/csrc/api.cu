@@ -289,6 +289,48 @@ void prof_end(Handle* h, size_t start, cudaStream_t s) {
   if (start != SIZE_MAX) cudaEventRecord(h->ev_pool[start + 1], s);
 }
 
+std::string tune_header(const Handle* h) {
+  char buf[96];
+  std::snprintf(buf, sizeof buf, "tenergy-autotune 1 sms=%d cc=%d.%d", h->num_sms, h->cc_major, h->cc_minor);
+  return buf;
+}
+
+// Entries of a file written for another kind of GPU, and malformed lines, are
+// skipped; the tuner checks each entry against its candidates before use.
+static void tune_load(Handle* h) {
+  FILE* f = std::fopen(h->tune_path.c_str(), "r");
+  if (!f) return;
+  char line[256];
+  if (std::fgets(line, sizeof line, f)) {
+    std::string first(line);
+    while (!first.empty() && (first.back() == '\n' || first.back() == '\r')) first.pop_back();
+    if (first == tune_header(h)) {
+      while (std::fgets(line, sizeof line, f)) {
+        int o, v, mode, tb, nnt;
+        char extra;
+        if (std::sscanf(line, "%d %d %d %d %d %c", &o, &v, &mode, &tb, &nnt, &extra) == 5)
+          h->tune_file[std::make_tuple(o, v, mode)] = std::make_pair(tb, nnt);
+      }
+    }
+  }
+  std::fclose(f);
+}
+
+void tune_save(Handle* h) {
+  if (h->tune_path.empty()) return;
+  auto all = h->tune_file;
+  for (const auto& kv : h->tuned) all[kv.first] = kv.second;
+  const std::string tmp = h->tune_path + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  bool ok = std::fprintf(f, "%s\n", tune_header(h).c_str()) > 0;
+  for (const auto& kv : all)
+    ok = ok && std::fprintf(f, "%d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                            std::get<2>(kv.first), kv.second.first, kv.second.second) > 0;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok || std::rename(tmp.c_str(), h->tune_path.c_str()) != 0) std::remove(tmp.c_str());
+}
+
 te_status ensure_workspace_public(Handle* h, size_t bytes) { return ensure_workspace(h, bytes); }
 te_status ensure_triples_public(Handle* h, int nocc) { return ensure_triples(h, nocc); }
 
@@ -304,7 +346,7 @@ using namespace te;
 
 extern "C" {
 
-te_status te_create(te_handle* out, int device) {
+te_status te_create(te_handle* out, int device, const char* autotune_cache_path) {
   if (!out) return fail(TE_EINVAL, "null handle pointer");
   *out = nullptr;
   int ndev = 0;
@@ -328,6 +370,10 @@ te_status te_create(te_handle* out, int device) {
     cudaGetLastError();
     delete h;
     return fail(TE_ENOMEM, "error-word allocation failed");
+  }
+  if (autotune_cache_path && *autotune_cache_path) {
+    h->tune_path = autotune_cache_path;
+    tune_load(h);
   }
   *out = reinterpret_cast<te_handle>(h);
   return TE_OK;
@@ -530,6 +576,25 @@ te_status te_workspace_bytes(te_handle hh, const te_cluster* c, te_precision p, 
     return TE_OK;
   }
   return tc_workspace_bytes(h, c, p, bytes);
+}
+
+te_status te_reserve(te_handle hh, const te_cluster* c, te_precision p, int what) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !c) return fail(TE_EINVAL, "null argument");
+  if (c->nocc < 1 || c->nvir < 1) return fail(TE_EINVAL, "nocc and nvir must be >= 1");
+  if (what < 1 || what > (TE_RESERVE_ENERGY | TE_RESERVE_VJP)) return fail(TE_EINVAL, "what must be 1, 2 or 3");
+  if (p < TE_FP64 || p > TE_OZAKI) return fail(TE_EINVAL, "unknown precision %d", (int)p);
+  DeviceGuard g(h->device);
+  size_t need = 0;
+  if (what & TE_RESERVE_ENERGY) {
+    te_status st = te_workspace_bytes(hh, c, p, &need);
+    if (st != TE_OK) return st;
+  }
+  if (what & TE_RESERVE_VJP)
+    need = std::max(need, p == TE_FP64 ? vjp_fp64_bytes(c->nocc, c->nvir) : vjp_tc_bytes(c->nocc, c->nvir, h->num_sms));
+  te_status st = ensure_workspace(h, need);
+  if (st != TE_OK) return st;
+  return ensure_triples(h, (int)c->nocc);
 }
 
 const char* te_last_error(void) { return g_last_error; }

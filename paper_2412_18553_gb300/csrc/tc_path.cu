@@ -1040,6 +1040,11 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
     if (!cand.empty()) h->tuned[key] = cand[0];
     return TE_OK;
   }
+  const auto cached = h->tune_file.find(key);  // a cache file's pick, if it is one of these
+  if (cached != h->tune_file.end() && std::find(cand.begin(), cand.end(), cached->second) != cand.end()) {
+    h->tuned[key] = cached->second;
+    return TE_OK;
+  }
   TcState* st = tc_state(h);
   te_status rs = get_encoder(st);
   if (rs != TE_OK) return rs;
@@ -1111,6 +1116,7 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess) return fail(TE_ECUDA, "autotune launch failed");
   h->tuned[key] = best;
+  tune_save(h);
   return TE_OK;
 }
 

@@ -79,9 +79,18 @@ struct Handle {
   cudaStream_t cap_stream = nullptr;
   // autotuned tile shapes: (nocc, nvir, mode) -> (TB, n_nt)
   std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
+  // the autotune cache file and the entries read from it (checked against the
+  // tuner's candidates before use)
+  std::string tune_path;
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> tune_file;
 };
 
 void drop_graphs(Handle* h);
+
+// autotune cache file: first line of the format for this handle's GPU; write
+// the file from tune_file and tuned (no-op without a path)
+std::string tune_header(const Handle* h);
+void tune_save(Handle* h);
 
 // Profiling helpers: begin/end a timed launch of `kind` on stream s.
 size_t prof_begin(Handle* h, int kind, cudaStream_t s);
@@ -116,6 +125,9 @@ cudaError_t launch_reduce_total(const double* e_triples, int64_t n, double* e_ou
 // adjoint of E(T) in float64 (vjp.cu)
 te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
                        cudaStream_t s);
+// workspace bytes of the two adjoints (vjp.cu)
+size_t vjp_fp64_bytes(int64_t o, int64_t v);
+size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms);
 // the same with the contractions on the tensor cores in exact BF16 slices (vjp.cu)
 te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
                      cudaStream_t s);

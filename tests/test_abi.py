@@ -51,7 +51,7 @@ def test_struct_layout_matches_header():
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU error path")
 def test_create_without_gpu_reports_cuda_error(lib):
     h = ctypes.c_void_p(123)
-    st = lib.te_create(ctypes.byref(h), 0)
+    st = lib.te_create(ctypes.byref(h), 0, None)
     assert st == 3  # TE_ECUDA
     assert h.value is None
     assert b"device" in lib.te_last_error()
@@ -59,7 +59,8 @@ def test_create_without_gpu_reports_cuda_error(lib):
 
 def test_null_arguments_are_rejected(lib):
     from paper_2412_18553_gb300._lib import TeCluster
-    assert lib.te_create(None, 0) == 1
+    assert lib.te_create(None, 0, None) == 1
+    assert lib.te_reserve(None, None, 0, 1) == 1
     assert lib.t_energy(None, None, 0, None, None) == 1
     assert lib.t_energy_batched(None, None, 0, 0, None, None) == 1
     assert lib.te_sync(None, None) == 1
