@@ -17,6 +17,7 @@
 // + ovs(jb,kc) t1(ia) + ovs(ia,kc) t1(jb) with ovs = (ovov + ovov^T)/2 gives the
 // ovov and t1 parts.  Triples are processed one after another on the stream
 // and every accumulation has a fixed order, so the gradient is deterministic.
+#include <atomic>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -299,20 +300,144 @@ __device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, cons
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* __restrict__ part) {
-  __shared__ __align__(16) __nv_bfloat16 As[OZ_NS][OZ_BM][OZ_LD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[OZ_NS][OZ_BN][OZ_LD];
+// Tiles of 64 x 64 outputs, 32 k per stage, two stages in flight (cp.async).
+// Each operand tile sits in shared memory k-major ([row][k]) when its view is
+// contiguous along k, else row-major ([k][row]) when contiguous along its rows
+// (columns); 16-byte chunks of eight BF16 values are copied asynchronously
+// where the view allows, element by element otherwise.
+template <bool AK, bool BK>
+struct OzTile {
+  static constexpr int A = AK ? OZ_BM * OZ_LD : OZ_BK * (OZ_BM + 8);
+  static constexpr int B = BK ? OZ_BN * OZ_LD : OZ_BK * (OZ_BN + 8);
+  static constexpr int STAGE = OZ_NS * (A + B);  // elements
+  static constexpr size_t BYTES = 2 * STAGE * sizeof(__nv_bfloat16);
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// four 8 x 8 BF16 matrices from shared memory, as stored / transposed
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const __nv_bfloat16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const __nv_bfloat16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+
+// Eight elements (rows r + e step_r, k + e step_k) of every slice, element by
+// element, zero outside the view: ragged edges and views without a
+// contiguous index.  Rolled loops, so the pipelined loop stays small enough
+// for the instruction cache.
+__device__ __forceinline__ void oz_fill_slow(const __nv_bfloat16* __restrict__ src, int64_t ps, __nv_bfloat16* dst,
+                                          int dps, int r, int k, int step_r, int step_k, int R, int ke, int R2,
+                                          int64_t r1s, int64_t r2s, int K2, int64_t k1s, int64_t k2s) {
+#pragma unroll 1
+  for (int e = 0; e < 8; ++e) {
+    const int rr = r + e * step_r, kk = k + e * step_k;
+    const bool ok = rr < R && kk < ke;
+    const int64_t off =
+        ok ? (int64_t)(rr / R2) * r1s + (int64_t)(rr % R2) * r2s + (int64_t)(kk / K2) * k1s + (int64_t)(kk % K2) * k2s
+           : 0;
+#pragma unroll 1
+    for (int sl = 0; sl < OZ_NS; ++sl) dst[sl * dps + e] = ok ? src[off + sl * ps] : __float2bfloat16_rn(0.f);
+  }
+}
+
+template <bool AK, bool BK>
+__global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* __restrict__ part, int a_vec,
+                                                  int b_vec) {
+  using T = OzTile<AK, BK>;
+  extern __shared__ __align__(16) unsigned char oz_smem[];
+  __nv_bfloat16* smem = reinterpret_cast<__nv_bfloat16*>(oz_smem);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int M = (int)(g.M1 * g.M2), N = (int)g.N, K = (int)(g.K1 * g.K2), K2 = (int)g.K2;
+  const int M = (int)(g.M1 * g.M2), N = (int)g.N, K2 = (int)g.K2;
   const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
-  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  // loader: thread -> one row (A) / column (B) and 16 consecutive k of the 32
-  const int lr = tid >> 1, lk = (tid & 1) * 16;
-  const int am = m0 + lr, bn = n0 + lr;
-  const bool am_ok = am < M, bn_ok = bn < N;
-  const int64_t a_row = am_ok ? (int64_t)(am / (int)g.M2) * g.a_m1 + (int64_t)(am % (int)g.M2) * g.a_m2 : 0;
-  const int64_t b_col = bn_ok ? (int64_t)bn * g.b_n : 0;
-  // warp tile 32 x 32: 2 x 4 MMA tiles of 16 x 8
+  const int kb = blockIdx.z * kchunk, ke = min((int)(g.K1 * g.K2), kb + kchunk);
+  const int nst = (ke - kb + OZ_BK - 1) / OZ_BK;
+
+  auto a_row = [&](int m) { return (int64_t)(m / (int)g.M2) * g.a_m1 + (int64_t)(m % (int)g.M2) * g.a_m2; };
+  auto a_kof = [&](int k) { return (int64_t)(k / K2) * g.a_k1 + (int64_t)(k % K2) * g.a_k2; };
+  auto b_kof = [&](int k) { return (int64_t)(k / K2) * g.b_k1 + (int64_t)(k % K2) * g.b_k2; };
+  // the row (column) part of this thread's chunk offsets is the same at every stage
+  int64_t a_roff[2];
+#pragma unroll
+  for (int c2 = 0; c2 < 2; ++c2) {
+    const int m = AK ? m0 + (tid >> 2) + 32 * c2 : m0 + (tid & 7) * 8;
+    a_roff[c2] = m < M ? a_row(m) : 0;
+  }
+
+  // one 8-element chunk: elements e = 0..7 along the tile's contiguous direction
+  auto load_stage = [&](int buf, int k0) {
+    __nv_bfloat16* As = smem + buf * T::STAGE;
+    __nv_bfloat16* Bs = As + OZ_NS * T::A;
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int c = tid + 128 * c2;  // 256 chunks per slice and operand
+      // ---- A ----
+      {
+        int m, k, step_m, step_k;  // first element and the step between the 8
+        __nv_bfloat16* dst0;
+        if (AK) {
+          m = m0 + (c >> 2);
+          k = k0 + (c & 3) * 8;
+          step_m = 0;
+          step_k = 1;
+          dst0 = As + (c >> 2) * OZ_LD + (c & 3) * 8;
+        } else {
+          k = k0 + (c >> 3);
+          m = m0 + (c & 7) * 8;
+          step_m = 1;
+          step_k = 0;
+          dst0 = As + (c >> 3) * (OZ_BM + 8) + (c & 7) * 8;
+        }
+        const bool full = a_vec && (AK ? (m < M && k + 8 <= ke) : (k < ke && m + 8 <= M));
+        if (full) {
+          const __nv_bfloat16* src = g.A + a_roff[c2] + a_kof(k);
+#pragma unroll
+          for (int sl = 0; sl < OZ_NS; ++sl) cp_async16(dst0 + sl * T::A, src + sl * g.a_ps);
+        } else {
+          oz_fill_slow(g.A, g.a_ps, dst0, T::A, m, k, step_m, step_k, M, ke, (int)g.M2, g.a_m1, g.a_m2, K2, g.a_k1,
+                       g.a_k2);
+        }
+      }
+      // ---- B ----
+      {
+        int n, k, step_n, step_k;
+        __nv_bfloat16* dst0;
+        if (BK) {
+          n = n0 + (c >> 2);
+          k = k0 + (c & 3) * 8;
+          step_n = 0;
+          step_k = 1;
+          dst0 = Bs + (c >> 2) * OZ_LD + (c & 3) * 8;
+        } else {
+          k = k0 + (c >> 3);
+          n = n0 + (c & 7) * 8;
+          step_n = 1;
+          step_k = 0;
+          dst0 = Bs + (c >> 3) * (OZ_BN + 8) + (c & 7) * 8;
+        }
+        const bool full = b_vec && (BK ? (n < N && k + 8 <= ke) : (k < ke && n + 8 <= N));
+        if (full) {
+          const __nv_bfloat16* src = g.B + (int64_t)n * g.b_n + b_kof(k);
+#pragma unroll
+          for (int sl = 0; sl < OZ_NS; ++sl) cp_async16(dst0 + sl * T::B, src + sl * g.b_ps);
+        } else {
+          oz_fill_slow(g.B, g.b_ps, dst0, T::B, n, k, step_n, step_k, N, ke, 1, g.b_n, 0, K2, g.b_k1, g.b_k2);
+        }
+      }
+    }
+  };
+
   const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
   const int gq = lane >> 2, tq = lane & 3;
   float acc[3][2][4][4];
@@ -324,154 +449,43 @@ __global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* _
       for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[l][i][j][q] = 0.f;
-  // Loads: an operand that is contiguous along k (8 consecutive k in one k1
-  // row), or along its row index m / column index n, loads eight BF16 values
-  // per 16-byte instruction; others element by element.
-  auto aligned16 = [](const __nv_bfloat16* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; };
-  const bool a_kvec = g.a_ps % 8 == 0 && aligned16(g.A) &&
-                      ((K2 == 1 && g.a_k1 == 1) || (K2 % 8 == 0 && g.a_k2 == 1 && g.a_k1 % 8 == 0)) &&
-                      (g.a_m1 % 8 == 0 || g.M1 == 1) && (g.a_m2 % 8 == 0 || g.M2 == 1);
-  const bool b_kvec = g.b_ps % 8 == 0 && aligned16(g.B) &&
-                      ((K2 == 1 && g.b_k1 == 1) || (K2 % 8 == 0 && g.b_k2 == 1 && g.b_k1 % 8 == 0)) && g.b_n % 8 == 0;
-  const bool a_mvec = !a_kvec && g.a_ps % 8 == 0 && aligned16(g.A) &&
-                      ((g.M2 == 1 && g.a_m1 == 1) || (g.M2 % 8 == 0 && g.a_m2 == 1 && g.a_m1 % 8 == 0)) &&
-                      g.a_k1 % 8 == 0 && g.a_k2 % 8 == 0;
-  const bool b_nvec = !b_kvec && g.b_ps % 8 == 0 && aligned16(g.B) && g.b_n == 1 && g.b_k1 % 8 == 0 &&
-                      g.b_k2 % 8 == 0;
-  int k1 = (kb + lk) / K2, k2 = (kb + lk) % K2;  // cursor of this thread's first k
-  for (int k0 = kb; k0 < ke; k0 += OZ_BK) {
-    if (a_kvec || b_kvec) {
-#pragma unroll
-      for (int u = 0; u < 16; u += 8) {
-        const int kk = k0 + lk + u;
-        const int q1 = kk / K2, q2 = kk % K2;
-#pragma unroll
-        for (int op = 0; op < 2; ++op) {
-          const bool vec = op == 0 ? a_kvec : b_kvec;
-          if (!vec) continue;
-          const bool ok = op == 0 ? am_ok : bn_ok;
-          const __nv_bfloat16* src0 = op == 0 ? g.A + a_row + (int64_t)q1 * g.a_k1 + (int64_t)q2 * g.a_k2
-                                              : g.B + b_col + (int64_t)q1 * g.b_k1 + (int64_t)q2 * g.b_k2;
-          const int64_t ps = op == 0 ? g.a_ps : g.b_ps;
-#pragma unroll
-          for (int sl = 0; sl < OZ_NS; ++sl) {
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            const __nv_bfloat16* src = src0 + sl * ps;
-            if (ok && kk + 8 <= ke) {
-              val = *reinterpret_cast<const uint4*>(src);
-            } else if (ok) {
-              __align__(16) __nv_bfloat16 tmp[8];
-#pragma unroll
-              for (int q = 0; q < 8; ++q) tmp[q] = kk + q < ke ? src[q] : __float2bfloat16_rn(0.f);
-              val = *reinterpret_cast<const uint4*>(tmp);
-            }
-            if (op == 0) *reinterpret_cast<uint4*>(&As[sl][lr][lk + u]) = val;
-            else *reinterpret_cast<uint4*>(&Bs[sl][lr][lk + u]) = val;
-          }
-        }
-      }
-    }
-    if (a_mvec || b_nvec) {
-      // item: 8 consecutive rows (columns) x one k; 8 groups x 32 k over 128 threads
-#pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const int grp = tid & 7, kq = (tid >> 3) + 16 * it;
-        const int kk = k0 + kq;
-        const bool k_ok = kk < ke;
-        const int q1 = k_ok ? kk / K2 : 0, q2 = k_ok ? kk % K2 : 0;
-#pragma unroll
-        for (int op = 0; op < 2; ++op) {
-          const bool vec = op == 0 ? a_mvec : b_nvec;
-          if (!vec) continue;
-          const int r0 = (op == 0 ? m0 : n0) + grp * 8;
-          const int lim = op == 0 ? M : N;
-          __nv_bfloat16(*dst)[OZ_BM][OZ_LD] = op == 0 ? As : Bs;
-          if (k_ok && r0 + 8 <= lim) {
-            const __nv_bfloat16* src0 =
-                op == 0 ? g.A + (int64_t)(r0 / (int)g.M2) * g.a_m1 + (int64_t)(r0 % (int)g.M2) * g.a_m2 +
-                              (int64_t)q1 * g.a_k1 + (int64_t)q2 * g.a_k2
-                        : g.B + (int64_t)r0 + (int64_t)q1 * g.b_k1 + (int64_t)q2 * g.b_k2;
-            const int64_t ps = op == 0 ? g.a_ps : g.b_ps;
-#pragma unroll
-            for (int sl = 0; sl < OZ_NS; ++sl) {
-              const uint4 val = *reinterpret_cast<const uint4*>(src0 + sl * ps);
-              const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&val);
-#pragma unroll
-              for (int q = 0; q < 8; ++q) dst[sl][grp * 8 + q][kq] = e8[q];
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int r = r0 + q;
-              const bool ok = k_ok && r < lim;
-              const int64_t off = !ok ? 0
-                                  : op == 0 ? (int64_t)(r / (int)g.M2) * g.a_m1 + (int64_t)(r % (int)g.M2) * g.a_m2 +
-                                                  (int64_t)q1 * g.a_k1 + (int64_t)q2 * g.a_k2
-                                            : (int64_t)r * g.b_n + (int64_t)q1 * g.b_k1 + (int64_t)q2 * g.b_k2;
-#pragma unroll
-              for (int sl = 0; sl < OZ_NS; ++sl)
-                dst[sl][grp * 8 + q][kq] =
-                    ok ? (op == 0 ? g.A[off + sl * g.a_ps] : g.B[off + sl * g.b_ps]) : __float2bfloat16_rn(0.f);
-            }
-          }
-        }
-      }
-    }
-    if (!a_kvec && !a_mvec) {
-      int c1 = k1, c2 = k2;
-#pragma unroll 4
-      for (int u = 0; u < 16; ++u) {
-        const bool k_ok = k0 + lk + u < ke;
-        const int64_t ka = (int64_t)c1 * g.a_k1 + (int64_t)c2 * g.a_k2;
-#pragma unroll
-        for (int sl = 0; sl < OZ_NS; ++sl)
-          As[sl][lr][lk + u] = (am_ok && k_ok) ? g.A[a_row + ka + sl * g.a_ps] : __float2bfloat16_rn(0.f);
-        if (++c2 == K2) {
-          c2 = 0;
-          ++c1;
-        }
-      }
-    }
-    if (!b_kvec && !b_nvec) {
-      int c1 = k1, c2 = k2;
-#pragma unroll 4
-      for (int u = 0; u < 16; ++u) {
-        const bool k_ok = k0 + lk + u < ke;
-        const int64_t kbo = (int64_t)c1 * g.b_k1 + (int64_t)c2 * g.b_k2;
-#pragma unroll
-        for (int sl = 0; sl < OZ_NS; ++sl)
-          Bs[sl][lr][lk + u] = (bn_ok && k_ok) ? g.B[b_col + kbo + sl * g.b_ps] : __float2bfloat16_rn(0.f);
-        if (++c2 == K2) {
-          c2 = 0;
-          ++c1;
-        }
-      }
-    }
-    // advance the cursor by OZ_BK
-    k2 += OZ_BK;
-    while (k2 >= K2) {
-      k2 -= K2;
-      ++k1;
-    }
+
+  if (nst > 0) load_stage(0, kb);
+  cp_async_commit();
+  for (int st = 0; st < nst; ++st) {
+    if (st + 1 < nst) load_stage((st + 1) & 1, kb + (st + 1) * OZ_BK);
+    cp_async_commit();
+    cp_async_wait1();  // every group but the newest: this stage's copies have landed
     __syncthreads();
+    const __nv_bfloat16* As = smem + (st & 1) * T::STAGE;
+    const __nv_bfloat16* Bs = As + OZ_NS * T::A;
 #pragma unroll
     for (int kk = 0; kk < OZ_BK; kk += 16) {
       uint32_t af[OZ_NS][2][4], bf[OZ_NS][4][2];
+      // ldmatrix: lane l addresses row (l & 7) of 8 x 8 matrix (l >> 3)
+      const int lr = lane & 7, lm = lane >> 3;
 #pragma unroll
       for (int sl = 0; sl < OZ_NS; ++sl) {
+        const __nv_bfloat16* a = As + sl * T::A;
+        const __nv_bfloat16* b = Bs + sl * T::B;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-          const int r = wm + i * 16 + gq;
-          af[sl][i][0] = *reinterpret_cast<const uint32_t*>(&As[sl][r][kk + 2 * tq]);
-          af[sl][i][1] = *reinterpret_cast<const uint32_t*>(&As[sl][r + 8][kk + 2 * tq]);
-          af[sl][i][2] = *reinterpret_cast<const uint32_t*>(&As[sl][r][kk + 2 * tq + 8]);
-          af[sl][i][3] = *reinterpret_cast<const uint32_t*>(&As[sl][r + 8][kk + 2 * tq + 8]);
+          const int r = wm + i * 16;
+          // matrices: (rows r, k kk), (rows r+8, k kk), (rows r, k kk+8), (rows r+8, k kk+8)
+          if (AK) ldsm_x4(af[sl][i], a + (r + lr + (lm & 1) * 8) * OZ_LD + kk + (lm >> 1) * 8);
+          else ldsm_x4_t(af[sl][i], a + (kk + lr + (lm >> 1) * 8) * (OZ_BM + 8) + r + (lm & 1) * 8);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int cidx = wn + j * 8 + gq;
-          bf[sl][j][0] = *reinterpret_cast<const uint32_t*>(&Bs[sl][cidx][kk + 2 * tq]);
-          bf[sl][j][1] = *reinterpret_cast<const uint32_t*>(&Bs[sl][cidx][kk + 2 * tq + 8]);
+        for (int j = 0; j < 4; j += 2) {
+          // matrices: (cols j, k kk), (cols j, k kk+8), (cols j+1, k kk), (cols j+1, k kk+8)
+          uint32_t t[4];
+          const int cb = wn + (j + (lm >> 1)) * 8;
+          if (BK) ldsm_x4(t, b + (cb + lr) * OZ_LD + kk + (lm & 1) * 8);
+          else ldsm_x4_t(t, b + (kk + lr + (lm & 1) * 8) * (OZ_BN + 8) + cb);
+          bf[sl][j][0] = t[0];
+          bf[sl][j][1] = t[1];
+          bf[sl][j + 1][0] = t[2];
+          bf[sl][j + 1][1] = t[3];
         }
       }
 #pragma unroll
@@ -485,11 +499,32 @@ __global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* _
             for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[lev][i][j], af[sa][i], bf[sb][j]);
         }
     }
-    __syncthreads();
+    __syncthreads();  // the buffer is refilled two stages on
   }
   const double scale = ldexp(g.alpha, *g.ea + *g.eb);
+  // this thread's four output rows (i, half h) and their offsets in C
+  int64_t crow[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int m = m0 + wm + i * 16 + gq + hh * 8;
+      crow[i][hh] = m < M ? (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2 : 0;
+    }
+  // Per 16-row half: every old value of C is loaded before any store, so the
+  // loads overlap (a store could otherwise alias the next load).
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    double val[4][4], old[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
+        const int n = n0 + wn + j * 8 + 2 * tq + (q & 1);
+        val[j][q] = scale * (((double)acc[0][i][j][q] + (double)acc[1][i][j][q]) + (double)acc[2][i][j][q]);
+        old[j][q] = (!part && !g.overwrite && m < M && n < N) ? g.C[crow[i][q >> 1] + n * g.c_n] : 0.0;
+      }
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -497,14 +532,10 @@ __global__ void __launch_bounds__(128) k_gemm_oz(OzView g, int kchunk, double* _
         const int m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
         const int n = n0 + wn + j * 8 + 2 * tq + (q & 1);
         if (m >= M || n >= N) continue;
-        const double val = scale * (((double)acc[0][i][j][q] + (double)acc[1][i][j][q]) + (double)acc[2][i][j][q]);
-        if (part) {
-          part[((int64_t)blockIdx.z * M + m) * N + n] = val;
-        } else {
-          double* cp = g.C + (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2 + n * g.c_n;
-          *cp = g.overwrite ? val : *cp + val;
-        }
+        if (part) part[((int64_t)blockIdx.z * M + m) * N + n] = val[j][q];
+        else g.C[crow[i][q >> 1] + n * g.c_n] = old[j][q] + val[j][q];
       }
+  }
 }
 
 // C[m,n] += sum_z part[z][m][n], z in order (alpha is already applied)
@@ -520,6 +551,23 @@ __global__ void k_splitk_add_oz(OzView g, int nsplit, const double* __restrict__
   }
 }
 
+template <bool AK, bool BK>
+static cudaError_t launch_oz2(const OzView& g, dim3 grid, int kchunk, double* part, int av, int bv, cudaStream_t s) {
+  const size_t bytes = OzTile<AK, BK>::BYTES;
+  static std::atomic<unsigned long long> opted{0};  // devices this instantiation may use `bytes` on
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(opted.load() & bit)) {
+    e = cudaFuncSetAttribute(k_gemm_oz2<AK, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    opted.fetch_or(bit);
+  }
+  k_gemm_oz2<AK, BK><<<grid, 128, bytes, s>>>(g, kchunk, part, av, bv);
+  return cudaGetLastError();
+}
+
 // K in splits of at most OZ_KMAX (exactness), more when the output has few tiles
 static cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
                            int64_t* launches) {
@@ -533,7 +581,29 @@ static cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_
   const int nsplit = (int)((K + kchunk - 1) / kchunk);
   if (nsplit > 1 && (int64_t)nsplit * M * g.N > scratch_cap) return cudaErrorInvalidValue;
   dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)nsplit);
-  k_gemm_oz<<<grid, 128, 0, s>>>(g, kchunk, nsplit > 1 ? scratch : nullptr);
+  // tile orientation per operand: k-major if the view is contiguous along k,
+  // else row-major if contiguous along its rows (columns), else k-major
+  // element by element
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const bool a_k = g.a_ps % 8 == 0 && al16(g.A) &&
+                   ((g.K2 == 1 && g.a_k1 == 1) || (g.K2 % 8 == 0 && g.a_k2 == 1 && g.a_k1 % 8 == 0)) &&
+                   (g.a_m1 % 8 == 0 || g.M1 == 1) && (g.a_m2 % 8 == 0 || g.M2 == 1);
+  const bool a_m = !a_k && g.a_ps % 8 == 0 && al16(g.A) &&
+                   ((g.M2 == 1 && g.a_m1 == 1) || (g.M2 % 8 == 0 && g.a_m2 == 1 && g.a_m1 % 8 == 0)) &&
+                   g.a_k1 % 8 == 0 && (g.K2 == 1 || g.a_k2 % 8 == 0);
+  const bool b_k = g.b_ps % 8 == 0 && al16(g.B) &&
+                   ((g.K2 == 1 && g.b_k1 == 1) || (g.K2 % 8 == 0 && g.b_k2 == 1 && g.b_k1 % 8 == 0)) && g.b_n % 8 == 0;
+  const bool b_n = !b_k && g.b_ps % 8 == 0 && al16(g.B) && g.b_n == 1 && g.b_k1 % 8 == 0 &&
+                   (g.K2 == 1 || g.b_k2 % 8 == 0);
+  double* pp = nsplit > 1 ? scratch : nullptr;
+  const bool AK = !a_m, BK = !b_n;
+  const int av = (a_k || a_m) ? 1 : 0, bv = (b_k || b_n) ? 1 : 0;
+  cudaError_t err;
+  if (AK && BK) err = launch_oz2<true, true>(g, grid, kchunk, pp, av, bv, s);
+  else if (AK) err = launch_oz2<true, false>(g, grid, kchunk, pp, av, bv, s);
+  else if (BK) err = launch_oz2<false, true>(g, grid, kchunk, pp, av, bv, s);
+  else err = launch_oz2<false, false>(g, grid, kchunk, pp, av, bv, s);
+  if (err != cudaSuccess) return err;
   ++*launches;
   if (nsplit > 1) {
     const int64_t MN = M * g.N;
