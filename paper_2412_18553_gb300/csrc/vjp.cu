@@ -225,7 +225,8 @@ __global__ void k_splitk_add(GemmView g, int nsplit, const double* __restrict__ 
   const int M = (int)(g.M1 * g.M2);
   const int64_t MN = (int64_t)M * g.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
+    double s = 0.0;  // in split order; unrolled so that many loads are in flight
+#pragma unroll 16
     for (int z = 0; z < nsplit; ++z) s += part[z * MN + e];
     const int m = (int)(e / g.N), n = (int)(e % g.N);
     const int64_t crow = (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2;
@@ -543,7 +544,8 @@ __global__ void k_splitk_add_oz(OzView g, int nsplit, const double* __restrict__
   const int M = (int)(g.M1 * g.M2);
   const int64_t MN = (int64_t)M * g.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
+    double s = 0.0;  // in split order; unrolled so that many loads are in flight
+#pragma unroll 16
     for (int z = 0; z < nsplit; ++z) s += part[z * MN + e];
     const int m = (int)(e / g.N), n = (int)(e % g.N);
     double* cp = g.C + (int64_t)(m / (int)g.M2) * g.c_m1 + (int64_t)(m % (int)g.M2) * g.c_m2 + n * g.c_n;
