@@ -221,6 +221,108 @@ def t_energy_restricted(c: Inputs):
 
 
 # ---------------------------------------------------------------------------
+# Fragment-projected energy: Eq. (E_corr_CCSD_T) with a general C^f
+# ---------------------------------------------------------------------------
+#
+# E_x = 2 sum_{(ia>=jb>=kc)} sum_{i'} A R[Z]_{ijk} W~_{i'jk} C^f_{ii'}: the first
+# occupied index of W~ is projected.  Reading: the sum is the full one,
+# E_x = (1/3) sum_{ijk} sum_{abc} sum_{i'} C^f_{ii'} W~_{i'jk} R[Z]_{ijk}, which is
+# the printed restricted sum when C^f = 1.  For a general C^f the restricted
+# sum over a >= b >= c depends on how the virtual orbitals are labelled (the
+# summand is no longer symmetric under joint permutations of abc and ijk), the
+# full sum does not.
+
+def project_first(cf, wt, j, k):
+    """sum_{i'} cf[i, i'] W~_{i'jk} for every i, as an array [i, a, b, c];
+    ``wt(p, q, r)`` returns W~_{pqr}."""
+    o = cf.shape[0]
+    stack = torch.stack([wt(p, j, k) for p in range(o)])
+    return torch.einsum("ip,pabc->iabc", cf, stack)
+
+
+def _blocks(c: Inputs):
+    """W~ and Z = (W~ + Y)/D of every ordered triple, built on demand and kept."""
+    wt_cache, z_cache = {}, {}
+
+    def wt(p, q, r):
+        if (p, q, r) not in wt_cache:
+            wt_cache[(p, q, r)] = w_tilde(c, p, q, r)
+        return wt_cache[(p, q, r)]
+
+    def z(p, q, r):
+        if (p, q, r) not in z_cache:
+            z_cache[(p, q, r)] = (wt(p, q, r) + y_disconnected(c, p, q, r)) / denominator(c, p, q, r)
+        return z_cache[(p, q, r)]
+    return wt, z
+
+
+def triple_energy_projected(c: Inputs, cf, i, j, k, blocks=None, slot=0):
+    """e^f_{ijk} = sum_{abc} sum_{i'} cf[i,i'] W~_{i'jk} R[Z]_{ijk} for one ordered
+    triple.  ``slot`` = 1 or 2 projects the second or third occupied index of
+    W~ instead (the same total after the sum over all ordered triples)."""
+    wt, z = blocks if blocks is not None else _blocks(c)
+    zz = _ByOrdering((i, j, k), z)
+    rz = r_operator(zz)
+    ijk = (i, j, k)
+    o = cf.shape[0]
+    wp = torch.zeros_like(rz)
+    for p in range(o):
+        idx = list(ijk)
+        idx[slot] = p
+        wp = wp + cf[ijk[slot], p] * wt(*idx)
+    return (wp * rz).sum()
+
+
+def t_energy_projected(c: Inputs, cf, slot=0):
+    """E_x = (1/3) sum over all ordered triples of e^f_{ijk} (float64 scalar)."""
+    cf = torch.as_tensor(np.asarray(cf), dtype=torch.float64)
+    blocks = _blocks(c)
+    o = c.nocc
+    total = torch.zeros((), dtype=torch.float64)
+    for i in range(o):
+        for j in range(o):
+            for k in range(o):
+                total = total + triple_energy_projected(c, cf, i, j, k, blocks, slot)
+    return total / 3.0
+
+
+def triple_share_projected(c: Inputs, cf, i, j, k, blocks=None):
+    """The share of the unique triple {i,j,k}: (1/3) sum over its distinct
+    orderings of e^f.  Summed over the unique triples this is E_x."""
+    cf = torch.as_tensor(np.asarray(cf), dtype=torch.float64)
+    blocks = blocks if blocks is not None else _blocks(c)
+    total = torch.zeros((), dtype=torch.float64)
+    for perm in set(itertools.permutations((i, j, k))):
+        total = total + triple_energy_projected(c, cf, *perm, blocks)
+    return total / 3.0
+
+
+def t_energy_projected_restricted(c: Inputs, cf):
+    """The printed restricted form taken literally with a general C^f:
+    2 sum_{a>=b>=c} A sum_{ijk} sum_{i'} R[Z]_{ijk} W~_{i'jk} C^f_{ii'} (tiny
+    clusters; kept to show why the full sum is the reading)."""
+    o, v = c.nocc, c.nvir
+    cf = torch.as_tensor(np.asarray(cf), dtype=torch.float64)
+    wt, z = _blocks(c)
+    Wt = torch.stack([torch.stack([torch.stack([wt(i, j, k) for k in range(o)])
+                                   for j in range(o)]) for i in range(o)])
+    Z = torch.stack([torch.stack([torch.stack([z(i, j, k) for k in range(o)])
+                                  for j in range(o)]) for i in range(o)])
+    RZ = ((4.0 * Z - 2.0 * torch.einsum("kjiabc->ijkabc", Z) - 2.0 * torch.einsum("ikjabc->ijkabc", Z))
+          + (torch.einsum("kijabc->ijkabc", Z) + torch.einsum("jkiabc->ijkabc", Z)
+             - 2.0 * torch.einsum("jikabc->ijkabc", Z)))
+    WP = torch.einsum("ip,pjkabc->ijkabc", cf, Wt)
+    a = torch.arange(v)
+    ge = (a[:, None, None] >= a[None, :, None]) & (a[None, :, None] >= a[None, None, :])
+    eq_ab = a[:, None, None] == a[None, :, None]
+    eq_bc = a[None, :, None] == a[None, None, :]
+    A = torch.where(eq_ab & eq_bc, 1.0 / 6.0,
+                    torch.where(eq_ab | eq_bc, 0.5, 1.0)).to(torch.float64)
+    A = torch.where(ge, A, torch.zeros((), dtype=torch.float64))
+    return 2.0 * (A[None, None, None] * RZ * WP).sum()
+
+
+# ---------------------------------------------------------------------------
 # Gradient
 # ---------------------------------------------------------------------------
 
