@@ -48,6 +48,8 @@ def parse():
                     help="with --workload batch96: time every s-th seed of the 96 (extrapolated by flop count)")
     ap.add_argument("--no-vjp", action="store_true",
                     help="skip the adjoint measurement (nocc=16 nvir=120, exact-slice and float64)")
+    ap.add_argument("--no-frag", action="store_true",
+                    help="skip the fragment-projected energy (nocc=16 nvir=120, exact-slice and float64)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched measurement (16 clusters, nocc 8..20, nvir = 8 nocc)")
     return ap.parse_args()
@@ -388,6 +390,43 @@ def main():
             vjp["speedup_vs_fp64"] = vjp["fp64"]["ms"] / vjp["ozaki"]["ms"]
         del qa
 
+    # fragment-projected E(T) (Eq. E_corr_CCSD_T with a general C^f) of the same
+    # cluster; the projector spans 6 of the 16 occupied orbitals
+    frag = None
+    if not args.no_frag:
+        import tegen
+        oq, vq, nq, sq = tegen.WORKLOADS["o16v120"]
+        cq = tegen.make_cluster(oq, vq, nq, sq)
+        qa = {n: torch.as_tensor(np.ascontiguousarray(x)).to(torch.device("cuda", local)) for n, x in cq.arrays().items()}
+        u, _ = np.linalg.qr(np.random.default_rng(16).standard_normal((oq, oq)))
+        cf = u[:, :6] @ u[:, :6].T
+        tiny = tegen.make_cluster(2, 8, 40, 0)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        Fq = te.flop_count(oq, vq)
+        frag = {"workload": f"o16v120: nocc={oq} nvir={vq} naux={nq} seed={sq}, projector of rank 6"}
+        for fprec in ("ozaki", "fp64"):
+            te.t_energy_frag({n: torch.as_tensor(x).cuda(local) for n, x in tiny.arrays().items()}, np.eye(2),
+                             fprec, handle=h)
+            torch.cuda.synchronize()
+            barrier()
+            l0 = h.profile_read(reset=False)["launches"]
+            f0.record()
+            ef = te.t_energy_frag(qa, cf, fprec, handle=h)
+            f1.record()
+            torch.cuda.synchronize()
+            fms = f0.elapsed_time(f1)
+            ft = torch.tensor([fms], device="cuda")
+            if world > 1:
+                torch.distributed.all_reduce(ft, op=torch.distributed.ReduceOp.MAX)
+            fms = float(ft.item())
+            frag[fprec] = {"ms": fms, "gflops_3F": world * 3 * Fq / (fms / 1e3) / 1e9, "e_frag_ha": float(ef),
+                           "launches": h.profile_read(reset=False)["launches"] - l0}
+        if "ozaki" in frag and "fp64" in frag:
+            frag["speedup_vs_fp64"] = frag["fp64"]["ms"] / frag["ozaki"]["ms"]
+            frag["dE_ozaki_vs_fp64_ha"] = abs(frag["ozaki"]["e_frag_ha"] - frag["fp64"]["e_frag_ha"])
+        del qa
+
     pk, pk_src = peaks()
     if prec == "fp64":
         roof = None
@@ -431,6 +470,7 @@ def main():
                "profile": prof,
                "batch16": batch,
                "vjp": vjp,
+               "frag": frag,
                "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
         print(json.dumps(out))
     if world > 1:

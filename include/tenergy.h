@@ -157,6 +157,26 @@ te_status t_energy_vjp(te_handle h, const te_cluster* c, te_precision p,
                        double gE, double* e_out, te_cluster_grad* g,
                        te_stream_t s);
 
+/* Fragment-projected E(T) of one cluster: Eq. E_corr_CCSD_T with a general
+ * C^f, i.e. the first occupied index of W~ projected,
+ *   E_x = (1/3) sum_{ijk} sum_{abc} sum_{i'} cf[i][i'] W~_{i'jk}^{abc} R[Z]_{ijk}^{abc},
+ * summed over all ordered occupied triples (the printed restricted sum over
+ * a >= b >= c is this sum when cf is the identity; for other cf it would
+ * depend on the labelling of the virtual orbitals).  cf: device float64
+ * [nocc][nocc], row-major, caller-owned; a fragment projector is
+ * cf[i][i'] = sum_f C[i][f] C[i'][f], symmetric, but any matrix is accepted.
+ * With cf = identity the result is t_energy's.  Projectors of fragments that
+ * partition the occupied space sum to t_energy (Eq. C_f).
+ * p: TE_FP64 (DFMA contractions) or TE_OZAKI (exact BF16 slices on the tensor
+ * cores, same accuracy class as t_energy's TE_OZAKI); others give
+ * TE_EUNSUPPORTED.  e_out (nullable): device, one double, overwritten.
+ * e_triples (nullable, not both null): device [nocc (nocc+1)(nocc+2)/6 -
+ * nocc] doubles, the per-triple shares in t_energy_triples' canonical order,
+ * (1/3) sum over each triple's distinct orderings.  Costs about four times
+ * the adjoint's forward contractions; deterministic. */
+te_status t_energy_frag(te_handle h, const te_cluster* c, const double* cf, te_precision p,
+                        double* e_out, double* e_triples, te_stream_t s);
+
 /* Wait for the work of handle h on stream s and report a device-side
  * watchdog expiry (TE_ETIMEOUT) or an asynchronous CUDA error (TE_ECUDA). */
 te_status te_sync(te_handle h, te_stream_t s);
@@ -169,13 +189,15 @@ te_status te_workspace_bytes(te_handle h, const te_cluster* c, te_precision p,
 /* Allocate the handle's workspace (and its table of occupied triples) for a
  * cluster of c->nocc, c->nvir in mode p now, instead of on the first call, so
  * that later calls of that size or smaller allocate nothing.  Only nocc and
- * nvir are read; the array pointers may be NULL.  what: TE_RESERVE_ENERGY for
- * t_energy / t_energy_triples / t_energy_batched, TE_RESERVE_VJP for
- * t_energy_vjp, or both.  TE_ENOMEM if the device cannot hold it (the handle
- * keeps what it had); TE_EUNSUPPORTED inside a stream capture.  Synchronises
- * the device when a smaller workspace is replaced. */
+ * nvir are read; the array pointers may be NULL.  what: any non-empty
+ * combination of TE_RESERVE_ENERGY (t_energy, t_energy_triples,
+ * t_energy_batched), TE_RESERVE_VJP (t_energy_vjp) and TE_RESERVE_FRAG
+ * (t_energy_frag).  TE_ENOMEM if the device cannot hold it (the handle keeps
+ * what it had); TE_EUNSUPPORTED inside a stream capture.  Synchronises the
+ * device when a smaller workspace is replaced. */
 #define TE_RESERVE_ENERGY 1
 #define TE_RESERVE_VJP 2
+#define TE_RESERVE_FRAG 4
 te_status te_reserve(te_handle h, const te_cluster* c, te_precision p, int what);
 
 /* Launch accounting of one handle.  Kernel launches are always counted; with

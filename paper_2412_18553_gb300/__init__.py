@@ -24,7 +24,7 @@ from ._lib import PRECISIONS, TEnergyError, TeCluster, TeClusterGrad
 NAMES = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
 
 __all__ = ["Handle", "t_energy", "t_energy_triples", "t_energy_batched", "t_energy_vjp",
-           "t_energy_fp64_noalloc",
+           "t_energy_fp64_noalloc", "t_energy_frag",
            "TEnergy", "num_unique_triples", "flop_count", "TEnergyError", "NAMES"]
 
 
@@ -106,12 +106,13 @@ class Handle:
         _lib.check(_lib.load().te_profile_read(self.ptr, ctypes.byref(pr), 1 if reset else 0))
         return {f: getattr(pr, f) for f, _ in pr._fields_}
 
-    def reserve(self, nocc: int, nvir: int, precision="fp64", energy=True, vjp=False):
+    def reserve(self, nocc: int, nvir: int, precision="fp64", energy=True, vjp=False, frag=False):
         """Allocate the workspace for clusters up to (nocc, nvir) now, for the
-        energy calls and / or the adjoint, so that later calls allocate nothing."""
+        energy calls, the adjoint and / or the projected energy, so that later
+        calls allocate nothing."""
         c = _lib.TeCluster()
         c.nocc, c.nvir = int(nocc), int(nvir)
-        what = (1 if energy else 0) | (2 if vjp else 0)
+        what = (1 if energy else 0) | (2 if vjp else 0) | (4 if frag else 0)
         _lib.check(_lib.load().te_reserve(self.ptr, ctypes.byref(c), _prec(precision), what))
 
     def workspace_bytes(self, cluster, precision="fp64") -> int:
@@ -249,6 +250,30 @@ def t_energy_vjp(cluster, gE=1.0, precision="fp64", handle=None, device=None, st
                                         ctypes.c_void_p(e.data_ptr()), ctypes.byref(g),
                                         _stream(dev, stream)))
     return e, grads
+
+
+def t_energy_frag(cluster, cf, precision="fp64", handle=None, device=None, stream=None, shares=False):
+    """Fragment-projected E(T) (Eq. E_corr_CCSD_T with a general C^f): cf is
+    the [nocc, nocc] projector acting on W~'s first occupied index.  Returns a
+    0-dim float64 CUDA tensor, or (E, per-triple shares) with shares=True.
+    precision: "fp64" or "ozaki"."""
+    dev = _device_of(cluster, device)
+    h = _handle(handle, dev)
+    t = _tensors(cluster, dev)
+    o = t["eps_o"].shape[0]
+    cf = torch.as_tensor(cf, dtype=torch.float64).to(torch.device("cuda", dev)).contiguous()
+    if tuple(cf.shape) != (o, o):
+        raise ValueError(f"cf must be [{o}, {o}], got {tuple(cf.shape)}")
+    e = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
+    sh = torch.empty(max(1, num_unique_triples(o)), dtype=torch.float64, device=e.device) if shares else None
+    c = _struct(t)
+    _lib.check(_lib.load().t_energy_frag(h.ptr, ctypes.byref(c), ctypes.c_void_p(cf.data_ptr()), _prec(precision),
+                                         ctypes.c_void_p(e.data_ptr()),
+                                         ctypes.c_void_p(sh.data_ptr()) if shares else None,
+                                         _stream(dev, stream)))
+    if shares:
+        return e, sh[:num_unique_triples(o)]
+    return e
 
 
 def t_energy_fp64_noalloc(cluster, device=None, stream=None) -> torch.Tensor:

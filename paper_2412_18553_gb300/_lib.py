@@ -44,6 +44,8 @@ SIGNATURES = [
                                         c_void_p, c_void_p]),
     ("t_energy_vjp", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int, ctypes.c_double,
                                     c_void_p, ctypes.POINTER(TeClusterGrad), c_void_p]),
+    ("t_energy_frag", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), c_void_p, ctypes.c_int,
+                                     c_void_p, c_void_p, c_void_p]),
     ("te_sync", ctypes.c_int, [c_void_p, c_void_p]),
     ("te_workspace_bytes", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_size_t)]),

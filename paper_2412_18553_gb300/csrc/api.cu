@@ -543,6 +543,24 @@ te_status t_energy_vjp(te_handle hh, const te_cluster* c, te_precision p, double
   return run_vjp_tc(h, c, gE, e_out, gr, s);
 }
 
+te_status t_energy_frag(te_handle hh, const te_cluster* c, const double* cf, te_precision p, double* e_out,
+                        double* e_triples, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (!cf) return fail(TE_EINVAL, "null projector");
+  if (!e_out && !e_triples) return fail(TE_EINVAL, "no output");
+  if (p != TE_FP64 && p != TE_OZAKI)
+    return fail(TE_EUNSUPPORTED, "the projected energy runs in TE_FP64 or TE_OZAKI (got %d)", (int)p);
+  if (h->capturing) return fail(TE_EINVAL, "t_energy_frag cannot run inside a graph capture");
+  DeviceGuard g(h->device);
+  te_status st = validate(h, c, p, s);
+  if (st != TE_OK) return st;
+  if (p == TE_OZAKI && h->cc_major != 10 && h->cc_major != 11)
+    return fail(TE_EUNSUPPORTED, "exact-slice contractions need an sm_100-family GPU");
+  return run_frag(h, c, cf, p, e_out, e_triples, s);
+}
+
 te_status te_sync(te_handle hh, te_stream_t ss) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return fail(TE_EINVAL, "null handle");
@@ -582,7 +600,8 @@ te_status te_reserve(te_handle hh, const te_cluster* c, te_precision p, int what
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !c) return fail(TE_EINVAL, "null argument");
   if (c->nocc < 1 || c->nvir < 1) return fail(TE_EINVAL, "nocc and nvir must be >= 1");
-  if (what < 1 || what > (TE_RESERVE_ENERGY | TE_RESERVE_VJP)) return fail(TE_EINVAL, "what must be 1, 2 or 3");
+  if (what < 1 || what > (TE_RESERVE_ENERGY | TE_RESERVE_VJP | TE_RESERVE_FRAG))
+    return fail(TE_EINVAL, "what must be a non-empty combination of TE_RESERVE_ENERGY, _VJP, _FRAG");
   if (p < TE_FP64 || p > TE_OZAKI) return fail(TE_EINVAL, "unknown precision %d", (int)p);
   DeviceGuard g(h->device);
   size_t need = 0;
@@ -592,6 +611,7 @@ te_status te_reserve(te_handle hh, const te_cluster* c, te_precision p, int what
   }
   if (what & TE_RESERVE_VJP)
     need = std::max(need, p == TE_FP64 ? vjp_fp64_bytes(c->nocc, c->nvir) : vjp_tc_bytes(c->nocc, c->nvir, h->num_sms));
+  if (what & TE_RESERVE_FRAG) need = std::max(need, frag_bytes(c->nocc, c->nvir, p, h->num_sms));
   te_status st = ensure_workspace(h, need);
   if (st != TE_OK) return st;
   return ensure_triples(h, (int)c->nocc);

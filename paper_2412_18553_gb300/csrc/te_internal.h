@@ -125,6 +125,11 @@ cudaError_t launch_reduce_total(const double* e_triples, int64_t n, double* e_ou
 // adjoint of E(T) in float64 (vjp.cu)
 te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
                        cudaStream_t s);
+// fragment-projected E(T) (vjp.cu): cf device [nocc][nocc]; precision TE_FP64 or
+// exact slices; per-triple shares to e_triples (nullable), total to e_out (nullable)
+size_t frag_bytes(int64_t o, int64_t v, te_precision p, int num_sms);
+te_status run_frag(Handle* h, const te_cluster* c, const double* cf, te_precision p, double* e_out,
+                   double* e_triples, cudaStream_t s);
 // workspace bytes of the two adjoints (vjp.cu)
 size_t vjp_fp64_bytes(int64_t o, int64_t v);
 size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms);
