@@ -291,6 +291,7 @@ struct OzView {
 };
 
 constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_KMAX = 1024, OZ_NS = 4;
+constexpr int OZ_THREADS = 256;  // eight warps, each 32 x 16 outputs
 constexpr int OZ_LD = OZ_BK + 8;  // padded row (bf16): conflict-free fragment loads
 
 __device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b) {
@@ -354,8 +355,8 @@ __device__ __forceinline__ void oz_fill_slow(const __nv_bfloat16* __restrict__ s
 }
 
 template <bool AK, bool BK>
-__global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* __restrict__ part, int a_vec,
-                                                  int b_vec) {
+__global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk, double* __restrict__ part,
+                                                            int a_vec, int b_vec) {
   using T = OzTile<AK, BK>;
   extern __shared__ __align__(16) unsigned char oz_smem[];
   __nv_bfloat16* smem = reinterpret_cast<__nv_bfloat16*>(oz_smem);
@@ -368,11 +369,14 @@ __global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* 
   auto a_row = [&](int m) { return (int64_t)(m / (int)g.M2) * g.a_m1 + (int64_t)(m % (int)g.M2) * g.a_m2; };
   auto a_kof = [&](int k) { return (int64_t)(k / K2) * g.a_k1 + (int64_t)(k % K2) * g.a_k2; };
   auto b_kof = [&](int k) { return (int64_t)(k / K2) * g.b_k1 + (int64_t)(k % K2) * g.b_k2; };
-  // the row (column) part of this thread's chunk offsets is the same at every stage
-  int64_t a_roff[2];
+  // 256 chunks of 8 elements per slice and operand, OZ_CH per thread; the row
+  // (column) part of a chunk's offset is the same at every stage
+  constexpr int OZ_CH = 256 / OZ_THREADS;
+  int64_t a_roff[OZ_CH];
 #pragma unroll
-  for (int c2 = 0; c2 < 2; ++c2) {
-    const int m = AK ? m0 + (tid >> 2) + 32 * c2 : m0 + (tid & 7) * 8;
+  for (int c2 = 0; c2 < OZ_CH; ++c2) {
+    const int c = tid + OZ_THREADS * c2;
+    const int m = AK ? m0 + (c >> 2) : m0 + (c & 7) * 8;
     a_roff[c2] = m < M ? a_row(m) : 0;
   }
 
@@ -381,8 +385,8 @@ __global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* 
     __nv_bfloat16* As = smem + buf * T::STAGE;
     __nv_bfloat16* Bs = As + OZ_NS * T::A;
 #pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      const int c = tid + 128 * c2;  // 256 chunks per slice and operand
+    for (int c2 = 0; c2 < OZ_CH; ++c2) {
+      const int c = tid + OZ_THREADS * c2;
       // ---- A ----
       {
         int m, k, step_m, step_k;  // first element and the step between the 8
@@ -439,15 +443,15 @@ __global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* 
     }
   };
 
-  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 16;
   const int gq = lane >> 2, tq = lane & 3;
-  float acc[3][2][4][4];
+  float acc[3][2][2][4];
 #pragma unroll
   for (int l = 0; l < 3; ++l)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < 2; ++j)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[l][i][j][q] = 0.f;
 
@@ -462,43 +466,42 @@ __global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* 
     const __nv_bfloat16* Bs = As + OZ_NS * T::A;
 #pragma unroll
     for (int kk = 0; kk < OZ_BK; kk += 16) {
-      uint32_t af[OZ_NS][2][4], bf[OZ_NS][4][2];
       // ldmatrix: lane l addresses row (l & 7) of 8 x 8 matrix (l >> 3)
       const int lr = lane & 7, lm = lane >> 3;
+      uint32_t bf[OZ_NS][2][2];
 #pragma unroll
       for (int sl = 0; sl < OZ_NS; ++sl) {
-        const __nv_bfloat16* a = As + sl * T::A;
+        // matrices: (cols 0-7, k kk), (cols 0-7, k kk+8), (cols 8-15, k kk), (cols 8-15, k kk+8)
         const __nv_bfloat16* b = Bs + sl * T::B;
+        uint32_t t[4];
+        const int cb = wn + (lm >> 1) * 8;
+        if (BK) ldsm_x4(t, b + (cb + lr) * OZ_LD + kk + (lm & 1) * 8);
+        else ldsm_x4_t(t, b + (kk + lr + (lm & 1) * 8) * (OZ_BN + 8) + cb);
+        bf[sl][0][0] = t[0];
+        bf[sl][0][1] = t[1];
+        bf[sl][1][0] = t[2];
+        bf[sl][1][1] = t[3];
+      }
+#pragma unroll
+      for (int sa = 0; sa < OZ_NS; ++sa) {
+        uint32_t af[2][4];  // A slice sa, loaded when its products are due
+        const __nv_bfloat16* a = As + sa * T::A;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const int r = wm + i * 16;
           // matrices: (rows r, k kk), (rows r+8, k kk), (rows r, k kk+8), (rows r+8, k kk+8)
-          if (AK) ldsm_x4(af[sl][i], a + (r + lr + (lm & 1) * 8) * OZ_LD + kk + (lm >> 1) * 8);
-          else ldsm_x4_t(af[sl][i], a + (kk + lr + (lm >> 1) * 8) * (OZ_BM + 8) + r + (lm & 1) * 8);
+          if (AK) ldsm_x4(af[i], a + (r + lr + (lm & 1) * 8) * OZ_LD + kk + (lm >> 1) * 8);
+          else ldsm_x4_t(af[i], a + (kk + lr + (lm >> 1) * 8) * (OZ_BM + 8) + r + (lm & 1) * 8);
         }
-#pragma unroll
-        for (int j = 0; j < 4; j += 2) {
-          // matrices: (cols j, k kk), (cols j, k kk+8), (cols j+1, k kk), (cols j+1, k kk+8)
-          uint32_t t[4];
-          const int cb = wn + (j + (lm >> 1)) * 8;
-          if (BK) ldsm_x4(t, b + (cb + lr) * OZ_LD + kk + (lm & 1) * 8);
-          else ldsm_x4_t(t, b + (kk + lr + (lm & 1) * 8) * (OZ_BN + 8) + cb);
-          bf[sl][j][0] = t[0];
-          bf[sl][j][1] = t[1];
-          bf[sl][j + 1][0] = t[2];
-          bf[sl][j + 1][1] = t[3];
-        }
-      }
-#pragma unroll
-      for (int sa = 0; sa < OZ_NS; ++sa)
 #pragma unroll
         for (int sb = 0; sb < OZ_NS - sa; ++sb) {
           const int lev = sa + sb == 0 ? 0 : (sa + sb == 1 ? 1 : 2);
 #pragma unroll
           for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[lev][i][j], af[sa][i], bf[sb][j]);
+            for (int j = 0; j < 2; ++j) mma_bf16_16816(acc[lev][i][j], af[i], bf[sb][j]);
         }
+      }
     }
     __syncthreads();  // the buffer is refilled two stages on
   }
@@ -516,9 +519,9 @@ __global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* 
   // loads overlap (a store could otherwise alias the next load).
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    double val[4][4], old[4][4];
+    double val[2][4], old[2][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(128) k_gemm_oz2(OzView g, int kchunk, double* 
         old[j][q] = (!part && !g.overwrite && m < M && n < N) ? g.C[crow[i][q >> 1] + n * g.c_n] : 0.0;
       }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
@@ -566,7 +569,7 @@ static cudaError_t launch_oz2(const OzView& g, dim3 grid, int kchunk, double* pa
     if (e != cudaSuccess) return e;
     opted.fetch_or(bit);
   }
-  k_gemm_oz2<AK, BK><<<grid, 128, bytes, s>>>(g, kchunk, part, av, bv);
+  k_gemm_oz2<AK, BK><<<grid, OZ_THREADS, bytes, s>>>(g, kchunk, part, av, bv);
   return cudaGetLastError();
 }
 
