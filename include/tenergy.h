@@ -172,8 +172,13 @@ te_status t_energy_vjp(te_handle h, const te_cluster* c, te_precision p,
  * TE_EUNSUPPORTED.  e_out (nullable): device, one double, overwritten.
  * e_triples (nullable, not both null): device [nocc (nocc+1)(nocc+2)/6 -
  * nocc] doubles, the per-triple shares in t_energy_triples' canonical order,
- * (1/3) sum over each triple's distinct orderings.  Costs about four times
- * the adjoint's forward contractions; deterministic. */
+ * (1/3) sum over each triple's distinct orderings.  Costs about three
+ * times t_energy's contractions, on the strided-view GEMMs of the adjoint;
+ * deterministic.  Workspace (what te_reserve with TE_RESERVE_FRAG
+ * allocates): about 8 nocc nvir^3 bytes for the transformed ovvv, plus three
+ * exact-slice operand sets of the same size each in TE_OZAKI (about 34 GB at
+ * nocc=32, nvir=320); TE_ENOMEM before any launch when the device cannot
+ * hold it. */
 te_status t_energy_frag(te_handle h, const te_cluster* c, const double* cf, te_precision p,
                         double* e_out, double* e_triples, te_stream_t s);
 
