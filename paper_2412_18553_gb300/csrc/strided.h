@@ -1,0 +1,82 @@
+// Strided-view contractions shared by the adjoint (vjp.cu) and the
+// fragment-projected energy (frag.cu): a float64 DFMA GEMM and an exact-slice
+// BF16 tensor-core GEMM over two-index row and K views, and the per-element
+// assembly of W~ and Y from a triple's three natural-layout G blocks.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "te_internal.h"
+
+namespace te {
+
+// one unique triple's epilogue arguments
+struct AdjArgs {
+  int o, v;
+  int i, j, k;
+  double w;  // gE * m / 3
+  const double* G;      // [3][v][v][v] for this triple
+  const double* ovs;    // [o][v][o][v]
+  const double* t1;     // [o][v]
+  const double* eps_o;
+  const double* eps_v;
+  double* dW;           // [v^3]
+  double* dY;           // [v^3]
+  double* dD;           // [v^3]
+  double* epart;        // per-block partial energies (unweighted by gE: m/3 e)
+  unsigned long long* dwmax;  // if set: max |dW~| (bit pattern of a non-negative double)
+  double* dpart;        // per-block sums of dD (the orbital-energy gradient of the triple's occupied indices)
+};
+
+__device__ __forceinline__ double wt_at(const AdjArgs& A, int x, int y, int z) {
+  const int64_t v = A.v, v2 = v * v, v3 = v2 * v;
+  return A.G[(x * v + y) * v + z] + A.G[v3 + (y * v + z) * v + x] + A.G[2 * v3 + (z * v + x) * v + y];
+}
+
+__device__ __forceinline__ double y_at(const AdjArgs& A, int x, int y, int z) {
+  const int64_t v = A.v, o = A.o;
+  auto ovs = [&](int P1, int a, int P2, int b) { return A.ovs[(((int64_t)P1 * v + a) * o + P2) * v + b]; };
+  return ovs(A.i, x, A.j, y) * A.t1[(int64_t)A.k * v + z] + ovs(A.j, y, A.k, z) * A.t1[(int64_t)A.i * v + x] +
+         ovs(A.i, x, A.k, z) * A.t1[(int64_t)A.j * v + y];
+}
+
+// C[m,n] += alpha sum_k A[m,k] B[k,n], m = (m1, m2) and k = (k1, k2) with a
+// stride per index (float64, DFMA; deterministic split-K)
+struct GemmView {
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t M1, M2, N, K1, K2;
+  int64_t a_m1, a_m2, a_k1, a_k2;
+  int64_t b_k1, b_k2, b_n;
+  int64_t c_m1, c_m2, c_n;
+  double alpha;
+};
+
+// the same over four BF16 slice planes per operand (slice s at base + s *
+// plane), C (+)= alpha 2^(ea + eb) sum_k A B (exact-slice products on mma.sync)
+struct OzView {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int64_t a_ps, b_ps;  // slice plane strides (elements)
+  double* C;
+  int64_t M1, M2, N, K1, K2;
+  int64_t a_m1, a_m2, a_k1, a_k2;
+  int64_t b_k1, b_k2, b_n;
+  int64_t c_m1, c_m2, c_n;
+  double alpha;
+  const int* ea;  // device scale exponents of A's and B's slices
+  const int* eb;
+  int overwrite;  // store instead of accumulate (single K split only)
+};
+
+cudaError_t gemm_strided(const GemmView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
+                         int64_t* launches);
+cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
+                    int64_t* launches);
+// doubles of split-K scratch the two GEMMs need for a cluster's contractions
+int64_t splitk_cap(int64_t o, int64_t v);
+int64_t oz_scratch_cap(int64_t o, int64_t v, int num_sms);
+// out = scale * (fixed-order sum of part[0..n))
+cudaError_t launch_sum_share(const double* part, int64_t n, double scale, double* out, cudaStream_t s);
+
+}  // namespace te

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 
+#include "strided.h"
 #include "tc_path.h"
 #include "te_internal.h"
 
@@ -30,35 +31,6 @@ namespace te {
 // ---------------------------------------------------------------------------
 // per-triple adjoint of the energy epilogue, one thread per ordered (a,b,c)
 // ---------------------------------------------------------------------------
-
-struct AdjArgs {
-  int o, v;
-  int i, j, k;
-  double w;  // gE * m / 3
-  const double* G;      // [3][v][v][v] for this triple
-  const double* ovs;    // [o][v][o][v]
-  const double* t1;     // [o][v]
-  const double* eps_o;
-  const double* eps_v;
-  double* dW;           // [v^3]
-  double* dY;           // [v^3]
-  double* dD;           // [v^3]
-  double* epart;        // per-block partial energies (unweighted by gE: m/3 e)
-  unsigned long long* dwmax;  // if set: max |dW~| (bit pattern of a non-negative double)
-  double* dpart;        // per-block sums of dD (the orbital-energy gradient of the triple's occupied indices)
-};
-
-__device__ __forceinline__ double wt_at(const AdjArgs& A, int x, int y, int z) {
-  const int64_t v = A.v, v2 = v * v, v3 = v2 * v;
-  return A.G[(x * v + y) * v + z] + A.G[v3 + (y * v + z) * v + x] + A.G[2 * v3 + (z * v + x) * v + y];
-}
-
-__device__ __forceinline__ double y_at(const AdjArgs& A, int x, int y, int z) {
-  const int64_t v = A.v, o = A.o;
-  auto ovs = [&](int P1, int a, int P2, int b) { return A.ovs[(((int64_t)P1 * v + a) * o + P2) * v + b]; };
-  return ovs(A.i, x, A.j, y) * A.t1[(int64_t)A.k * v + z] + ovs(A.j, y, A.k, z) * A.t1[(int64_t)A.i * v + x] +
-         ovs(A.i, x, A.k, z) * A.t1[(int64_t)A.j * v + y];
-}
 
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
   __shared__ double red[8], redd[8];
@@ -120,16 +92,6 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
 // are added in split order by k_splitk_add, so the result is deterministic.
 // ---------------------------------------------------------------------------
 
-struct GemmView {
-  const double* A;
-  const double* B;
-  double* C;
-  int64_t M1, M2, N, K1, K2;
-  int64_t a_m1, a_m2, a_k1, a_k2;
-  int64_t b_k1, b_k2, b_n;
-  int64_t c_m1, c_m2, c_n;
-  double alpha;
-};
 
 constexpr int GT = 64, GK = 16;
 
@@ -245,8 +207,8 @@ static int num_splits(int64_t tiles, int64_t K, int64_t MN, int num_sms, int64_t
   return (int)std::max<int64_t>(1, want);
 }
 
-static cudaError_t gemm(const GemmView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
-                        int64_t* launches) {
+cudaError_t gemm_strided(const GemmView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
+                         int64_t* launches) {
   const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
   const int64_t tm = (M + GT - 1) / GT, tn = (g.N + GT - 1) / GT;
   const int ns = num_splits(tm * tn, K, M * g.N, num_sms, scratch_cap);
@@ -275,20 +237,6 @@ static cudaError_t gemm(const GemmView& g, int num_sms, double* scratch, int64_t
 // approximately; each block's sums go to float64 once, at its end.
 // ---------------------------------------------------------------------------
 
-struct OzView {
-  const __nv_bfloat16* A;
-  const __nv_bfloat16* B;
-  int64_t a_ps, b_ps;  // slice plane strides (elements)
-  double* C;
-  int64_t M1, M2, N, K1, K2;
-  int64_t a_m1, a_m2, a_k1, a_k2;
-  int64_t b_k1, b_k2, b_n;
-  int64_t c_m1, c_m2, c_n;
-  double alpha;
-  const int* ea;  // device scale exponents of A's and B's slices
-  const int* eb;
-  int overwrite;  // store instead of accumulate (single K split only)
-};
 
 constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_KMAX = 1024, OZ_NS = 4;
 constexpr int OZ_THREADS = 256;  // eight warps, each 32 x 16 outputs
@@ -574,7 +522,7 @@ static cudaError_t launch_oz2(const OzView& g, dim3 grid, int kchunk, double* pa
 }
 
 // K in splits of at most OZ_KMAX (exactness), more when the output has few tiles
-static cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
+cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
                            int64_t* launches) {
   const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
   const int64_t tm = (M + OZ_BM - 1) / OZ_BM, tn = (g.N + OZ_BN - 1) / OZ_BN;
@@ -765,6 +713,11 @@ __global__ void __launch_bounds__(256) k_sum_share(const double* __restrict__ pa
   }
 }
 
+cudaError_t launch_sum_share(const double* part, int64_t n, double scale, double* out, cudaStream_t s) {
+  k_sum_share<<<1, 256, 0, s>>>(part, n, scale, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // driver
 // ---------------------------------------------------------------------------
@@ -774,7 +727,7 @@ struct VjpWork {
 };
 
 // doubles of split-K scratch: room for the partial tiles of a v x v output
-static int64_t splitk_cap(int64_t o, int64_t v) { return 80 * std::max(v * v, o * v); }
+int64_t splitk_cap(int64_t o, int64_t v) { return 80 * std::max(v * v, o * v); }
 
 size_t vjp_fp64_bytes(int64_t o, int64_t v) {
   const int64_t v3 = v * v * v, nt = num_unique_triples(o);
@@ -872,7 +825,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
       const double* t2rq = c->t2 + ((int64_t)rr * o + qq) * v2;
       const double* t2rp = c->t2 + ((int64_t)rr * o + pp) * v2;
       auto run = [&](GemmView gv) {
-        if (e == cudaSuccess) e = gemm(gv, h->num_sms, W.splitk, splitk_cap(o, v), s, &h->n_launches);
+        if (e == cudaSuccess) e = gemm_strided(gv, h->num_sms, W.splitk, splitk_cap(o, v), s, &h->n_launches);
       };
       if (g->ovvv) {
         // (a) dovvv[p,x,y,d] += sum_z G[x,y,z] t2[r,q,z,d]
@@ -936,7 +889,7 @@ namespace te {
 // the adjoint with the contractions on the tensor cores (exact BF16 slices)
 // ---------------------------------------------------------------------------
 
-static int64_t oz_scratch_cap(int64_t o, int64_t v, int num_sms) {
+int64_t oz_scratch_cap(int64_t o, int64_t v, int num_sms) {
   const int64_t splits = std::max<int64_t>((v * v + OZ_KMAX - 1) / OZ_KMAX + 1, 2LL * num_sms);
   return splits * std::max(v * v, o * v);
 }
@@ -1142,285 +1095,5 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
   if (e != cudaSuccess) return fail(TE_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
   return TE_OK;
 }
-
-// ---------------------------------------------------------------------------
-// Fragment-projected E(T): Eq. E_corr_CCSD_T with a general C^f
-// ---------------------------------------------------------------------------
-// E_x = (1/3) sum_{ijk} sum_{abc} sum_{i'} C_{ii'} W~_{i'jk} R[Z]_{ijk}: C acts on
-// the first occupied index of W~.  Summed over all ordered triples, C on any
-// one of the three occupied indices gives the same total, so every unique
-// triple takes the average S W~ = 1/3 (C_1 + C_2 + C_3) W~, which keeps the
-// joint (ijk, abc) permutation symmetry of W~:
-//   share_{ijk} = (m/3) sum_{abc} (S W~)_{ijk} R[V]_{ijk} / D_{ijk},  V = W~ + Y.
-// S W~ = P[S X] groups into G-like blocks like W~ = P[X].  C on one occupied
-// index of a G segment lands on exactly one of its two factors, and summing
-// the three placements gives two products per segment:
-//   SG(p,q,r) = 1/3 [ ovvvC[p] t2[r,q] + ovvv[p] t2C[r,q] + ovvvC[q] t2[r,p] + ovvv[q] t2C[r,p]
-//                     + t2LC[p] nooT[q][r] + t2L[p] nooTC[q][r] + t2LC[q] nooT[p][r] + t2L[q] nooTC[p][r] ]
-// with ovvvC = C on the first index of ovvv; t2C = C on the first plus C on
-// the second index of t2; t2LC = the t2L copy of t2 with C on its second
-// index; nooTC = the nooT copy of ooov with C on its first plus on its third
-// index.
-
-// out[a][p][b] (+)= sum_{p'} C[p][p'] in[a][p'][b]: C on one occupied index,
-// `outer` and `inner` the sizes around it; fixed summation order
-__global__ void k_occ_transform(const double* __restrict__ in, const double* __restrict__ C, int o, int64_t outer,
-                                int64_t inner, double* __restrict__ out, int accumulate) {
-  const int64_t n = outer * o * inner;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = e / (o * inner), b = e % inner;
-    const int p = (int)((e / inner) % o);
-    const double* src = in + a * o * inner + b;
-    double s = 0.0;
-    for (int q = 0; q < o; ++q) s += C[p * o + q] * src[q * inner];
-    out[e] = accumulate ? out[e] + s : s;
-  }
-}
-
-// per-block sums of (S W~) R[V] / D over the abc of one triple
-__global__ void __launch_bounds__(256) k_energy_proj(AdjArgs A, const double* __restrict__ SG) {
-  __shared__ double red[8];
-  const int64_t v = A.v, v3 = v * v * v;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double contrib = 0.0;
-  if (e < v3) {
-    const int a = (int)(e / (v * v)), b = (int)((e / v) % v), c = (int)(e % v);
-    const double W0 = wt_at(A, a, b, c), W1 = wt_at(A, a, c, b), W2 = wt_at(A, b, a, c);
-    const double W3 = wt_at(A, b, c, a), W4 = wt_at(A, c, a, b), W5 = wt_at(A, c, b, a);
-    const double Y0 = y_at(A, a, b, c), Y1 = y_at(A, a, c, b), Y2 = y_at(A, b, a, c);
-    const double Y3 = y_at(A, b, c, a), Y4 = y_at(A, c, a, b), Y5 = y_at(A, c, b, a);
-    // R at position abc: 4 X_abc + X_bca + X_cab - 2 (X_cba + X_acb + X_bac)
-    const double V0 = W0 + Y0, V1 = W1 + Y1, V2 = W2 + Y2, V3 = W3 + Y3, V4 = W4 + Y4, V5 = W5 + Y5;
-    const double RV = (4.0 * V0 - 2.0 * V5 - 2.0 * V1) + (V3 + V4 - 2.0 * V2);
-    AdjArgs S = A;
-    S.G = SG;
-    const double D = (A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k]) - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
-    contrib = wt_at(S, a, b, c) * RV / D;
-  }
-  for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = contrib;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += red[w];
-    A.epart[blockIdx.x] = t;
-  }
-}
-
-struct FragWork {
-  double *ovvvC, *t2C, *t2C2, *ooovC;      // C on occupied indices of the inputs
-  double *t2L, *nooT, *ovs;                // float64 helper copies of the inputs
-  double *t2LC, *nooTC, *ovs_unused;       // the same of t2C2 and ooovC
-  double *G, *SG;                          // [3][v][v][v] each
-  double *epart, *shares, *scratch;
-  int64_t scratch_cap;
-  char* slices[3];                         // exact-slice planes (mixed precision only)
-};
-
-static size_t frag_layout(int64_t o, int64_t v, bool slices, int num_sms, char* base, FragWork* W);
-
-size_t frag_bytes(int64_t o, int64_t v, te_precision p, int num_sms) {
-  FragWork W;
-  return frag_layout(o, v, p != TE_FP64, num_sms, nullptr, &W);
-}
-
-// carve the workspace (base = nullptr: sizes only)
-static size_t frag_layout(int64_t o, int64_t v, bool slices, int num_sms, char* base, FragWork* W) {
-  const int64_t v3 = v * v * v, nt = num_unique_triples(o), nblk = (v3 + 255) / 256;
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    off = (off + 1023) & ~size_t(1023);
-    char* r = base ? base + off : nullptr;
-    off += bytes;
-    return r;
-  };
-  auto d = [&](int64_t n) { return reinterpret_cast<double*>(take((size_t)n * 8)); };
-  W->ovvvC = d(o * v3);
-  W->t2C = d(o * o * v * v);
-  W->t2C2 = d(o * o * v * v);
-  W->ooovC = d(o * o * o * v);
-  W->t2L = d(o * v * v * o);
-  W->nooT = d(o * o * v * o);
-  W->ovs = d(o * v * o * v);
-  W->t2LC = d(o * v * v * o);
-  W->nooTC = d(o * o * v * o);
-  W->ovs_unused = d(o * v * o * v);
-  W->G = d(3 * v3);
-  W->SG = d(3 * v3);
-  W->epart = d(nblk);
-  W->shares = d(std::max<int64_t>(1, nt));
-  W->scratch_cap = slices ? oz_scratch_cap(o, v, num_sms) : splitk_cap(o, v);
-  W->scratch = d(W->scratch_cap);
-  for (int k = 0; k < 3; ++k) W->slices[k] = slices ? take(tc_slices_bytes((int)o, (int)v) + 1024) : nullptr;
-  return off + 1024;
-}
-
-te_status run_frag(Handle* h, const te_cluster* c, const double* cf, te_precision p, double* e_out,
-                   double* e_triples, cudaStream_t s) {
-  const int o = (int)c->nocc, v = (int)c->nvir;
-  const int64_t v2 = (int64_t)v * v, v3 = v2 * v, nt = num_unique_triples(o), nblk = (v3 + 255) / 256;
-  const bool oz = p != TE_FP64;
-  te_status st = ensure_workspace_public(h, frag_bytes(o, v, p, h->num_sms));
-  if (st != TE_OK) return st;
-  st = ensure_triples_public(h, o);
-  if (st != TE_OK) return st;
-  FragWork W;
-  frag_layout(o, v, oz, h->num_sms,
-              reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023)), &W);
-
-  // C on the occupied indices of the inputs
-  auto tr = [&](const double* in, int64_t outer, int64_t inner, double* out, int acc) {
-    const int64_t n = outer * o * inner;
-    k_occ_transform<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8 * 1024), 256, 0, s>>>(in, cf, o, outer,
-                                                                                           inner, out, acc);
-    ++h->n_launches;
-  };
-  tr(c->ovvv, 1, v3, W.ovvvC, 0);                           // ovvv[p,a,b,d]: first index
-  tr(c->t2, 1, (int64_t)o * v2, W.t2C, 0);                  // t2[r,q,a,b]: first index
-  tr(c->t2, o, v2, W.t2C, 1);                               //   plus second index
-  tr(c->t2, o, v2, W.t2C2, 0);                              // second index only
-  tr(c->ooov, 1, (int64_t)o * o * v, W.ooovC, 0);           // ooov[p,l,r,z]: first index
-  tr(c->ooov, (int64_t)o * o, v, W.ooovC, 1);               //   plus third index
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(TE_ECUDA, "transform launch: %s", cudaGetErrorString(e));
-
-  // float64 helper copies: t2L, nooT, ovs of the inputs; t2L of t2C2, nooT of ooovC
-  Prepared P{};
-  P.o = o; P.v = v; P.eps_o = c->eps_o; P.eps_v = c->eps_v; P.ovvv = c->ovvv; P.t2 = c->t2; P.t1 = c->t1;
-  P.t2L = W.t2L; P.nooT = W.nooT; P.ovs = W.ovs;
-  e = launch_prep_fp64(c, &P, s);
-  te_cluster cx = *c;
-  cx.t2 = W.t2C2;
-  cx.ooov = W.ooovC;
-  Prepared PX{};
-  PX.o = o; PX.v = v; PX.t2L = W.t2LC; PX.nooT = W.nooTC; PX.ovs = W.ovs_unused;
-  if (e == cudaSuccess) e = launch_prep_fp64(&cx, &PX, s);
-  h->n_launches += 6;
-  if (e != cudaSuccess) return fail(TE_ECUDA, "prep: %s", cudaGetErrorString(e));
-
-  // exact-slice planes: the inputs; (ovvvC, t2C, ooovC) for ovvv, t2 and nooT;
-  // t2C2 for t2L
-  SliceSet S0{}, SA{}, SB{};
-  if (oz) {
-    te_cluster ca = *c, cb = *c;
-    ca.ovvv = W.ovvvC;
-    ca.t2 = W.t2C;
-    ca.ooov = W.ooovC;
-    cb.t2 = W.t2C2;
-    st = tc_prepare_slices(c, W.slices[0], &S0, s);
-    if (st == TE_OK) st = tc_prepare_slices(&ca, W.slices[1], &SA, s);
-    if (st == TE_OK) st = tc_prepare_slices(&cb, W.slices[2], &SB, s);
-    if (st != TE_OK) return st;
-    h->n_launches += 18;
-  }
-
-  using bf = __nv_bfloat16;
-  std::vector<Triple> trip = unique_triples(o);
-  const double third = 1.0 / 3.0;
-  for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
-    const Triple T = trip[t];
-    e = cudaMemsetAsync(W.SG, 0, sizeof(double) * 3 * v3, s);
-    if (e != cudaSuccess) break;
-    if (!oz) {
-      e = launch_gemm_fp64(&P, h->d_triples, t, 1, W.G, s);
-      ++h->n_launches;
-    }
-    for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
-      int pp, qq, rr;
-      if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
-      else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
-      else { pp = T.k; qq = T.i; rr = T.j; }
-      double* Gg = W.G + gi * v3;
-      double* SGg = W.SG + gi * v3;
-      if (!oz) {
-        // float64: the eight products of SG(p,q,r), rows (x, y), columns z
-        auto run = [&](const double* A, int64_t am1, int64_t am2, int64_t K, const double* B, int64_t bn) {
-          if (e == cudaSuccess)
-            e = gemm(GemmView{A, B, SGg, v, v, v, K, 1, am1, am2, 1, 0, 1, 0, bn, v2, v, 1, third}, h->num_sms,
-                     W.scratch, W.scratch_cap, s, &h->n_launches);
-        };
-        const int64_t orq = ((int64_t)rr * o + qq) * v2, orp = ((int64_t)rr * o + pp) * v2;
-        run(W.ovvvC + pp * v3, v2, v, v, c->t2 + orq, v);     // S1: ovvvC[p,x,y,d] t2[r,q,z,d]
-        run(c->ovvv + pp * v3, v2, v, v, W.t2C + orq, v);     //     ovvv[p] t2C[r,q]
-        run(W.ovvvC + qq * v3, v, v2, v, c->t2 + orp, v);     // S2: ovvvC[q,y,x,d] t2[r,p,z,d]
-        run(c->ovvv + qq * v3, v, v2, v, W.t2C + orp, v);     //     ovvv[q] t2C[r,p]
-        const int64_t lp = (int64_t)pp * v2 * o, lq = (int64_t)qq * v2 * o;
-        const int64_t nqr = ((int64_t)qq * o + rr) * v * o, npr = ((int64_t)pp * o + rr) * v * o;
-        run(W.t2LC + lp, o, (int64_t)v * o, o, W.nooT + nqr, o);   // S3: t2LC[p][y][x][l] nooT[q][r][z][l]
-        run(W.t2L + lp, o, (int64_t)v * o, o, W.nooTC + nqr, o);   //     t2L[p] nooTC[q][r]
-        run(W.t2LC + lq, (int64_t)v * o, o, o, W.nooT + npr, o);   // S4: t2LC[q][x][y][l] nooT[p][r][z][l]
-        run(W.t2L + lq, (int64_t)v * o, o, o, W.nooTC + npr, o);   //     t2L[q] nooTC[p][r]
-      } else {
-        auto run = [&](const OzView& gv) {
-          if (e == cudaSuccess) e = gemm_oz(gv, h->num_sms, W.scratch, W.scratch_cap, s, &h->n_launches);
-        };
-        const int64_t vp = S0.vp, op = S0.op;
-        auto ovvv_of = [&](const SliceSet& S, int x) { return static_cast<const bf*>(S.ovvv) + x * S.ovvv_p; };
-        auto t2_of = [&](const SliceSet& S, int r, int q) {
-          return static_cast<const bf*>(S.t2) + ((int64_t)r * o + q) * S.t2_rq;
-        };
-        auto t2L_of = [&](const SliceSet& S, int q) { return static_cast<const bf*>(S.t2L) + q * S.t2L_q; };
-        auto nooT_of = [&](const SliceSet& S, int p, int r) {
-          return static_cast<const bf*>(S.nooT) + ((int64_t)p * o + r) * S.nooT_pr;
-        };
-        // S1: rows (x, y) of ovvv[p] (K = d), columns z of t2[r,q]
-        auto s1 = [&](const SliceSet& SX, const SliceSet& ST, int ov, int r, int q, double* C, double al, int ow) {
-          run(OzView{ovvv_of(SX, ov), t2_of(ST, r, q), SX.ovvv_plane, ST.t2_plane, C, v, v, v, v, 1, v * vp, vp, 1,
-                     0, 1, 0, vp, v2, v, 1, al, SX.exps + 0, ST.exps + 1, ow});
-        };
-        // S2: rows (x, y) of ovvv[q] read transposed (y, x)
-        auto s2 = [&](const SliceSet& SX, const SliceSet& ST, int ov, int r, int q, double* C, double al) {
-          run(OzView{ovvv_of(SX, ov), t2_of(ST, r, q), SX.ovvv_plane, ST.t2_plane, C, v, v, v, v, 1, vp, v * vp, 1,
-                     0, 1, 0, vp, v2, v, 1, al, SX.exps + 0, ST.exps + 1, 0});
-        };
-        // S3: t2L[p][y][x][l] nooT[q][r][z][l]
-        auto s3 = [&](const SliceSet& SL, const SliceSet& SN, int lp, int nq, int nr, double* C, double al) {
-          run(OzView{t2L_of(SL, lp), nooT_of(SN, nq, nr), SL.t2L_plane, SN.nooT_plane, C, v, v, v, o, 1, op,
-                     v * op, 1, 0, 1, 0, op, v2, v, 1, al, SL.exps + 2, SN.exps + 3, 0});
-        };
-        // S4: t2L[q][x][y][l] nooT[p][r][z][l]
-        auto s4 = [&](const SliceSet& SL, const SliceSet& SN, int lq, int np, int nr, double* C, double al) {
-          run(OzView{t2L_of(SL, lq), nooT_of(SN, np, nr), SL.t2L_plane, SN.nooT_plane, C, v, v, v, o, 1, v * op,
-                     op, 1, 0, 1, 0, op, v2, v, 1, al, SL.exps + 2, SN.exps + 3, 0});
-        };
-        // the G block itself (first product overwrites)
-        s1(S0, S0, pp, rr, qq, Gg, 1.0, 1);
-        s2(S0, S0, qq, rr, pp, Gg, 1.0);
-        s3(S0, S0, pp, qq, rr, Gg, 1.0);
-        s4(S0, S0, qq, pp, rr, Gg, 1.0);
-        // its projection
-        s1(SA, S0, pp, rr, qq, SGg, third, 0);
-        s1(S0, SA, pp, rr, qq, SGg, third, 0);
-        s2(SA, S0, qq, rr, pp, SGg, third);
-        s2(S0, SA, qq, rr, pp, SGg, third);
-        s3(SB, S0, pp, qq, rr, SGg, third);
-        s3(S0, SA, pp, qq, rr, SGg, third);
-        s4(SB, S0, qq, pp, rr, SGg, third);
-        s4(S0, SA, qq, pp, rr, SGg, third);
-      }
-    }
-    if (e != cudaSuccess) break;
-    AdjArgs A{};
-    A.o = o; A.v = v; A.i = T.i; A.j = T.j; A.k = T.k;
-    A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v; A.epart = W.epart;
-    k_energy_proj<<<(unsigned)nblk, 256, 0, s>>>(A, W.SG);
-    k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
-    h->n_launches += 2;
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess && e_triples && nt > 0)
-    e = cudaMemcpyAsync(e_triples, W.shares, sizeof(double) * nt, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && e_out) {
-    if (nt > 0) {
-      e = launch_reduce_total(W.shares, nt, e_out, s);
-      ++h->n_launches;
-    } else {
-      e = cudaMemsetAsync(e_out, 0, sizeof(double), s);
-    }
-  }
-  if (e != cudaSuccess) return fail(TE_ECUDA, "projected energy launch: %s", cudaGetErrorString(e));
-  return TE_OK;
-}
-
 
 }  // namespace te
