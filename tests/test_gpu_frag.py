@@ -6,7 +6,8 @@ and exact-slice ("ozaki"):
   for a general (non-symmetric) matrix;
 * the identity projector gives t_energy's value;
 * projectors of a partition of the occupied space add up to t_energy;
-* nocc=16 nvir=120: exact-slice against float64;
+* nocc=16 nvir=120: sampled per-triple shares against stored oracle values
+  (tests/golden/oracle_o16v120_frag.json), and exact-slice against float64;
 * determinism and argument checks."""
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ import torch
 
 import tegen
 from oracle import t_energy as O
-from gpu_common import need_gpu, shuffled
+from gpu_common import check_inputs_match, golden, need_gpu, shuffled
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +77,20 @@ def test_partition_of_unity(te, prec):
         total += float(te.t_energy_frag(a, f @ f.T, prec))
     e = float(te.t_energy(a, "fp64"))
     assert abs(total - e) <= (1e-11 if prec == "fp64" else 1e-7) * abs(e) + (0 if prec == "fp64" else 1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_o16v120_sampled_shares_vs_golden(te, prec):
+    """float64: 1e-12 relative per share; exact-slice: 1e-9 Ha per share (the
+    per-share bar of the unprojected energy at this size)."""
+    g = golden("o16v120_frag")
+    cl = tegen.make_cluster(g["nocc"], g["nvir"], g["naux"], g["seed"])
+    check_inputs_match(cl, g)
+    _, sh = te.t_energy_frag(dev(cl.arrays()), np.array(g["cf"]), prec, shares=True)
+    sh = sh.cpu().numpy()
+    for idx, ref in zip(g["triple_index"], g["shares"]):
+        tol = 1e-12 * abs(ref) + 1e-18 if prec == "fp64" else 1e-9
+        assert abs(sh[idx] - ref) <= tol, (idx, sh[idx], ref)
 
 
 def test_exact_slice_against_float64_o16v120(te):
