@@ -110,10 +110,12 @@ class Clocks:
 
 
 def make_workload(name, device):
+    """The named workload's seven arrays on cuda:device, or on the host when
+    device is None (the oracle's reference arm on a machine without a GPU)."""
     import tegen
     o, v, naux, seed = tegen.WORKLOADS[name]
-    cl = tegen.make_cluster(o, v, naux, seed, device="cuda")
-    dev = torch.device("cuda", device)
+    cl = tegen.make_cluster(o, v, naux, seed, device="cuda" if device is not None else "cpu")
+    dev = torch.device("cuda", device) if device is not None else torch.device("cpu")
     arrs = {}
     for n, x in cl.arrays().items():
         t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
@@ -196,7 +198,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    (o, v, naux, seed), arrs = make_workload(args.workload, 0)
+    (o, v, naux, seed), arrs = make_workload(args.workload, 0 if torch.cuda.is_available() else None)
     from oracle import t_energy as O
     torch.set_num_threads(os.cpu_count() or 1)
     c = O.inputs(**{n: t.cpu() for n, t in arrs.items()})
