@@ -441,8 +441,8 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
   for (int64_t x = 0; x < n; ++x) {
     te_status st = host_check(h, cs + x, p);
     if (st != TE_OK) {
-      char msg[512];
-      snprintf(msg, sizeof(msg), "cluster %lld: %s", (long long)x, te_last_error());
+      char msg[600];  // the message buffer holds at most 511 characters, plus the prefix
+      snprintf(msg, sizeof(msg), "cluster %lld: %.511s", (long long)x, te_last_error());
       return fail(st, "%s", msg);
     }
   }

@@ -552,7 +552,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
     const int quad = warp & 3;
     const int chunk0 = (warp - 2) >> 2;  // 0 or 1: this warp's first 16-column chunk
     const int row = quad * 32 + lane;
-    const int64_t v2 = (int64_t)P.v * P.v;
     float gscale = 1.f;
     if (is_ozaki(MODE)) gscale = ldexpf(1.f, P.exps[4]);
     uint32_t acc = 0, acc_phase = 0;
@@ -757,7 +756,6 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.ldz = round_up(v, 4);
   const int64_t tiles = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
   int64_t want = (4LL * std::max(1, h->num_sms) + tiles - 1) / tiles;
-  const int64_t nbk = (v + 7) / 8;
   const int64_t per_slot = g_slot_floats(v, pl.cw) * 4;
   const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(6LL << 30) / per_slot);
   want = std::max<int64_t>(want, 4);  // fewer launches per cluster
@@ -881,7 +879,7 @@ struct EnergyMapsHost {
 static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, int nslots, const TcBuffers& b,
                                    EnergyMapsHost* E) {
   std::memset(E, 0, sizeof(*E));
-  const uint64_t V = v, O = o, cw = pl.cw, ldz = pl.ldz, vq = pl.vq;
+  const uint64_t V = v, O = o, vq = pl.vq;
   te_status s;
   {  // ovs32 [i][a][j][vq]: dims (b, j, a, i)
     const uint64_t d[4] = {V, O, V, O};
