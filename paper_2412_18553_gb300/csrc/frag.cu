@@ -48,7 +48,8 @@ __global__ void k_occ_transform(const double* __restrict__ in, const double* __r
   }
 }
 
-// per-block sums of (S W~) R[V] / D over the abc of one triple
+// per-block sums of (S W~) R[V] / D over the abc of one triple, one thread per
+// orbit representative a >= b >= c
 __global__ void __launch_bounds__(256) k_energy_proj(AdjArgs A, const double* __restrict__ SG) {
   __shared__ double red[8];
   const int64_t v = A.v, v3 = v * v * v;
@@ -56,17 +57,23 @@ __global__ void __launch_bounds__(256) k_energy_proj(AdjArgs A, const double* __
   double contrib = 0.0;
   if (e < v3) {
     const int a = (int)(e / (v * v)), b = (int)((e / v) % v), c = (int)(e % v);
-    const double W0 = wt_at(A, a, b, c), W1 = wt_at(A, a, c, b), W2 = wt_at(A, b, a, c);
-    const double W3 = wt_at(A, b, c, a), W4 = wt_at(A, c, a, b), W5 = wt_at(A, c, b, a);
-    const double Y0 = y_at(A, a, b, c), Y1 = y_at(A, a, c, b), Y2 = y_at(A, b, a, c);
-    const double Y3 = y_at(A, b, c, a), Y4 = y_at(A, c, a, b), Y5 = y_at(A, c, b, a);
-    // R at position abc: 4 X_abc + X_bca + X_cab - 2 (X_cba + X_acb + X_bac)
-    const double V0 = W0 + Y0, V1 = W1 + Y1, V2 = W2 + Y2, V3 = W3 + Y3, V4 = W4 + Y4, V5 = W5 + Y5;
-    const double RV = (4.0 * V0 - 2.0 * V5 - 2.0 * V1) + (V3 + V4 - 2.0 * V2);
-    AdjArgs S = A;
-    S.G = SG;
-    const double D = (A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k]) - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
-    contrib = wt_at(S, a, b, c) * RV / D;
+    if (a >= b && b >= c) {
+      double W[6], Y[6], V[6], RV[6];
+      orbit_values(A, a, b, c, W, Y);
+#pragma unroll
+      for (int n = 0; n < 6; ++n) V[n] = W[n] + Y[n];
+      r_orbit(V, RV);
+      AdjArgs S = A;
+      S.G = SG;
+      const int p[6][3] = {{a, b, c}, {a, c, b}, {b, a, c}, {b, c, a}, {c, a, b}, {c, b, a}};
+      const unsigned distinct = orbit_distinct(a, b, c);
+      const double D = (A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k]) - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
+      double t = 0.0;
+#pragma unroll
+      for (int n = 0; n < 6; ++n)
+        if (distinct >> n & 1u) t += wt_at(S, p[n][0], p[n][1], p[n][2]) * RV[n];
+      contrib = t / D;
+    }
   }
   for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = contrib;

@@ -39,6 +39,44 @@ __device__ __forceinline__ double y_at(const AdjArgs& A, int x, int y, int z) {
          ovs(A.i, x, A.k, z) * A.t1[(int64_t)A.j * v + y];
 }
 
+// The orbit of (a, b, c) under permutations, positions in the order abc,
+// acb, bac, bca, cab, cba (0, 3, 4 even; 1, 2, 5 odd): their linear indices,
+// and which of them are distinct elements (a = b or b = c merge positions).
+__device__ __forceinline__ void orbit_index(int64_t v, int a, int b, int c, int64_t* idx) {
+  idx[0] = (a * v + b) * v + c;
+  idx[1] = (a * v + c) * v + b;
+  idx[2] = (b * v + a) * v + c;
+  idx[3] = (b * v + c) * v + a;
+  idx[4] = (c * v + a) * v + b;
+  idx[5] = (c * v + b) * v + a;
+}
+__device__ __forceinline__ unsigned orbit_distinct(int a, int b, int c) {
+  if (a == b && b == c) return 0x01u;
+  if (a == b) return 0x13u;  // abc = bac, acb = bca, cab = cba: keep 0, 1, 4
+  if (b == c) return 0x0Du;  // abc = acb, bac = cab, bca = cba: keep 0, 2, 3
+  return 0x3Fu;
+}
+// R at every position of the orbit (identity 4, 3-cycles +1, transpositions
+// -2): 3 x_p + (sum over p's parity class) - 2 (sum over the other class)
+__device__ __forceinline__ void r_orbit(const double* x, double* r) {
+  const double se = (x[0] + x[3]) + x[4], so = (x[1] + x[2]) + x[5];
+  r[0] = (3.0 * x[0] + se) - 2.0 * so;
+  r[3] = (3.0 * x[3] + se) - 2.0 * so;
+  r[4] = (3.0 * x[4] + se) - 2.0 * so;
+  r[1] = (3.0 * x[1] + so) - 2.0 * se;
+  r[2] = (3.0 * x[2] + so) - 2.0 * se;
+  r[5] = (3.0 * x[5] + so) - 2.0 * se;
+}
+// W~ and Y at the six positions of the orbit of (a, b, c)
+__device__ __forceinline__ void orbit_values(const AdjArgs& A, int a, int b, int c, double* W, double* Y) {
+  const int p[6][3] = {{a, b, c}, {a, c, b}, {b, a, c}, {b, c, a}, {c, a, b}, {c, b, a}};
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    W[n] = wt_at(A, p[n][0], p[n][1], p[n][2]);
+    Y[n] = y_at(A, p[n][0], p[n][1], p[n][2]);
+  }
+}
+
 // C[m,n] += alpha sum_k A[m,k] B[k,n], m = (m1, m2) and k = (k1, k2) with a
 // stride per index (float64, DFMA; deterministic split-K)
 struct GemmView {

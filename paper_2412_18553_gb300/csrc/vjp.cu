@@ -32,32 +32,40 @@ namespace te {
 // per-triple adjoint of the energy epilogue, one thread per ordered (a,b,c)
 // ---------------------------------------------------------------------------
 
+// One thread per orbit representative a >= b >= c (the other threads of the
+// v^3 grid have nothing to do): W~ and Y are formed once per orbit and every
+// distinct element of the orbit gets its dW~, dY and dD.
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
   __shared__ double red[8], redd[8];
   const int64_t v = A.v, v3 = v * v * v;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double contrib = 0.0, dsum = 0.0;
+  double contrib = 0.0, dsum = 0.0, wmax = 0.0;
   if (e < v3) {
     const int a = (int)(e / (v * v)), b = (int)((e / v) % v), c = (int)(e % v);
-    // positions abc, acb, bac, bca, cab, cba
-    const double W0 = wt_at(A, a, b, c), W1 = wt_at(A, a, c, b), W2 = wt_at(A, b, a, c);
-    const double W3 = wt_at(A, b, c, a), W4 = wt_at(A, c, a, b), W5 = wt_at(A, c, b, a);
-    const double Y0 = y_at(A, a, b, c), Y1 = y_at(A, a, c, b), Y2 = y_at(A, b, a, c);
-    const double Y3 = y_at(A, b, c, a), Y4 = y_at(A, c, a, b), Y5 = y_at(A, c, b, a);
-    // R at position abc: 4 X_abc + X_bca + X_cab - 2 (X_cba + X_acb + X_bac)
-    auto R0 = [](double x0, double x1, double x2, double x3, double x4, double x5) {
-      return (4.0 * x0 - 2.0 * x5 - 2.0 * x1) + (x3 + x4 - 2.0 * x2);
-    };
-    const double D = (A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k]) - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
-    const double RW = R0(W0, W1, W2, W3, W4, W5);
-    const double RY = R0(Y0, Y1, Y2, Y3, Y4, Y5);
-    const double RV = RW + RY;
-    const double rD = 1.0 / D, q = A.w * rD;
-    A.dW[e] = q * (2.0 * RW + RY);
-    A.dY[e] = q * RW;
-    dsum = -q * W0 * RV * rD;
-    A.dD[e] = dsum;
-    contrib = W0 * RV * rD;
+    if (a >= b && b >= c) {
+      double W[6], Y[6], RW[6], RY[6];
+      int64_t idx[6];
+      orbit_values(A, a, b, c, W, Y);
+      orbit_index(v, a, b, c, idx);
+      r_orbit(W, RW);
+      r_orbit(Y, RY);
+      const unsigned distinct = orbit_distinct(a, b, c);
+      const double D = (A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k]) - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
+      const double rD = 1.0 / D, q = A.w * rD;
+#pragma unroll
+      for (int n = 0; n < 6; ++n) {
+        if (!(distinct >> n & 1u)) continue;
+        const double RV = RW[n] + RY[n];
+        const double dw = q * (2.0 * RW[n] + RY[n]);
+        const double dd = -q * W[n] * RV * rD;
+        A.dW[idx[n]] = dw;
+        A.dY[idx[n]] = q * RW[n];
+        A.dD[idx[n]] = dd;
+        dsum += dd;
+        contrib += W[n] * RV * rD;
+        wmax = fmax(wmax, fabs(dw));
+      }
+    }
   }
   for (int off = 16; off > 0; off >>= 1) {
     contrib += __shfl_down_sync(0xffffffffu, contrib, off);
@@ -68,7 +76,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
     redd[threadIdx.x >> 5] = dsum;
   }
   if (A.dwmax) {
-    double m = e < v3 ? fabs(A.dW[e]) : 0.0;
+    double m = wmax;
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(A.dwmax, (unsigned long long)__double_as_longlong(m));
   }
