@@ -20,6 +20,14 @@ Formula (C^f = identity, i.e. the whole-cluster (T)):
 * R[X]_{ijk} = 4 X_{ijk} + X_{kij} + X_{jki} - 2 X_{kji} - 2 X_{ikj} - 2 X_{jik}
   (fixed abc).
 
+With a general C^f (``t_energy_projected``): the first occupied index of W~
+is projected, E_x = (1/3) sum_{ijk} sum_{abc} sum_{i'} C^f_{ii'} W~_{i'jk} R[Z]_{ijk}
+over all ordered triples; at C^f = 1 this is the restricted sum below, and
+for a general C^f the literal restricted sum would depend on the labelling of
+the virtual orbitals, so the full sum is the reading.  Pinned by
+tests/test_oracle_projected.py (identity, partition of unity, slot
+independence, shares, linearity).
+
 Readings where the printed text is garbled (each is listed in the design notes):
 
 * the bracket of Eq. W is read as  sum_d (ia|bd) t_{kj}^{cd} - sum_l (ia|jl) t_{lk}^{bc}
