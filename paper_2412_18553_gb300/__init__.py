@@ -257,13 +257,14 @@ def t_energy_frag(cluster, cf, precision="fp64", handle=None, device=None, strea
     the [nocc, nocc] projector acting on W~'s first occupied index.  Returns a
     0-dim float64 CUDA tensor, or (E, per-triple shares) with shares=True.
     precision: "fp64" or "ozaki"."""
+    o = int(_as_dict(cluster)["eps_o"].shape[0])
+    cf = torch.as_tensor(cf, dtype=torch.float64)
+    if tuple(cf.shape) != (o, o):
+        raise ValueError(f"cf must be [{o}, {o}], got {tuple(cf.shape)}")
     dev = _device_of(cluster, device)
     h = _handle(handle, dev)
     t = _tensors(cluster, dev)
-    o = t["eps_o"].shape[0]
-    cf = torch.as_tensor(cf, dtype=torch.float64).to(torch.device("cuda", dev)).contiguous()
-    if tuple(cf.shape) != (o, o):
-        raise ValueError(f"cf must be [{o}, {o}], got {tuple(cf.shape)}")
+    cf = cf.to(torch.device("cuda", dev)).contiguous()
     e = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
     sh = torch.empty(max(1, num_unique_triples(o)), dtype=torch.float64, device=e.device) if shares else None
     c = _struct(t)

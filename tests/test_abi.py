@@ -74,3 +74,12 @@ def test_canonical_triple_order_matches_oracle():
     for o in range(1, 7):
         assert len(unique_triples(o)) == te.num_unique_triples(o)
     assert unique_triples(3) == [(1, 0, 0), (1, 1, 0), (2, 0, 0), (2, 1, 0), (2, 1, 1), (2, 2, 0), (2, 2, 1)]
+
+
+def test_projector_shape_is_checked_before_any_device_work(lib):
+    import numpy as np
+    import paper_2412_18553_gb300 as te
+    import tegen
+    cl = tegen.make_cluster(3, 5, 32, 0).arrays()
+    with pytest.raises(ValueError):
+        te.t_energy_frag(cl, np.eye(4))
