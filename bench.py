@@ -28,6 +28,7 @@ import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
 WORKLOAD = "o32v320"
+TRAFFIC_PER_TRIPLE = 2.486e9  # k_gemm_tc DRAM bytes per triple at nvir = 320, 7-bit slices (ncu)
 METRIC = "(T) GFLOP/s & clusters/s, tensor-pipe % of peak, at |dE(T)|<=1e-7 Ha vs FP64"
 
 
@@ -52,6 +53,15 @@ def parse():
                     help="skip the fragment-projected energy (nocc=16 nvir=120, exact-slice and float64)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched measurement (16 clusters, nocc 8..20, nvir = 8 nocc)")
+    ap.add_argument("--no-fp64-anchor", action="store_true",
+                    help="skip the one float64 GPU pass over the whole cluster (about 11 minutes at "
+                         "nocc=32 nvir=320) that gives the FP64 GPU rate and the whole-cluster |dE|")
+    ap.add_argument("--vjp-triples", type=int, default=0,
+                    help="time the adjoint of this many single-triple ranges of the workload itself "
+                         "(both modes) and extrapolate; for clusters whose whole adjoint is too long")
+    ap.add_argument("--no-batch96", action="store_true",
+                    help="skip the 96-cluster uneven batch leg (every --batch-stride-th seed timed, "
+                         "extrapolated by flop count)")
     return ap.parse_args()
 
 
@@ -123,26 +133,26 @@ def make_workload(name, device):
     return (o, v, naux, seed), arrs
 
 
-def run_batch96(args):
+def batch96_leg(te, h, prec, stride, local, fp64_seeds=1):
     """The 96-cluster uneven batch (seeds 0..95: nocc ~ [10,40], nvir = round(nocc
     U[8,12]), naux = 4 (o + v)).  Its float64 ovvv totals 709 GB, more than one
     GPU (or the host) holds, so clusters are formed one after another on the
-    device (outside the timed region) and each is timed on its own after an
-    untimed call that autotunes its tiles.  ``--batch-stride s`` times seeds
-    0, s, 2s, ...; clusters/s of the whole batch is then extrapolated by flop
-    count and says so."""
+    device (outside the timed region; ovvv by the generator's GPU GEMM) and each
+    is timed on its own after an untimed call that warms and tunes it.  Seeds 0,
+    s, 2s, ... are timed; clusters/s of the whole batch is extrapolated by flop
+    count and says so.  The float64 GPU path is timed the same way on the
+    ``fp64_seeds`` timed seeds of least work, with |dE| of those clusters."""
     import tegen
-    import paper_2412_18553_gb300 as te
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    h = te.Handle(local)
-    prec = args.precision
-    seeds = list(range(0, 96, max(1, args.batch_stride)))
+    seeds = list(range(0, 96, max(1, stride)))
     F_all = sum(te.flop_count(*tegen.batch_sizes(s)[:2]) for s in range(96))
+    F_of = {s: te.flop_count(*tegen.batch_sizes(s)[:2]) for s in seeds}
+    f64_pick = sorted(seeds, key=lambda s: F_of[s])[:max(0, fp64_seeds)]
     tot_ms, F_run, launches = 0.0, 0.0, 0
-    clocks = Clocks(local)
+    f64_ms, f64_F, dE = 0.0, 0.0, []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     for s in seeds:
-        c = tegen.make_batch([s], rule="uneven", device="cuda")[0]
+        c = tegen.make_batch([s], rule="uneven", device="cuda", host_flop_limit=0.0)[0]
         a = {n: (x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))).to(
             torch.device("cuda", local)).contiguous() for n, x in c.arrays().items()}
         del c
@@ -150,28 +160,103 @@ def run_batch96(args):
         te.t_energy(a, prec, handle=h)
         torch.cuda.synchronize()
         l0 = h.profile_read(reset=False)["launches"]
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        te.t_energy(a, prec, handle=h)
+        eb = te.t_energy(a, prec, handle=h)
         e1.record()
         torch.cuda.synchronize()
         tot_ms += e0.elapsed_time(e1)
         launches += h.profile_read(reset=False)["launches"] - l0
-        F_run += te.flop_count(int(a["eps_o"].shape[0]), int(a["eps_v"].shape[0]))
+        F_run += F_of[s]
+        if s in f64_pick:
+            e0.record()
+            e64 = te.t_energy(a, "fp64", handle=h)
+            e1.record()
+            torch.cuda.synchronize()
+            f64_ms += e0.elapsed_time(e1)
+            f64_F += F_of[s]
+            dE.append({"seed": s, "dE_ha": abs(float(eb) - float(e64)), "e_t_ha": float(e64)})
         del a
         torch.cuda.empty_cache()
-    clk = clocks.stop()
+    h.sync()
     t_all = tot_ms / 1e3 * (F_all / F_run)
-    out = {"metric": "clusters/s of the 96-cluster uneven batch", "value": 96.0 / t_all, "unit": "clusters/s",
-           "n_gpus": 1, "higher_is_better": True, "precision": prec,
-           "gflops": F_run / (tot_ms / 1e3) / 1e9, "clusters_timed": len(seeds), "seconds_timed": tot_ms / 1e3,
-           "flop_batch": F_all, "flop_timed": F_run,
-           "extrapolated": len(seeds) < 96, "gpu_launches": launches, "clocks": clk,
-           "config": {"workload": "batch96: seeds 0..95, nocc ~ [10,40], nvir = round(nocc U[8,12]), naux = 4(o+v)",
-                      "timed_seeds": seeds, "l2": "inputs larger than L2"}}
+    out = {"workload": "batch96: seeds 0..95, nocc ~ [10,40], nvir = round(nocc U[8,12]), naux = 4(o+v)",
+           "precision": prec, "clusters_per_s": 96.0 / t_all, "gflops": F_run / (tot_ms / 1e3) / 1e9,
+           "timed_seeds": seeds, "seconds_timed": tot_ms / 1e3, "flop_batch": F_all, "flop_timed": F_run,
+           "extrapolated": len(seeds) < 96, "gpu_launches": launches}
+    if f64_F > 0:
+        t64 = f64_ms / 1e3 * (F_all / f64_F)
+        out["fp64_gpu"] = {"clusters_per_s": 96.0 / t64, "gflops": f64_F / (f64_ms / 1e3) / 1e9,
+                           "timed_seeds": f64_pick, "seconds_timed": f64_ms / 1e3, "extrapolated": True}
+        out["speedup_vs_fp64"] = out["clusters_per_s"] / out["fp64_gpu"]["clusters_per_s"]
+        out["dE_vs_fp64"] = dE
+    return out
+
+
+def run_batch96(args):
+    """``--workload batch96``: the batch leg alone, as its own JSON line."""
+    import paper_2412_18553_gb300 as te
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    h = te.Handle(local)
+    clocks = Clocks(local)
+    leg = batch96_leg(te, h, args.precision, args.batch_stride, local)
+    clk = clocks.stop()
+    out = {"metric": "clusters/s of the 96-cluster uneven batch", "value": leg["clusters_per_s"],
+           "unit": "clusters/s", "n_gpus": 1, "higher_is_better": True, "clocks": clk,
+           "gpu_launches": leg["gpu_launches"], "config": {"workload": leg["workload"], "l2": "inputs larger than L2"},
+           "batch96": leg}
     print(json.dumps(out))
     return 0
+
+
+def vjp_sample_leg(te, h, arrs, o, v, ntrip, world):
+    """t_energy_vjp_triples over ``ntrip`` single-triple ranges spread over the
+    canonical order (the heaviest last), exact slices and float64, CUDA-event
+    timed; the whole-cluster adjoint time is extrapolated by triple count.
+    The two modes' gradients are compared per input on 4096 entries (the 2048
+    largest of the exact-slice gradient and 2048 seeded ones), relative to the
+    float64 gradient's largest magnitude; only one gradient set is alive on
+    the device at a time."""
+    nt = te.num_unique_triples(o)
+    picks = sorted(set([nt - 1] + [q * (nt // max(1, ntrip)) for q in range(max(0, ntrip - 1))]))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {"triples": picks, "ntriples": nt}
+    sample = {}
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    for prec in ("ozaki", "fp64"):
+        ms, es, rel = 0.0, [], {}
+        for tt in picks:
+            torch.cuda.synchronize()
+            e0.record()
+            e, g = te.t_energy_vjp_triples(arrs, tt, tt + 1, precision=prec, handle=h)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            es.append(float(e))
+            for n, x in g.items():
+                flat = x.view(-1)
+                if prec == "ozaki":
+                    k = min(2048, flat.numel())
+                    top = flat.abs().topk(k).indices
+                    rnd = torch.randint(0, flat.numel(), (k,), device="cuda", generator=gen)
+                    idx = torch.cat([top, rnd])
+                    sample[(tt, n)] = (idx, flat[idx].clone())
+                else:
+                    idx, vo = sample.pop((tt, n))
+                    scale = max(float(flat.abs().max()), 1e-300)
+                    rel[n] = max(rel.get(n, 0.0), float((vo - flat[idx]).abs().max()) / scale)
+            del e, g
+            torch.cuda.empty_cache()
+        out[prec] = {"ms_per_triple": ms / len(picks), "ms_cluster_extrapolated": ms / len(picks) * nt,
+                     "gflops_3F": world * 3 * 12.0 * v ** 3 * (v + o) / (ms / len(picks) / 1e3) / 1e9,
+                     "shares": es}
+        if prec == "fp64":
+            out["grad_rel_diff_ozaki_vs_fp64"] = rel
+    out["speedup_vs_fp64"] = out["fp64"]["ms_per_triple"] / out["ozaki"]["ms_per_triple"]
+    out["dE_shares_ozaki_vs_fp64_ha"] = max(abs(a - b) for a, b in zip(out["ozaki"]["shares"], out["fp64"]["shares"]))
+    out["extrapolated"] = True
+    return out
 
 
 def cpu_oracle_sample(arrs, o, v, ntrip, seconds_cap=40.0):
@@ -288,11 +373,38 @@ def main():
     picks = sorted(set([nt - 1 - q * max(1, nt // (4 * nchk)) for q in range(nchk // 2)] +
                        [q * max(1, nt // nchk) for q in range(nchk - nchk // 2)]))
     d_sh = []
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    f64_sample_ms = 0.0
     for tt in picks:
         a = te.t_energy_triples(arrs, tt, tt + 1, prec, handle=h).item()
-        b = te.t_energy_triples(arrs, tt, tt + 1, "fp64", handle=h).item()
-        d_sh.append((tt, a, b))
+        s0.record(stream)
+        b = te.t_energy_triples(arrs, tt, tt + 1, "fp64", handle=h)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        f64_sample_ms += s0.elapsed_time(s1)
+        d_sh.append((tt, a, b.item()))
     max_d = max(abs(a - b) for _, a, b in d_sh)
+    # float64 rate on the sampled triples (every triple does the same contraction work)
+    f64_sampled = {"gflops": 12.0 * len(picks) * v ** 3 * (v + o) / (f64_sample_ms / 1e3) / 1e9,
+                   "triples": len(picks), "ms": f64_sample_ms}
+
+    # the plain float64 GPU path on the same cluster, once, after the timed
+    # region: its rate (the anchor of the mixed path's speed-up) and the
+    # whole-cluster |dE| that qualifies the headline metric
+    fp64 = None
+    if not args.no_fp64_anchor and prec != "fp64":
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        e64 = te.t_energy(arrs, "fp64", handle=h)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        h.sync()
+        fms = a0.elapsed_time(a1)
+        fp64 = {"ms": fms, "gflops": F / (fms / 1e3) / 1e9, "e_t_ha": float(e64),
+                "dE_total_vs_fp64_ha": abs(e_val - float(e64)), "speedup_vs_fp64": fms / per_step}
 
     # end to end through the public API with host (pinned) buffers
     e2e = None
@@ -358,6 +470,18 @@ def main():
                  "clusters_per_s": world * 16 / (bms / 1e3), "gflops": world * Fb / (bms / 1e3) / 1e9,
                  "ms_per_batch": bms, "graph": True}
         del bdev
+
+    # the 96-cluster uneven batch: a timed subset of seeds, extrapolated by flop count
+    b96 = None
+    if not args.no_batch96 and world == 1:
+        b96 = batch96_leg(te, h, prec, args.batch_stride, local)
+
+    # adjoint on a sample of triples of this cluster (when the whole-cluster
+    # adjoint is too long to run here: every triple does the same contraction
+    # work, so the whole-cluster time is extrapolated by triple count)
+    vjp_sample = None
+    if args.vjp_triples > 0:
+        vjp_sample = vjp_sample_leg(te, h, arrs, o, v, args.vjp_triples, world)
 
     # adjoint: gradient of E(T) for the nocc=16 nvir=120 cluster (seed 3), float64
     vjp = None
@@ -439,13 +563,17 @@ def main():
         gemm_avg_ms = prof["gemm_ms"] / max(1, prof["gemm_launches"])
         alg_per_launch = nprod * F * args.steps / max(1, prof["gemm_launches"])
         achieved = alg_per_launch / (gemm_avg_ms / 1e3) / 1e12
-        # DRAM bytes per launch: the ncu capture in profiles/k_gemm_tc_o8v320_ozaki.md
-        # measured 2.486 GB per triple at nvir = 320 (same tiles as this workload),
-        # scaled by the triples one launch processes; other shapes: not captured
+        # DRAM bytes per launch: an ncu capture of the same kernel at nocc=8
+        # nvir=320 (the same tiles and per-triple work) measured 2.486 GB per
+        # triple; scaled here by the triples one launch processes (not
+        # measured in this run; other shapes: not captured)
         tpl = te.num_unique_triples(o) * args.steps / max(1, prof["gemm_launches"])
-        traffic = 2.486e9 * tpl if (v == 320 and prec == "ozaki" and nprod == 10) else None
+        traffic = TRAFFIC_PER_TRIPLE * tpl if (v == 320 and prec == "ozaki" and nprod == 10) else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": (f"ncu dram bytes of k_gemm_tc at nocc=8 nvir=320, {TRAFFIC_PER_TRIPLE:.4g} "
+                                   f"per triple, scaled by {tpl:.3g} triples per launch; not measured in this run")
+                if traffic is not None else None,
                 "kernel": "k_gemm_tc", "peak_source": f"{pk_src} bf16 sustained"
                 + ("" if prec in ("bf16x3", "ozaki") else " x 1.1/2.25 (tf32)"),
                 "gemm_share_of_step": prof["gemm_ms"] / max(1e-9, ms),
@@ -469,9 +597,15 @@ def main():
                "e_t_ha": e_val,
                "dE_sampled_triples_max_ha": max_d,
                "dE_sampled": [{"triple": tt, "share": a, "share_fp64": b} for tt, a, b in d_sh],
+               "fp64_sampled_triples": f64_sampled,
+               "vjp_sample": vjp_sample,
                "gpu_launches": prof["launches"],
                "profile": prof,
+               "fp64_gpu": fp64,
+               "dE_total_vs_fp64_ha": fp64["dE_total_vs_fp64_ha"] if fp64 else None,
+               "speedup_vs_fp64": fp64["speedup_vs_fp64"] if fp64 else None,
                "batch16": batch,
+               "batch96": b96,
                "vjp": vjp,
                "frag": frag,
                "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}

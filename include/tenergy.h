@@ -26,12 +26,19 @@
  *     t2    [o][o][v][v] t2[i,j,a,b]   = t_ij^ab
  *   with o = nocc >= 1, v = nvir >= 1.  No symmetry of any array is assumed.
  * - The orbital energies must satisfy max(eps_o) < min(eps_v) (every D < 0);
- *   they need not be sorted.  Inputs must be finite.
+ *   they need not be sorted.  Every entry must be finite.
  * - Calls are asynchronous on the given CUDA stream (0 = legacy default
- *   stream).  Argument errors are reported before any launch (TE_EINVAL),
- *   workspace allocation failures as TE_ENOMEM, launch failures as TE_ECUDA.
- *   A device-side watchdog never traps: a kernel whose bounded wait expires
+ *   stream): none synchronises the stream or the device once its workspace
+ *   exists (te_reserve allocates it up front).  Errors in the descriptor
+ *   (null pointers, sizes, mode) are reported before any launch (TE_EINVAL);
+ *   the values are checked on the device by the call's first kernel (every
+ *   entry finite, max(eps_o) < min(eps_v)), and a violation is reported by
+ *   the next te_sync() as TE_EINVAL, naming the array or the ordering and
+ *   the cluster; the outputs of that call are then unspecified.  Workspace
+ *   allocation failures give TE_ENOMEM, launch failures TE_ECUDA.  A
+ *   device-side watchdog never traps: a kernel whose bounded wait expires
  *   records an error word and returns; te_sync() reports it as TE_ETIMEOUT.
+ *   The error word is the handle's: it stays set until te_sync reads it.
  * - Results are deterministic: fixed-order reductions, no floating-point
  *   atomics; repeated calls give bitwise identical outputs.
  * - A handle owns its workspace (operand copies for the mixed modes, partial
@@ -157,6 +164,28 @@ te_status t_energy_vjp(te_handle h, const te_cluster* c, te_precision p,
                        double gE, double* e_out, te_cluster_grad* g,
                        te_stream_t s);
 
+/* The adjoint restricted to the canonical triples [t_begin, t_end) (order as in
+ * t_energy_triples): g.X = gE * d/dX of the sum of those triples' shares, and
+ * e_out (nullable) receives that sum.  E(T) is additive over triples, so the
+ * adjoints of ranges that partition [0, ntriples) add up to t_energy_vjp's
+ * gradient: a caller can shard one cluster's gradient across GPUs, resume
+ * it, or time and check a sample of a large cluster.  Same modes, layouts
+ * and accuracy as t_energy_vjp; gradients are overwritten, not accumulated. */
+te_status t_energy_vjp_triples(te_handle h, const te_cluster* c, te_precision p,
+                               int64_t t_begin, int64_t t_end, double gE,
+                               double* e_out, te_cluster_grad* g, te_stream_t s);
+
+/* The adjoint of n independent clusters in one call (Eq. C_f: E = sum_x E_x,
+ * so dE/dX of cluster x is that cluster's own adjoint).  cs: HOST array of n
+ * descriptors; gE: HOST array of n upstream gradients (NULL: all 1);
+ * e_out: device array of n doubles (nullable); grads: HOST array of n
+ * gradient descriptors (device buffers, overwritten).  Every descriptor is
+ * checked before any launch; the handle's workspace is sized once for the
+ * largest member.  The clusters run one after another on s. */
+te_status t_energy_vjp_batched(te_handle h, const te_cluster* cs, int64_t n,
+                               te_precision p, const double* gE, double* e_out,
+                               te_cluster_grad* grads, te_stream_t s);
+
 /* Fragment-projected E(T) of one cluster: Eq. E_corr_CCSD_T with a general
  * C^f, i.e. the first occupied index of W~ projected,
  *   E_x = (1/3) sum_{ijk} sum_{abc} sum_{i'} cf[i][i'] W~_{i'jk}^{abc} R[Z]_{ijk}^{abc},
@@ -238,10 +267,12 @@ te_status te_profile_read(te_handle h, te_profile* out, int reset);
  * memory is touched.  The call allocates nothing: no cudaMalloc, cudaFree or
  * other allocating routine.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) once; make that first call before any stream
- * capture.  Like t_energy it reads eps_o/eps_v back to check max(eps_o) <
- * min(eps_v), which synchronises stream s.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so the address stays
+ * right after a device reset reloads the library image.  Unlike t_energy it
+ * reads eps_o/eps_v back to the host to check max(eps_o) < min(eps_v) (it
+ * has no handle whose error word could carry the result), which
+ * synchronises stream s.
  *
  * Every call shares the one array and it keeps the last call's contents;
  * each call writes every scratch byte before reading it.  Calls whose work
@@ -251,6 +282,14 @@ te_status te_profile_read(te_handle h, te_profile* out, int reset);
  * c: cluster (device float64 arrays as above); e_out: device pointer to one
  * double, overwritten with E(T); s: stream (0 = legacy default stream). */
 te_status t_energy_fp64_noalloc(const te_cluster* c, double* e_out, te_stream_t s);
+
+/* Most device bytes of workspace the handle may hold (0 = no limit, the
+ * default).  A call or te_reserve that would need more fails with TE_ENOMEM
+ * before any launch, as it would if the device had no room: a caller can
+ * give the library a memory budget (and test its handling of allocation
+ * failures).  TE_EINVAL if the handle already holds more than `bytes`.
+ * Not part of the paper. */
+te_status te_set_workspace_limit(te_handle h, size_t bytes);
 
 /* Message for the last non-OK status returned on the calling host thread. */
 const char* te_last_error(void);
@@ -269,6 +308,10 @@ te_status te_set_wait_limit_ns(te_handle h, uint64_t ns);
  * level-0 and level-1 products are exact in either width: K products of at
  * most 2^(2 bits) units stay below 2^24. */
 te_status te_set_ozaki_bits(te_handle h, int bits);
+
+/* Logging: with the environment variable TE_LOG set (and not "0") when a
+ * handle is created, the handle prints its tile plans, workspace sizes and
+ * autotune decisions to stderr. */
 
 /* Self-test of the device watchdog.  Launches on s one single-thread kernel
  * whose bounded wait is on a shared-memory mbarrier that nothing ever

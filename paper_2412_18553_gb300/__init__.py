@@ -9,7 +9,12 @@ Inputs (float64; CUDA tensors are used in place, host tensors or numpy arrays
 are copied to the device first):
   eps_o [o], eps_v [v], ovvv [o,v,v,v] = (ia|bd), ooov [o,o,o,v] = (jl|ia),
   ovov [o,v,o,v] = (ia|jb), t1 [o,v], t2 [o,o,v,v].
-Precision: "fp64", "tf32", "bf16x3", "tf32x3".
+Precision: "fp64", "ozaki" (exact BF16 slices on the tensor cores, the mode
+that meets 1e-7 Ha), "tf32", "bf16x3", "tf32x3".
+
+Calls are asynchronous: input values (finite entries, max eps_o < min eps_v)
+are checked on the device and a violation surfaces at the next
+``Handle.sync()`` (or ``sync()`` for the default handle) as TEnergyError.
 """
 from __future__ import annotations
 
@@ -24,6 +29,7 @@ from ._lib import PRECISIONS, TEnergyError, TeCluster, TeClusterGrad
 NAMES = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
 
 __all__ = ["Handle", "t_energy", "t_energy_triples", "t_energy_batched", "t_energy_vjp",
+           "t_energy_vjp_triples", "t_energy_vjp_batched", "sync",
            "t_energy_fp64_noalloc", "t_energy_frag",
            "TEnergy", "num_unique_triples", "flop_count", "TEnergyError", "NAMES"]
 
@@ -83,6 +89,11 @@ class Handle:
     def sync(self, stream=None):
         s = _stream(self.device, stream)
         _lib.check(_lib.load().te_sync(self.ptr, s))
+
+    def set_workspace_limit(self, nbytes: int):
+        """Most workspace bytes this handle may hold (0 = no limit); calls that
+        would need more raise TEnergyError (TE_ENOMEM) before any launch."""
+        _lib.check(_lib.load().te_set_workspace_limit(self.ptr, int(nbytes)))
 
     def set_wait_limit_ns(self, ns: int):
         _lib.check(_lib.load().te_set_wait_limit_ns(self.ptr, int(ns)))
@@ -249,6 +260,61 @@ def t_energy_vjp(cluster, gE=1.0, precision="fp64", handle=None, device=None, st
     _lib.check(_lib.load().t_energy_vjp(h.ptr, ctypes.byref(c), _prec(precision), float(gE),
                                         ctypes.c_void_p(e.data_ptr()), ctypes.byref(g),
                                         _stream(dev, stream)))
+    return e, grads
+
+
+def sync(device=None, stream=None):
+    """te_sync on the default handle of `device` (the handle the functions
+    below use when none is given): waits for its work on the stream and
+    raises TEnergyError for a failed device-side input check or watchdog."""
+    dev = torch.cuda.current_device() if device is None else device
+    _handle(None, dev).sync(stream)
+
+
+def _grad_struct(grads):
+    return TeClusterGrad(*(ctypes.c_void_p(grads[n].data_ptr()) for n in NAMES))
+
+
+def t_energy_vjp_triples(cluster, t_begin=0, t_end=None, gE=1.0, precision="fp64", handle=None, device=None,
+                         stream=None):
+    """(sum of the shares of triples [t_begin, t_end), grads): the adjoint
+    restricted to a canonical triple range; ranges that partition all
+    triples give gradients that add up to t_energy_vjp's."""
+    dev = _device_of(cluster, device)
+    h = _handle(handle, dev)
+    t = _tensors(cluster, dev)
+    if t_end is None:
+        t_end = num_unique_triples(t["eps_o"].shape[0])
+    grads = {n: torch.empty_like(t[n]) for n in NAMES}
+    g = _grad_struct(grads)
+    e = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
+    c = _struct(t)
+    _lib.check(_lib.load().t_energy_vjp_triples(h.ptr, ctypes.byref(c), _prec(precision), int(t_begin),
+                                                int(t_end), float(gE), ctypes.c_void_p(e.data_ptr()),
+                                                ctypes.byref(g), _stream(dev, stream)))
+    return e, grads
+
+
+def t_energy_vjp_batched(clusters, gE=None, precision="fp64", handle=None, device=None, stream=None):
+    """(E [n], list of gradient dicts): the adjoint of n independent clusters
+    in one library call; gE: n upstream gradients (default all 1)."""
+    clusters = list(clusters)
+    dev = _device_of(clusters[0], device) if clusters else (device or torch.cuda.current_device())
+    h = _handle(handle, dev)
+    ts = [_tensors(c, dev) for c in clusters]
+    n = len(ts)
+    arr = (TeCluster * max(1, n))(*[_struct(t) for t in ts])
+    grads = [{nm: torch.empty_like(t[nm]) for nm in NAMES} for t in ts]
+    garr = (TeClusterGrad * max(1, n))(*[_grad_struct(g) for g in grads])
+    gbuf = None
+    if gE is not None:
+        gl = [float(x) for x in gE]
+        if len(gl) != n:
+            raise ValueError(f"gE has {len(gl)} entries for {n} clusters")
+        gbuf = (ctypes.c_double * max(1, n))(*gl)
+    e = torch.empty((n,), dtype=torch.float64, device=torch.device("cuda", dev))
+    _lib.check(_lib.load().t_energy_vjp_batched(h.ptr, arr, n, _prec(precision), gbuf,
+                                                ctypes.c_void_p(e.data_ptr()), garr, _stream(dev, stream)))
     return e, grads
 
 

@@ -44,6 +44,11 @@ SIGNATURES = [
                                         c_void_p, c_void_p]),
     ("t_energy_vjp", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int, ctypes.c_double,
                                     c_void_p, ctypes.POINTER(TeClusterGrad), c_void_p]),
+    ("t_energy_vjp_triples", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int, c_int64, c_int64,
+                                            ctypes.c_double, c_void_p, ctypes.POINTER(TeClusterGrad), c_void_p]),
+    ("t_energy_vjp_batched", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), c_int64, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double), c_void_p,
+                                            ctypes.POINTER(TeClusterGrad), c_void_p]),
     ("t_energy_frag", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), c_void_p, ctypes.c_int,
                                      c_void_p, c_void_p, c_void_p]),
     ("te_sync", ctypes.c_int, [c_void_p, c_void_p]),
@@ -51,6 +56,7 @@ SIGNATURES = [
                                           ctypes.POINTER(ctypes.c_size_t)]),
     ("te_last_error", ctypes.c_char_p, []),
     ("te_set_wait_limit_ns", ctypes.c_int, [c_void_p, ctypes.c_uint64]),
+    ("te_set_workspace_limit", ctypes.c_int, [c_void_p, ctypes.c_size_t]),
     ("te_watchdog_selftest", ctypes.c_int, [c_void_p, ctypes.c_uint64, c_void_p]),
     ("te_set_ozaki_bits", ctypes.c_int, [c_void_p, ctypes.c_int]),
     ("te_profile_enable", ctypes.c_int, [c_void_p, ctypes.c_int]),

@@ -2,6 +2,7 @@
 // validation, handle workspace, and the launch sequence of each call.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <vector>
@@ -76,6 +77,9 @@ struct Carver {
 
 static te_status ensure_workspace(Handle* h, size_t bytes) {
   if (h->ws_bytes >= bytes) return TE_OK;
+  if (h->ws_limit && bytes > h->ws_limit)
+    return fail(TE_ENOMEM, "workspace of %zu bytes needed, above the handle's limit of %zu bytes", bytes,
+                h->ws_limit);
   if (h->capturing) return fail(TE_EUNSUPPORTED, "workspace growth inside a graph capture");
   drop_graphs(h);  // captured graphs hold the old workspace's addresses
   if (h->ws) {
@@ -84,7 +88,9 @@ static te_status ensure_workspace(Handle* h, size_t bytes) {
     h->ws = nullptr;
     h->ws_bytes = 0;
   }
-  const size_t want = bytes + bytes / 8;
+  size_t want = bytes + bytes / 8;
+  if (h->ws_limit) want = std::min(want, h->ws_limit);
+  if (h->log) std::fprintf(stderr, "[tenergy] workspace: %zu bytes (needed %zu)\n", want, bytes);
   if (cudaMalloc(&h->ws, want) != cudaSuccess) {
     cudaGetLastError();
     h->ws = nullptr;
@@ -146,41 +152,16 @@ static te_status host_check(const Handle* h, const te_cluster* c, te_precision p
   return TE_OK;
 }
 
-// Every denominator must be negative: max eps_o < min eps_v.  Reads all
-// clusters' orbital energies back with one synchronisation of s.
-static te_status check_eps(const te_cluster* cs, int64_t n, cudaStream_t s) {
-  std::vector<std::vector<double>> eo(n), ev(n);
-  for (int64_t x = 0; x < n; ++x) {
-    eo[x].resize(cs[x].nocc);
-    ev[x].resize(cs[x].nvir);
-    if (cudaMemcpyAsync(eo[x].data(), cs[x].eps_o, cs[x].nocc * sizeof(double), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(ev[x].data(), cs[x].eps_v, cs[x].nvir * sizeof(double), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess)
-      return fail(TE_ECUDA, "reading orbital energies failed: %s", cudaGetErrorString(cudaGetLastError()));
-  }
-  if (cudaStreamSynchronize(s) != cudaSuccess)
-    return fail(TE_ECUDA, "reading orbital energies failed: %s", cudaGetErrorString(cudaGetLastError()));
-  for (int64_t x = 0; x < n; ++x) {
-    double mo = -1e300, mv = 1e300;
-    for (double e : eo[x]) {
-      if (!(e == e) || e > 1e300 || e < -1e300) return fail(TE_EINVAL, "non-finite eps_o (cluster %lld)", (long long)x);
-      mo = std::max(mo, e);
-    }
-    for (double e : ev[x]) {
-      if (!(e == e) || e > 1e300 || e < -1e300) return fail(TE_EINVAL, "non-finite eps_v (cluster %lld)", (long long)x);
-      mv = std::min(mv, e);
-    }
-    if (!(mo < mv))
-      return fail(TE_EINVAL, "cluster %lld: max(eps_o) = %g must be below min(eps_v) = %g", (long long)x, mo, mv);
-  }
-  return TE_OK;
-}
-
-static te_status validate(const Handle* h, const te_cluster* c, te_precision p, cudaStream_t s) {
+// Host checks (descriptor, sizes, pointers), then the device-side value
+// checks (finite entries, max eps_o < min eps_v) launched on s: no host
+// synchronisation, the result is reported by te_sync.
+static te_status validate(Handle* h, const te_cluster* c, te_precision p, cudaStream_t s, int64_t cluster = 0) {
   te_status st = host_check(h, c, p);
   if (st != TE_OK) return st;
-  return check_eps(c, 1, s);
+  const cudaError_t e = launch_check_inputs(c, cluster, h->d_err, h->num_sms, s);
+  ++h->n_launches;
+  if (e != cudaSuccess) return fail(TE_ECUDA, "input check launch: %s", cudaGetErrorString(e));
+  return TE_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -371,6 +352,8 @@ te_status te_create(te_handle* out, int device, const char* autotune_cache_path)
     delete h;
     return fail(TE_ENOMEM, "error-word allocation failed");
   }
+  const char* lg = std::getenv("TE_LOG");
+  h->log = lg && *lg && std::strcmp(lg, "0") != 0;
   if (autotune_cache_path && *autotune_cache_path) {
     h->tune_path = autotune_cache_path;
     tune_load(h);
@@ -450,15 +433,13 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
   for (auto& ge : h->graphs) {
     if (ge.precision != (int)p || ge.e_out != e_out || (int64_t)ge.clusters.size() != n) continue;
     if (std::memcmp(ge.clusters.data(), cs, sizeof(te_cluster) * n) != 0) continue;
-    te_status st = check_eps(cs, n, s);
-    if (st != TE_OK) return st;
+    // the graph begins with every member's input check
     if (cudaGraphLaunch(ge.exec, s) != cudaSuccess)
       return fail(TE_ECUDA, "graph launch: %s", cudaGetErrorString(cudaGetLastError()));
     h->n_launches += ge.launches;
     return TE_OK;
   }
-  te_status st = check_eps(cs, n, s);
-  if (st != TE_OK) return st;
+  te_status st = TE_OK;
   // one workspace and one triple table for the whole batch
   size_t maxb = 0;
   int64_t maxo = 1;
@@ -489,6 +470,8 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
   const int64_t l0 = h->n_launches;
   for (int64_t x = 0; x < n && st == TE_OK; ++x) {
     const int64_t nt = num_unique_triples(cs[x].nocc);
+    st = validate(h, cs + x, p, h->cap_stream, x);
+    if (st != TE_OK) break;
     if (nt == 0) {
       if (cudaMemsetAsync(e_out + x, 0, sizeof(double), h->cap_stream) != cudaSuccess)
         st = fail(TE_ECUDA, "memset failed");
@@ -525,22 +508,82 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
   return TE_OK;
 }
 
+// The adjoint over the canonical triples [t_begin, t_end) of one cluster.
+static te_status vjp_range(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin, int64_t t_end,
+                           double gE, double* e_out, te_cluster_grad* gr, cudaStream_t s, int64_t cluster) {
+  if (!gr) return fail(TE_EINVAL, "null gradient descriptor");
+  if (!(gE == gE) || gE > 1e300 || gE < -1e300) return fail(TE_EINVAL, "non-finite gE");
+  if (h->capturing) return fail(TE_EINVAL, "the adjoint cannot run inside the library's graph capture");
+  te_status st = validate(h, c, p, s, cluster);
+  if (st != TE_OK) return st;
+  const int64_t nt = num_unique_triples(c->nocc);
+  if (t_begin < 0 || t_end > nt || t_begin > t_end)
+    return fail(TE_EINVAL, "triple range [%lld,%lld) outside [0,%lld)", (long long)t_begin, (long long)t_end,
+                (long long)nt);
+  // float64: DFMA contractions; the tensor-core modes: exact-slice contractions
+  if (p == TE_FP64) return run_vjp_fp64(h, c, t_begin, t_end, gE, e_out, gr, s);
+  if (h->cc_major != 10 && h->cc_major != 11)
+    return fail(TE_EUNSUPPORTED, "the tensor-core adjoint needs an sm_100-family GPU");
+  return run_vjp_tc(h, c, t_begin, t_end, gE, e_out, gr, s);
+}
+
 te_status t_energy_vjp(te_handle hh, const te_cluster* c, te_precision p, double gE, double* e_out,
                        te_cluster_grad* gr, te_stream_t ss) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
   if (!h) return fail(TE_EINVAL, "null handle");
-  if (!gr) return fail(TE_EINVAL, "null gradient descriptor");
-  if (!(gE == gE) || gE > 1e300 || gE < -1e300) return fail(TE_EINVAL, "non-finite gE");
-  if (h->capturing) return fail(TE_EINVAL, "t_energy_vjp cannot run inside a graph capture");
+  if (!c) return fail(TE_EINVAL, "null cluster descriptor");
   DeviceGuard g(h->device);
-  te_status st = validate(h, c, p, s);
-  if (st != TE_OK) return st;
-  // float64: DFMA contractions; the tensor-core modes: exact-slice contractions
-  if (p == TE_FP64) return run_vjp_fp64(h, c, gE, e_out, gr, s);
-  if (h->cc_major != 10 && h->cc_major != 11)
-    return fail(TE_EUNSUPPORTED, "the tensor-core adjoint needs an sm_100-family GPU");
-  return run_vjp_tc(h, c, gE, e_out, gr, s);
+  const int64_t nt = c->nocc >= 1 ? num_unique_triples(c->nocc) : 0;
+  return vjp_range(h, c, p, 0, nt, gE, e_out, gr, reinterpret_cast<cudaStream_t>(ss), 0);
+}
+
+te_status t_energy_vjp_triples(te_handle hh, const te_cluster* c, te_precision p, int64_t t_begin,
+                               int64_t t_end, double gE, double* e_out, te_cluster_grad* gr, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  DeviceGuard g(h->device);
+  return vjp_range(h, c, p, t_begin, t_end, gE, e_out, gr, reinterpret_cast<cudaStream_t>(ss), 0);
+}
+
+te_status t_energy_vjp_batched(te_handle hh, const te_cluster* cs, int64_t n, te_precision p, const double* gE,
+                               double* e_out, te_cluster_grad* grads, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (n < 0) return fail(TE_EINVAL, "negative batch size");
+  if (n == 0) return TE_OK;
+  if (!cs || !grads) return fail(TE_EINVAL, "null cluster or gradient array");
+  DeviceGuard g(h->device);
+  for (int64_t x = 0; x < n; ++x) {  // every descriptor before any launch
+    te_status st = host_check(h, cs + x, p);
+    if (st == TE_OK && gE && !(gE[x] == gE[x] && gE[x] < 1e300 && gE[x] > -1e300))
+      st = fail(TE_EINVAL, "non-finite gE");
+    if (st != TE_OK) {
+      char msg[600];
+      snprintf(msg, sizeof(msg), "cluster %lld: %.511s", (long long)x, te_last_error());
+      return fail(st, "%s", msg);
+    }
+  }
+  // the workspace of the largest member, once
+  size_t need = 0;
+  int64_t maxo = 1;
+  for (int64_t x = 0; x < n; ++x) {
+    need = std::max(need, p == TE_FP64 ? vjp_fp64_bytes(cs[x].nocc, cs[x].nvir)
+                                       : vjp_tc_bytes(cs[x].nocc, cs[x].nvir, h->num_sms));
+    maxo = std::max<int64_t>(maxo, cs[x].nocc);
+  }
+  te_status st = ensure_workspace(h, need);
+  if (st == TE_OK) st = ensure_triples(h, (int)maxo);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  for (int64_t x = 0; x < n && st == TE_OK; ++x) {
+    const int64_t nt = num_unique_triples(cs[x].nocc);
+    st = vjp_range(h, cs + x, p, 0, nt, gE ? gE[x] : 1.0, e_out ? e_out + x : nullptr, grads + x, s, x);
+    if (st != TE_OK) {
+      char msg[600];
+      snprintf(msg, sizeof(msg), "cluster %lld: %.511s", (long long)x, te_last_error());
+      return fail(st, "%s", msg);
+    }
+  }
+  return st;
 }
 
 te_status t_energy_frag(te_handle hh, const te_cluster* c, const double* cf, te_precision p, double* e_out,
@@ -575,6 +618,13 @@ te_status te_sync(te_handle hh, te_stream_t ss) {
     cudaMemset(h->d_err, 0, sizeof(err));
     if (err[0] & ERR_WAIT_TIMEOUT)
       return fail(TE_ETIMEOUT, "device wait expired (code %u, site %u, block %u)", err[0], err[1], err[2]);
+    if (err[0] & ERR_BAD_INPUT) {
+      static const char* what[9] = {"?", "eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2", ""};
+      if (err[1] == 8)
+        return fail(TE_EINVAL, "input check failed (cluster %u): max(eps_o) must be below min(eps_v)", err[2]);
+      return fail(TE_EINVAL, "input check failed (cluster %u): non-finite value in %s", err[2],
+                  what[err[1] < 8 ? err[1] : 0]);
+    }
     return fail(TE_ECUDA, "device check failed (code %u, site %u, block %u)", err[0], err[1], err[2]);
   }
   return TE_OK;
@@ -664,6 +714,15 @@ te_status te_set_ozaki_bits(te_handle hh, int bits) {
     drop_graphs(h);  // captured batches bake in the slice width
     h->ozaki_bits = bits;
   }
+  return TE_OK;
+}
+
+te_status te_set_workspace_limit(te_handle hh, size_t bytes) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (bytes && h->ws_bytes > bytes)
+    return fail(TE_EINVAL, "the handle already holds %zu bytes of workspace, above %zu", h->ws_bytes, bytes);
+  h->ws_limit = bytes;
   return TE_OK;
 }
 

@@ -1,8 +1,6 @@
 // Float64 E(T) without any device allocation: every scratch byte of the
 // float64 path (prepared operand copies, G blocks, partial sums, triple table)
 // is carved from one fixed-size array that the library image carries.
-#include <mutex>
-
 #include "te_internal.h"
 
 namespace te {
@@ -12,11 +10,9 @@ namespace te {
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;  // 64 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-// Device address of the array, looked up once per device.  In host code the
-// array's name is only a host-side stand-in, never a usable device pointer.
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static std::mutex g_noalloc_mutex;
-static void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+// In host code the array's name is only a host-side stand-in, never a usable
+// device pointer: each call asks the runtime for its address on the current
+// device (no caching, so a device reset that reloads the image is harmless).
 
 // Canonical unique triples (lexicographic i >= j >= k, i = j = k left out):
 // thread i writes the C(i+2,2) - 1 triples whose first index is i, starting
@@ -68,22 +64,13 @@ extern "C" te_status t_energy_fp64_noalloc(const te_cluster* c, double* e_out, t
   if (!c->eps_o || !c->eps_v || !c->ovvv || !c->ooov || !c->ovov || !c->t1 || !c->t2)
     return fail(TE_EINVAL, "null array pointer in cluster descriptor");
 
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return fail(TE_ECUDA, "no current CUDA device");
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(TE_EUNSUPPORTED, "device ordinal %d out of range", dev);
   void* base = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        return fail(TE_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
-      }
-      g_noalloc_addr[dev] = p;
+    const cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+    if (e != cudaSuccess || !base) {
+      cudaGetLastError();
+      return fail(TE_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
     }
-    base = g_noalloc_addr[dev];
   }
 
   // every denominator must be negative: max eps_o < min eps_v

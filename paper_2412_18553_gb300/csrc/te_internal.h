@@ -19,7 +19,14 @@ namespace te {
 enum : unsigned int {
   ERR_WAIT_TIMEOUT = 1u,   // a bounded mbarrier/flag wait expired
   ERR_BAD_TILE = 2u,       // a tile coordinate check failed (skipped access)
+  ERR_BAD_INPUT = 4u,      // an input value check failed (non-finite, eps ordering)
 };
+
+// Device-side input value checks of one cluster (checks.cu): every entry
+// finite and max(eps_o) < min(eps_v); a violation sets ERR_BAD_INPUT with the
+// site (1..7 the array, 8 the eps ordering) and `cluster` in the error word.
+cudaError_t launch_check_inputs(const te_cluster* c, int64_t cluster, unsigned int* err, int num_sms,
+                                cudaStream_t s);
 
 // One occupied triple of the canonical unique list.
 struct Triple {
@@ -54,6 +61,8 @@ struct Handle {
   // workspace (grows, never shrinks until destroy)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  size_t ws_limit = 0;  // most workspace bytes the handle may hold (0: no limit)
+  bool log = false;     // TE_LOG=1: tile plans and autotune decisions on stderr
   // triple table cache
   Triple* d_triples = nullptr;
   int triples_nocc = -1;
@@ -123,8 +132,9 @@ cudaError_t launch_reduce_total(const double* e_triples, int64_t n, double* e_ou
                                 cudaStream_t s);
 
 // adjoint of E(T) in float64 (vjp.cu)
-te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
-                       cudaStream_t s);
+// over the canonical triples [t_begin, t_end): the gradient of the sum of their shares
+te_status run_vjp_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_end, double gE,
+                       double* e_out, te_cluster_grad* g, cudaStream_t s);
 // fragment-projected E(T) (vjp.cu): cf device [nocc][nocc]; precision TE_FP64 or
 // exact slices; per-triple shares to e_triples (nullable), total to e_out (nullable)
 size_t frag_bytes(int64_t o, int64_t v, te_precision p, int num_sms);
@@ -134,8 +144,8 @@ te_status run_frag(Handle* h, const te_cluster* c, const double* cf, te_precisio
 size_t vjp_fp64_bytes(int64_t o, int64_t v);
 size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms);
 // the same with the contractions on the tensor cores in exact BF16 slices (vjp.cu)
-te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
-                     cudaStream_t s);
+te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_end, double gE,
+                     double* e_out, te_cluster_grad* g, cudaStream_t s);
 
 constexpr int ENERGY_TB = 8;  // virtual block edge of the energy kernel
 inline int64_t energy_num_blocks(int64_t v) { return (v + ENERGY_TB - 1) / ENERGY_TB; }

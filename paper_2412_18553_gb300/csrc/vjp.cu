@@ -748,8 +748,8 @@ size_t vjp_fp64_bytes(int64_t o, int64_t v) {
 te_status ensure_workspace_public(Handle* h, size_t bytes);
 te_status ensure_triples_public(Handle* h, int nocc);
 
-te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
-                       cudaStream_t s) {
+te_status run_vjp_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_end, double gE,
+                       double* e_out, te_cluster_grad* g, cudaStream_t s) {
   const int o = (int)c->nocc, v = (int)c->nvir;
   const int64_t v2 = (int64_t)v * v, v3 = v2 * v, nt = num_unique_triples(o);
   te_status st = ensure_workspace_public(h, vjp_fp64_bytes(o, v));
@@ -807,7 +807,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
   if (e != cudaSuccess) return fail(TE_ECUDA, "prep: %s", cudaGetErrorString(e));
 
   std::vector<Triple> trip = unique_triples(o);
-  for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
+  for (int64_t t = t_begin; t < t_end && e == cudaSuccess; ++t) {
     const Triple T = trip[t];
     e = launch_gemm_fp64(&P, h->d_triples, t, 1, W.G, s);
     if (e != cudaSuccess) break;
@@ -882,7 +882,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, double gE, double* e_out,
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && e_out) {
-    e = launch_reduce_total(W.shares, nt, e_out, s);
+    e = launch_reduce_total(W.shares + t_begin, t_end - t_begin, e_out, s);
     ++h->n_launches;
   }
   if (e != cudaSuccess) return fail(TE_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
@@ -911,8 +911,8 @@ size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms) {
          a(std::max<int64_t>(1, nt)) + a(oz_scratch_cap(o, v, num_sms)) + a(4) + 1024;
 }
 
-te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, te_cluster_grad* g,
-                     cudaStream_t s) {
+te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_end, double gE,
+                     double* e_out, te_cluster_grad* g, cudaStream_t s) {
   const int o = (int)c->nocc, v = (int)c->nvir;
   const int64_t v2 = (int64_t)v * v, v3 = v2 * v, nt = num_unique_triples(o);
   te_status st = ensure_workspace_public(h, vjp_tc_bytes(o, v, h->num_sms));
@@ -1005,7 +1005,7 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
   };
   auto runI = [&](const OzView& gv, int gi) { run(gi == 2 ? swapM(gv) : gv); };   // rows (x, y) of Gamma
   auto runII = [&](const OzView& gv, int gi) { run(gi == 2 ? swapK(gv) : gv); };  // k = (x, y) of Gamma
-  for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
+  for (int64_t t = t_begin; t < t_end && e == cudaSuccess; ++t) {
     const Triple T = trip[t];
     // forward G blocks, natural [g][x][y][z], four K segments each
     for (int gi = 0; gi < 3; ++gi) {
@@ -1097,7 +1097,7 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, double gE, double* e_out, t
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && e_out) {
-    e = launch_reduce_total(W.shares, nt, e_out, s);
+    e = launch_reduce_total(W.shares + t_begin, t_end - t_begin, e_out, s);
     ++h->n_launches;
   }
   if (e != cudaSuccess) return fail(TE_ECUDA, "vjp launch: %s", cudaGetErrorString(e));

@@ -117,10 +117,11 @@ def _ovvv_cuda(Bov, Bvv):
 
 
 def make_cluster(nocc: int, nvir: int, naux: int, seed: int, device: str = "cpu",
-                 rng=None) -> Cluster:
-    """Draw one synthetic cluster.  ``device="cuda"`` forms large ovvv on the GPU
-    (returned as a CUDA float64 tensor); small clusters are always formed on the
-    host in FP64 and returned as numpy arrays."""
+                 rng=None, host_flop_limit: float = HOST_FLOP_LIMIT) -> Cluster:
+    """Draw one synthetic cluster.  ``device="cuda"`` forms ovvv on the GPU
+    (returned as a CUDA float64 tensor) when it costs more than
+    ``host_flop_limit`` flops; smaller ones are formed on the host in FP64 and
+    returned as numpy arrays."""
     if rng is None:
         rng = np.random.default_rng(seed)
     eps_o, eps_v, B, t1 = _draw(nocc, nvir, naux, rng)
@@ -134,7 +135,7 @@ def make_cluster(nocc: int, nvir: int, naux: int, seed: int, device: str = "cpu"
           - eps_v[None, None, :, None] - eps_v[None, None, None, :])
     t2 = ovov.transpose(0, 2, 1, 3) / d2
     flops = 2.0 * o * v ** 3 * naux
-    if device == "cuda" and flops > HOST_FLOP_LIMIT:
+    if device == "cuda" and flops > host_flop_limit:
         ovvv = _ovvv_cuda(Bov, Bvv)
         how = "gpu-split-bf16x3"
     else:
@@ -172,11 +173,11 @@ def batch_sizes(seed: int, rule: str = "uneven"):
     return o, v, 4 * (o + v), rng
 
 
-def make_batch(seeds, rule="uneven", device="cpu"):
+def make_batch(seeds, rule="uneven", device="cpu", host_flop_limit=HOST_FLOP_LIMIT):
     out = []
     for s in seeds:
         o, v, naux, rng = batch_sizes(s, rule)
-        out.append(make_cluster(o, v, naux, s, device=device, rng=rng))
+        out.append(make_cluster(o, v, naux, s, device=device, rng=rng, host_flop_limit=host_flop_limit))
     return out
 
 
@@ -186,6 +187,8 @@ WORKLOADS = {
     "o32v320": (32, 320, 1280, 1),
     "o16v120": (16, 120, 544, 3),
     "o48v560": (48, 560, 2432, 7),
+    # between the two: whole-cluster comparison of the exact-slice and float64 paths
+    "o24v240": (24, 240, 960, 2),
     # same virtual space as o32v320 with 8 occupied orbitals: kernel profiling
     # at full tile shapes with a few GB on the device
     "o8v320": (8, 320, 1280, 1),

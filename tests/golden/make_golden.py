@@ -5,7 +5,8 @@ single-cluster workload it stores E(T) and the per-triple shares in canonical
 triple order, plus checksums of the generated inputs so a test can detect a
 generator that drew different numbers.
 
-    python tests/golden/make_golden.py o8v40 o16v120 o32v320:sample o16v120:frag
+    python tests/golden/make_golden.py o8v40 o16v120 o32v320:sample o16v120:frag \
+        o16v120:grad v8o:grad
 """
 import json
 import os
@@ -73,11 +74,59 @@ def main_frag(name):
         json.dump(out, f)
 
 
+# Gradient samples (the adjoint's parity at the gradient workload): the
+# oracle's reverse-mode gradient over every unique triple, at 64 seeded entries
+# of each input (all entries when fewer) plus each tensor's largest entry,
+# with each tensor's largest magnitude (the scale of the relative bar).
+GRAD_SAMPLE = 64
+GRAD_BATCH_MEMBERS = {"v8o": [11, 14]}  # the smallest members of the 16-cluster v = 8 nocc batch
+
+
+def grad_record(cl, label, rng_seed):
+    c = O.inputs(**cl.arrays())
+    t = time.time()
+    e, g = O.t_energy_grad(c)
+    rng = np.random.default_rng(rng_seed)
+    ent = {}
+    for n in O.NAMES:
+        a = g[n].numpy().ravel()
+        k = min(GRAD_SAMPLE, a.size)
+        idx = set(int(i) for i in rng.choice(a.size, k, replace=False))
+        idx.add(int(np.argmax(np.abs(a))))
+        idx = sorted(idx)
+        ent[n] = dict(index=idx, value=[float(a[i]) for i in idx], max_abs=float(np.max(np.abs(a))),
+                      shape=list(g[n].shape))
+    print(label, "E", e, f"{time.time() - t:.1f}s", flush=True)
+    return dict(e_t=float(e), grad=ent, checksums=checksums(cl), oracle_seconds=time.time() - t)
+
+
+def main_grad(name):
+    if name in GRAD_BATCH_MEMBERS:
+        members = []
+        for s in GRAD_BATCH_MEMBERS[name]:
+            o, v, naux, rng = tegen.batch_sizes(s, name)
+            cl = tegen.make_cluster(o, v, naux, s, rng=rng)
+            rec = grad_record(cl, f"{name} seed {s}", 1000 + s)
+            rec.update(seed=s, nocc=o, nvir=v, naux=naux)
+            members.append(rec)
+        out = dict(batch=name, members=members)
+    else:
+        o, v, naux, seed = tegen.WORKLOADS[name]
+        cl = tegen.make_cluster(o, v, naux, seed)
+        out = grad_record(cl, name, 1000 + seed)
+        out.update(workload=name, nocc=o, nvir=v, naux=naux, seed=seed)
+    with open(os.path.join(HERE, f"oracle_{name}_grad.json"), "w") as f:
+        json.dump(out, f)
+
+
 def main(names):
     torch.set_num_threads(os.cpu_count() or 1)
     for name in names:
         if name.endswith(":sample"):
             main_sample(name.split(":")[0])
+            continue
+        if name.endswith(":grad"):
+            main_grad(name.split(":")[0])
             continue
         if name.endswith(":frag"):
             main_frag(name.split(":")[0])

@@ -71,8 +71,10 @@ def test_invalid_orbital_energies_rejected(te):
     a = cl.arrays()
     a["eps_o"] = a["eps_o"].copy()
     a["eps_o"][1] = a["eps_v"].min() + 0.1
+    h = te.Handle(0)
+    te.t_energy(a, "fp64", handle=h)  # checked on the device: reported at sync
     with pytest.raises(te.TEnergyError) as ei:
-        te.t_energy(a, "fp64")
+        h.sync()
     assert ei.value.status == 1
 
 

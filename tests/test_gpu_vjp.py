@@ -135,3 +135,29 @@ def test_autograd_function_uses_the_adjoint(te, prec):
     _, g = te.t_energy_vjp(a, gE=2.0, precision=prec)
     for n, leaf in zip(NAMES, leaves):
         torch.testing.assert_close(leaf.grad, g[n], rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_triple_ranges_partition_the_gradient(te, prec):
+    """E is additive over triples: the adjoints of ranges that partition the
+    canonical triples add up to the whole cluster's adjoint, and their
+    energies to E (t_energy_vjp_triples)."""
+    cl = tegen.make_cluster(6, 29, 140, 13)
+    a = dev(shuffled(cl.arrays(), 13))
+    nt = te.num_unique_triples(6)
+    e, g = te.t_energy_vjp(a, gE=0.5, precision=prec)
+    cuts = [0, 1, 17, nt - 3, nt]
+    tot = {n: torch.zeros_like(g[n]) for n in NAMES}
+    esum = 0.0
+    for b, c in zip(cuts[:-1], cuts[1:]):
+        eb, gb = te.t_energy_vjp_triples(a, b, c, gE=0.5, precision=prec)
+        esum += float(eb)
+        for n in NAMES:
+            tot[n] += gb[n]
+    assert abs(esum - float(e)) <= 1e-13 * abs(float(e))
+    assert_grads_close(tot, {n: g[n].cpu().numpy() for n in NAMES}, 1e-12)
+    # an empty range: zero gradient, zero energy
+    e0, g0 = te.t_energy_vjp_triples(a, 5, 5, precision=prec)
+    assert float(e0) == 0.0 and all(float(g0[n].abs().max()) == 0.0 for n in NAMES)
+    with pytest.raises(te.TEnergyError):
+        te.t_energy_vjp_triples(a, 3, nt + 1, precision=prec)
