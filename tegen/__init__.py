@@ -41,6 +41,8 @@ __all__ = [
     "make_cluster",
     "batch_sizes",
     "make_batch",
+    "mp2_inputs",
+    "mp2_batch",
     "WORKLOADS",
     "eri_full",
 ]
@@ -144,6 +146,25 @@ def make_cluster(nocc: int, nvir: int, naux: int, seed: int, device: str = "cpu"
     return Cluster(o, v, eps_o, eps_v, ovvv, ooov, ovov, t1,
                    np.ascontiguousarray(t2),
                    meta=dict(naux=naux, seed=seed, ovvv_formed=how))
+
+
+def mp2_inputs(nocc: int, nvir: int, naux: int, seed: int, rng=None):
+    """The MP2 step's inputs for the same draw as ``make_cluster``: (eps_o,
+    eps_v, Bov) with Bov[P, i, a] the occupied-virtual block of the
+    density-fitting factor, C-contiguous float64."""
+    if rng is None:
+        rng = np.random.default_rng(seed)
+    eps_o, eps_v, B, _ = _draw(nocc, nvir, naux, rng)
+    return eps_o, eps_v, np.ascontiguousarray(B[:, :nocc, nocc:])
+
+
+def mp2_batch(seeds, rule="v8o"):
+    """MP2 inputs of batch members (sizes as in ``make_batch``)."""
+    out = []
+    for s in seeds:
+        o, v, naux, rng = batch_sizes(s, rule)
+        out.append(mp2_inputs(o, v, naux, s, rng=rng))
+    return out
 
 
 def eri_full(nocc: int, nvir: int, naux: int, seed: int) -> np.ndarray:
