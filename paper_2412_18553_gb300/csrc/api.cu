@@ -440,18 +440,8 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
     return TE_OK;
   }
   te_status st = TE_OK;
-  // one workspace and one triple table for the whole batch
-  size_t maxb = 0;
   int64_t maxo = 1;
-  for (int64_t x = 0; x < n; ++x) {
-    size_t b = 0;
-    st = te_workspace_bytes(hh, cs + x, p, &b);
-    if (st != TE_OK) return st;
-    maxb = std::max(maxb, b);
-    maxo = std::max<int64_t>(maxo, cs[x].nocc);
-  }
-  st = ensure_workspace(h, maxb);
-  if (st != TE_OK) return st;
+  for (int64_t x = 0; x < n; ++x) maxo = std::max<int64_t>(maxo, cs[x].nocc);
   st = ensure_triples(h, (int)maxo);
   if (st != TE_OK) return st;
   if (p != TE_FP64) {  // tile shapes tuned per (nocc, nvir) before the capture
@@ -460,6 +450,22 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
       if (st != TE_OK) return st;
     }
   }
+  // one workspace for the whole batch: float64 runs the members one after
+  // another; the tensor-core modes hold every member's operands and one G pool
+  size_t need = 0;
+  if (p == TE_FP64) {
+    for (int64_t x = 0; x < n; ++x) {
+      size_t b = 0;
+      st = te_workspace_bytes(hh, cs + x, p, &b);
+      if (st != TE_OK) return st;
+      need = std::max(need, b);
+    }
+  } else {
+    st = tc_batched_bytes(h, cs, n, p, &need);
+    if (st != TE_OK) return st;
+  }
+  st = ensure_workspace(h, need);
+  if (st != TE_OK) return st;
   // capture the batch's launches into one CUDA graph on an internal stream
   if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(TE_ECUDA, "stream creation failed");
@@ -468,10 +474,10 @@ te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_pre
     return fail(TE_ECUDA, "begin capture: %s", cudaGetErrorString(cudaGetLastError()));
   h->capturing = true;
   const int64_t l0 = h->n_launches;
-  for (int64_t x = 0; x < n && st == TE_OK; ++x) {
+  for (int64_t x = 0; x < n && st == TE_OK; ++x) st = validate(h, cs + x, p, h->cap_stream, x);
+  if (st == TE_OK && p != TE_FP64) st = run_tc_batched(h, cs, n, p, e_out, h->cap_stream);
+  for (int64_t x = 0; x < n && st == TE_OK && p == TE_FP64; ++x) {
     const int64_t nt = num_unique_triples(cs[x].nocc);
-    st = validate(h, cs + x, p, h->cap_stream, x);
-    if (st != TE_OK) break;
     if (nt == 0) {
       if (cudaMemsetAsync(e_out + x, 0, sizeof(double), h->cap_stream) != cudaSuccess)
         st = fail(TE_ECUDA, "memset failed");
@@ -619,11 +625,11 @@ te_status te_sync(te_handle hh, te_stream_t ss) {
     if (err[0] & ERR_WAIT_TIMEOUT)
       return fail(TE_ETIMEOUT, "device wait expired (code %u, site %u, block %u)", err[0], err[1], err[2]);
     if (err[0] & ERR_BAD_INPUT) {
-      static const char* what[9] = {"?", "eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2", ""};
+      static const char* what[10] = {"?", "eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2", "", "Bov"};
       if (err[1] == 8)
         return fail(TE_EINVAL, "input check failed (cluster %u): max(eps_o) must be below min(eps_v)", err[2]);
       return fail(TE_EINVAL, "input check failed (cluster %u): non-finite value in %s", err[2],
-                  what[err[1] < 8 ? err[1] : 0]);
+                  what[(err[1] < 10 && err[1] != 8) ? err[1] : 0]);
     }
     return fail(TE_ECUDA, "device check failed (code %u, site %u, block %u)", err[0], err[1], err[2]);
   }

@@ -19,6 +19,8 @@
 //   T = 3 sum_n w_n v_n + Ae Se + Ao So - 2 (Ae So + Ao Se)
 // D, its reciprocal (FP32 seed + one Newton step in FP64: error ~1e-14),
 // A T / D and the sums are FP64.
+#include <cstring>
+
 #include "energy_tc.h"
 #include "ptx_sm100.cuh"
 
@@ -169,24 +171,36 @@ __device__ __forceinline__ float y_at(const float* ovsS, const float* t1S, int l
 }
 
 struct EnergyMaps {
-  CUtensorMap ovs;  // ovs32 [o][v][o][vq], 4D (b, j, a, i)
-  CUtensorMap t1;   // t1 [o][vq], 2D (a, i)
+  CUtensorMap ovs[TC_MAX_CL];  // per cluster: ovs32 [o][v][o][vq], 4D (b, j, a, i)
+  CUtensorMap t1[TC_MAX_CL];   // per cluster: t1 [o][vq], 2D (a, i)
 };
 
 struct EnergyParams {
-  int o, v, nslots, nb;
-  int64_t nbt, items, t0;
-  const float* gbuf;  // orbit-major G: [slot][bt][g][pid][CW planes][512, swizzled]
+  int ncl, npieces;
+  int64_t items;
+  EnergyCl cl[TC_MAX_CL];
+  TcPiece pc[TC_MAX_PIECES];  // G: orbit-major [slot][bt][g][pid][CW planes][512, swizzled] from pc.gbuf
   const Triple* triples;
-  const double* eps_o;
-  const double* eps_v;
-  double* partials;  // [slot][grid][WARPS]
+  double* partials;  // [item]
   unsigned int* err;
   unsigned long long wait_ns;
 };
 
+struct PieceTable {
+  int n;
+  TcPiece pc[TC_MAX_PIECES];
+};
+
+// The piece holding launch item `it` (pieces are in item order).
+__device__ __forceinline__ int piece_of_item(const EnergyParams& P, int64_t it) {
+  int q = 0;
+  while (q + 1 < P.npieces && P.pc[q + 1].item0 <= it) ++q;
+  return q;
+}
+
 template <int CW>
-__global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant__ EnergyMaps M, const EnergyParams P) {
+__global__ void __launch_bounds__(THREADS, 1)
+    k_energy_tc(const __grid_constant__ EnergyMaps M, const __grid_constant__ EnergyParams P) {
   using L = Layout<CW>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
@@ -195,8 +209,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * L::buf + L::asm_bytes);  // [2]
   uint64_t* empty = full + 2;                                         // [2], one arrival per compute warp
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + 2);
-  int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][4]: X, Y, Z, slot
-  double* eps_s = reinterpret_cast<double*>(empty + 16);                          // eps_v[v], then eps_o[o]
+  int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][8]: X, Y, Z, slot, v, item
+  // [2][WARPS] warp sums of an item, 8-byte aligned after meta (full is 128-byte aligned: red sits at +104..+360)
+  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(meta + 2 * 8) + 7) & ~uintptr_t(7));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -207,7 +222,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
-  for (int q = tid; q < P.v + P.o; q += THREADS) eps_s[q] = q < P.v ? P.eps_v[q] : P.eps_o[q - P.v];
   __syncthreads();
 
   if (warp == WARPS) {
@@ -232,24 +246,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
         break;
       }
       ephase ^= 1u << b;
-      const int slot = (int)(it / P.nbt);
-      const int64_t bt = it % P.nbt;
+      const TcPiece& pc = P.pc[piece_of_item(P, it)];
+      const EnergyCl& C = P.cl[pc.cl];
+      const int64_t local = it - pc.item0;
+      const int slot = (int)(local / C.nbt);
+      const int64_t bt = local % C.nbt;
       int blk[3];
       decode_bt(bt, blk);
-      const Triple tr = P.triples[P.t0 + slot];
+      const Triple tr = P.triples[pc.t0 + slot];
       unsigned char* base = smem + (size_t)b * L::buf;
       if (lane == 0) {
-        meta[b * 4 + 0] = blk[0];
-        meta[b * 4 + 1] = blk[1];
-        meta[b * 4 + 2] = blk[2];
-        meta[b * 4 + 3] = slot;
+        meta[b * 8 + 0] = blk[0];
+        meta[b * 8 + 1] = blk[1];
+        meta[b * 8 + 2] = blk[2];
+        meta[b * 8 + 3] = pc.slot0 + slot;
+        meta[b * 8 + 4] = C.v;
+        meta[b * 8 + 5] = (int)(it >> 31);  // the item index, for this item's partials
+        meta[b * 8 + 6] = (int)(it & 0x7fffffff);
         ptx::mbar_arrive_expect_tx(&full[b], L::tx);  // first of the two arrivals
         pending |= 1u << b;
       }
       __syncwarp();
+      const CUtensorMap* map_ovs = &M.ovs[pc.cl];
+      const CUtensorMap* map_t1 = &M.t1[pc.cl];
       for (int q = lane; q < 28; q += 32) {
         if (q == 0) {  // the item's 18 cubes, contiguous ([g][pid] as in shared memory)
-          ptx::bulk_load(base, P.gbuf + it * (18 * TB * TB * TB * CW), 18 * L::cube_bytes, &full[b]);
+          ptx::bulk_load(base, pc.gbuf + local * (18 * TB * TB * TB * CW), 18 * L::cube_bytes, &full[b]);
         } else if (q < 19) {
           // ovs block (pair, sx, sy) with sx != sy: the only ones a permutation's Y reads
           const int rr = q - 1, pair = rr / 6, od = rr % 6;
@@ -257,23 +279,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
           const int r = pair * 9 + sx * 3 + sy;
           const int P1 = (pair == 1) ? tr.j : tr.i;
           const int P2 = (pair == 0) ? tr.j : tr.k;
-          ptx::tma_load_4d(base + L::cubes + r * 256, &M.ovs, &full[b], blk[sy] * TB, P2, blk[sx] * TB, P1);
+          ptx::tma_load_4d(base + L::cubes + r * 256, map_ovs, &full[b], blk[sy] * TB, P2, blk[sx] * TB, P1);
         } else {
           const int r = q - 19, which = r / 3, s2 = r % 3;
           const int occ = which == 0 ? tr.i : (which == 1 ? tr.j : tr.k);
-          ptx::tma_load_2d(base + L::cubes + L::ovs + r * 128, &M.t1, &full[b], blk[s2] * TB, occ);
+          ptx::tma_load_2d(base + L::cubes + L::ovs + r * 128, map_t1, &full[b], blk[s2] * TB, occ);
         }
       }
       {  // FP64 denominator pieces while the copies fly: dAB[la][lb] = e_i+e_j+e_k - e_a - e_b, epsC[lc] = e_c
+        // the 24 virtual energies of the three blocks, one load per lane, shared by shuffles
         double* dAB = reinterpret_cast<double*>(base + L::cubes + L::ovs + L::t1);
-        const double eo = eps_s[P.v + tr.i] + eps_s[P.v + tr.j] + eps_s[P.v + tr.k];
-        for (int q = lane; q < 72; q += 32) {
+        const int lq = lane < 24 ? blk[lane >> 3] * TB + (lane & 7) : 0;
+        const double ev = (lane < 24 && lq < C.v) ? C.eps_v[lq] : 0.0;
+        const double eo = C.eps_o[tr.i] + C.eps_o[tr.j] + C.eps_o[tr.k];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int q = lane + 32 * r;  // every lane shuffles; lanes with q >= 72 store nothing
+          const double ea = __shfl_sync(0xffffffffu, ev, q < 64 ? (q >> 3) : 16 + (q & 7));
+          const double eb = __shfl_sync(0xffffffffu, ev, 8 + (q & 7));
           if (q < 64) {
             const int qa = blk[0] * TB + (q >> 3), qb = blk[1] * TB + (q & 7);
-            dAB[q] = (qa < P.v && qb < P.v) ? (eo - eps_s[qa]) - eps_s[qb] : 0.0;
-          } else {
+            dAB[q] = (qa < C.v && qb < C.v) ? (eo - ea) - eb : 0.0;
+          } else if (q < 72) {
             const int qc = blk[2] * TB + (q - 64);
-            dAB[q] = qc < P.v ? eps_s[qc] : 0.0;
+            dAB[q] = qc < C.v ? ea : 0.0;
           }
         }
       }
@@ -305,8 +334,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
       pos_off[n] = n * 512 + cube_off(u, w, z);
     }
     float* asmY = asmW + CW * 6 * 512;
-    double acc = 0.0;  // this thread's sum over the items of the current triple slot
-    int cur_slot = -1;
     for (int64_t it = blockIdx.x; it < P.items; it += gridDim.x, b ^= 1) {
       int got = 0;
       if (!*abort_flag) got = ptx::mbar_wait(&full[b], (phase >> b) & 1u, P.wait_ns) ? 1 : 0;
@@ -318,19 +345,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
             P.err[2] = blockIdx.x;
           }
         }
-        cur_slot = -1;
         break;
       }
       phase ^= 1u << b;
-      const int bx = meta[b * 4 + 0], by = meta[b * 4 + 1], bz = meta[b * 4 + 2], slot = meta[b * 4 + 3];
-      if (slot != cur_slot) {
-        if (cur_slot >= 0) {  // fixed-order warp reduction of the finished slot
-          for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-          if (lane == 0) P.partials[((int64_t)cur_slot * gridDim.x + blockIdx.x) * WARPS + warp] = acc;
-        }
-        acc = 0.0;
-        cur_slot = slot;
-      }
+      const int bx = meta[b * 8 + 0], by = meta[b * 8 + 1], bz = meta[b * 8 + 2];
+      const int vv = meta[b * 8 + 4];
+      const int64_t item = ((int64_t)meta[b * 8 + 5] << 31) | (int64_t)meta[b * 8 + 6];
+      double acc = 0.0;  // this thread's orbit of the item
       const unsigned char* base = smem + (size_t)b * L::buf;
       const float* cube = reinterpret_cast<const float*>(base);
       const float* ovsS = reinterpret_cast<const float*>(base + L::cubes);
@@ -371,7 +392,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
 
       // ---- phase B ----
       const int a = bx * TB + la, bb = by * TB + lb, c = bz * TB + lc;
-      const bool valid = a < P.v && bb < P.v && c < P.v && !(bx == by && la < lb) && !(by == bz && lb < lc);
+      const bool valid = a < vv && bb < vv && c < vv && !(bx == by && la < lb) && !(by == bz && lb < lc);
       if (valid) {
         // orbit weight A (Eq. E_corr_CCSD_T): 1, 1/2 or 1/6
         const bool all3 = (a == bb && bb == c), two = (a == bb || bb == c);
@@ -419,11 +440,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_energy_tc(const __grid_constant_
           acc = fma(Tw, r1, acc);
         }
       }
-      asm volatile("bar.sync 1, %0;" ::"n"(WARPS * 32) : "memory");  // assembled area free
-    }
-    if (cur_slot >= 0) {
+      // fixed-order sum of the item: warps, then the 16 warp sums in order
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) P.partials[((int64_t)cur_slot * gridDim.x + blockIdx.x) * WARPS + warp] = acc;
+      if (lane == 0) red[b * WARPS + warp] = acc;
+      asm volatile("bar.sync 1, %0;" ::"n"(WARPS * 32) : "memory");  // assembled area free
+      if (warp == 0 && lane == 0) {  // red[b] is next written two items later, after two more barriers
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) sum += red[b * WARPS + w];
+        P.partials[item] = sum;
+      }
     }
   }
   __syncthreads();
@@ -435,32 +461,30 @@ int64_t energy_tc_grid(int num_sms, int64_t items) { return std::min<int64_t>(it
 
 size_t energy_tc_smem(int cw) {
   const size_t buf = cw == 2 ? Layout<2>::buf + Layout<2>::asm_bytes / 2 : Layout<1>::buf + Layout<1>::asm_bytes / 2;
-  return 2 * buf + 128 + 512;  // + eps staging, added by the launcher
+  return 2 * buf + 128 + 512;
 }
 
 cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   EnergyMaps M;
-  M.ovs = *e.map_ovs;
-  M.t1 = *e.map_t1;
-  EnergyParams P{};
-  P.o = e.o;
-  P.v = e.v;
-  P.nslots = e.nslots;
-  P.nb = (e.v + TB - 1) / TB;
-  P.gbuf = e.gbuf;
-  P.nbt = e.nbt;
-  P.items = (int64_t)e.nslots * e.nbt;
-  P.t0 = e.t0;
+  std::memset(&M, 0, sizeof(M));
+  for (int c = 0; c < e.ncl; ++c) {
+    M.ovs[c] = *e.map_ovs[c];
+    M.t1[c] = *e.map_t1[c];
+  }
+  EnergyParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.ncl = e.ncl;
+  P.npieces = e.npieces;
+  P.items = e.items;
+  for (int c = 0; c < e.ncl; ++c) P.cl[c] = e.cl[c];
+  for (int q = 0; q < e.npieces; ++q) P.pc[q] = e.pc[q];
   P.triples = e.triples;
-  P.eps_o = e.eps_o;
-  P.eps_v = e.eps_v;
   P.partials = e.partials;
   P.err = e.err;
   P.wait_ns = e.wait_ns;
-  const size_t smem = energy_tc_smem(e.cw) + sizeof(double) * (size_t)(e.v + e.o);
+  const size_t smem = energy_tc_smem(e.cw);
   const int64_t grid = energy_tc_grid(e.num_sms, P.items);
-  cudaError_t err = cudaMemsetAsync(P.partials, 0, sizeof(double) * (size_t)e.nslots * grid * WARPS, s);
-  if (err != cudaSuccess) return err;
+  cudaError_t err;
   if (e.cw == 2) {
     err = cudaFuncSetAttribute(k_energy_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -470,6 +494,53 @@ cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     k_energy_tc<1><<<(unsigned)grid, THREADS, smem, s>>>(M, P);
   }
+  return cudaGetLastError();
+}
+
+// One block per G slot of the launch: the slot's partials in a fixed order
+// (Neumaier), times m/3, into its piece's share array.
+__global__ void __launch_bounds__(256) k_reduce_pieces(const double* __restrict__ partials,
+                                                       const Triple* __restrict__ triples,
+                                                       const __grid_constant__ PieceTable T) {
+  const int gslot = blockIdx.x;
+  int q = 0;
+  while (q + 1 < T.n && T.pc[q + 1].slot0 <= gslot) ++q;
+  const TcPiece& pc = T.pc[q];
+  const int local = gslot - pc.slot0;
+  const int64_t nper = pc.nbt;
+  const double* x = partials + pc.item0 + (int64_t)local * pc.nbt;
+  __shared__ double ss[256], cc[256];
+  double sum = 0.0, c = 0.0;
+  for (int64_t i = threadIdx.x; i < nper; i += blockDim.x) {
+    const double t = sum + x[i];
+    if (fabs(sum) >= fabs(x[i])) c += (sum - t) + x[i];
+    else c += (x[i] - t) + sum;
+    sum = t;
+  }
+  ss[threadIdx.x] = sum;
+  cc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      double s1 = ss[threadIdx.x], c1 = cc[threadIdx.x] + cc[threadIdx.x + w];
+      const double y = ss[threadIdx.x + w], t = s1 + y;
+      if (fabs(s1) >= fabs(y)) c1 += (s1 - t) + y;
+      else c1 += (y - t) + s1;
+      ss[threadIdx.x] = t;
+      cc[threadIdx.x] = c1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) pc.shares[local] = (ss[0] + cc[0]) * ((double)triples[pc.t0 + local].m / 3.0);
+}
+
+cudaError_t launch_reduce_pieces(const double* partials, const Triple* triples, const TcPiece* pieces,
+                                 int npieces, int nslots, cudaStream_t s) {
+  PieceTable T;
+  std::memset(&T, 0, sizeof(T));
+  T.n = npieces;
+  for (int q = 0; q < npieces; ++q) T.pc[q] = pieces[q];
+  k_reduce_pieces<<<(unsigned)nslots, 256, 0, s>>>(partials, triples, T);
   return cudaGetLastError();
 }
 

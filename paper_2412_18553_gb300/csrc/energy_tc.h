@@ -8,19 +8,52 @@
 
 namespace te {
 
-struct EnergyLaunch {
-  int o, v, nslots, cw, num_sms;
-  int64_t nbt, t0;
-  const float* gbuf;           // orbit-major G: [slot][bt][g][pid][cw planes][512 swizzled]
-  const CUtensorMap* map_ovs;  // ovs32 [o][v][o][vq], 4D (b, j, a, i), box (8, 1, 8, 1)
-  const CUtensorMap* map_t1;   // t1 [o][vq], 2D (a, i), box (8, 1)
-  const Triple* triples;
-  const double* eps_o;
+// A launch of the contraction and energy kernels covers up to TC_MAX_CL
+// clusters and TC_MAX_PIECES pieces: a piece is one cluster's run of
+// consecutive canonical triples, each with its own G slot.  The per-cluster
+// constants, tensor maps and pieces travel as kernel parameters.
+constexpr int TC_MAX_CL = 8;
+constexpr int TC_MAX_PIECES = 48;
+
+struct TcPiece {
+  int cl;          // cluster (index into the launch's cluster table)
+  int ns;          // triples (G slots) of the piece
+  int slot0;       // first G slot, counted over the launch's pieces
+  int64_t t0;      // first canonical triple
+  int64_t tile0;   // first contraction tile of the piece
+  int64_t item0;   // first energy item of the piece
+  int64_t nbt;     // energy items per triple (the cluster's block triples)
+  float* gbuf;     // G of the piece's first slot
+  double* shares;  // per-triple shares of the piece (ns doubles)
+};
+
+// Per-cluster constants of the energy kernel.
+struct EnergyCl {
+  int o, v, nb;
+  int64_t nbt;          // block triples X >= Y >= Z of 8-wide virtual blocks
+  const double* eps_o;  // caller's arrays
   const double* eps_v;
-  double* partials;  // [nslots][energy_tc_grid(num_sms, nslots*nbt)][ENERGY_TC_WARPS], zeroed by the launch
+};
+
+struct EnergyLaunch {
+  int ncl, npieces, cw, num_sms, nslots;  // nslots: G slots over all pieces
+  int64_t items;                          // sum over pieces of ns * nbt
+  EnergyCl cl[TC_MAX_CL];
+  TcPiece pc[TC_MAX_PIECES];
+  const CUtensorMap* map_ovs[TC_MAX_CL];  // ovs32 [o][v][o][vq], 4D (b, j, a, i), box (8, 1, 8, 1)
+  const CUtensorMap* map_t1[TC_MAX_CL];   // t1 [o][vq], 2D (a, i), box (8, 1)
+  const Triple* triples;
+  double* partials;  // [items]: every item's fixed-order sum, all written
   unsigned int* err;
   unsigned long long wait_ns;
 };
+
+// Per-triple shares of every slot of a launch: shares[t] = (m_t / 3) times the
+// fixed-order sum of the slot's nbt item partials.  The order
+// depends on the cluster alone, not on the launch's other pieces, so a triple's
+// share is the same bits in a single-cluster call and in a batch.
+cudaError_t launch_reduce_pieces(const double* partials, const Triple* triples, const TcPiece* pieces,
+                                 int npieces, int nslots, cudaStream_t s);
 
 // Layout of one 8x8x8 G cube (shared by the contraction epilogue that writes it
 // and the energy kernel that reads it): element (u, w, z) of a plane sits at

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 
 #include "energy_tc.h"
@@ -65,7 +66,6 @@ struct ModeTraits {
   static constexpr bool tf32 = (MODE == TC_TF32 || MODE == TC_TF32X3);
   static constexpr int nparts = (MODE == TC_TF32) ? 1 : (MODE == TC_OZAKI ? 4 : (MODE == TC_OZAKI6 ? 5 : 2));
   static constexpr int nacc = is_ozaki(MODE) ? 3 : 1;   // accumulators per tile
-  static constexpr int nbuf = is_ozaki(MODE) ? 1 : 2;   // TMEM buffering
   static constexpr int beta = MODE == TC_OZAKI6 ? 6 : 7;  // bits per slice
 };
 
@@ -198,19 +198,14 @@ __global__ void k_ovs32(const double* __restrict__ ovov, float* __restrict__ ovs
   }
 }
 
-// t1_32[i][a] (a padded to vq) and a copy of eps_v
-__global__ void k_small_copies(const double* __restrict__ t1, const double* __restrict__ eps_v,
-                               float* __restrict__ t1_32, double* __restrict__ eps_copy, int o, int v, int vq) {
+// t1_32[i][a] = t1[i][a] as float32, a padded to vq
+__global__ void k_small_copies(const double* __restrict__ t1, float* __restrict__ t1_32, int o, int v, int vq) {
   const int64_t n = (int64_t)o * vq;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n + v;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    if (idx < n) {
-      const int a = (int)(idx % vq);
-      const int i = (int)(idx / vq);
-      t1_32[idx] = a < v ? (float)t1[(int64_t)i * v + a] : 0.f;
-    } else {
-      eps_copy[idx - n] = eps_v[idx - n];
-    }
+    const int a = (int)(idx % vq);
+    const int i = (int)(idx / vq);
+    t1_32[idx] = a < v ? (float)t1[(int64_t)i * v + a] : 0.f;
   }
 }
 
@@ -266,24 +261,38 @@ struct TcMaps {
   CUtensorMap b_noo;  // nooT slices [p][r][s][z][op], dims (op, z, s, r, p)
 };
 
-struct TcParams {
+// The maps of every cluster of a launch.
+struct TcMapSet {
+  TcMaps m[TC_MAX_CL];
+};
+
+// Per-cluster constants of a contraction launch.
+struct TcCl {
   int o, v;
   int TA, TB, NT;
   int n_mx, n_my, n_nt;
   int kw_chunks, ko_chunks;
   int kw_elems, ko_elems;  // elements per chunk
-  int cbw, cbo;            // chunk bytes (v- and o-segments)
-  int stages;
-  uint32_t stage_bytes, a_part_bytes, b_part_bytes;
-  uint32_t tmem_cols;
-  int64_t total_tiles;
-  int64_t t0;
-  const Triple* triples;
-  float* gbuf;
-  int ldz;                 // G row stride in elements (an element is 1 or 2 floats)
+  int cbo;                 // chunk bytes of the o-segments (the v-segments use TcParams::cbw)
+  int64_t slot_floats;     // G floats per triple slot
   const int* exps;         // OZAKI scale exponents
+};
+
+struct TcParams {
+  int ncl, npieces;
+  int cbw;                 // chunk bytes of the v-segments
+  int stages;
+  uint32_t stage_bytes;    // stage stride: the largest cluster's A and B parts
+  uint32_t a_part_bytes;   // 128 rows x cbw
+  uint32_t tmem_cols;
+  int nbuf;                // TMEM accumulator sets (1 or 2)
+  int nt_max;              // largest N tile: stride of the accumulator sets
+  int64_t total_tiles;
+  const Triple* triples;
   unsigned int* err;
   unsigned long long wait_ns;
+  TcCl cl[TC_MAX_CL];
+  TcPiece pc[TC_MAX_PIECES];
 };
 
 __device__ __forceinline__ uint32_t layout_code(int cb) { return cb == 128 ? 2u : (cb == 64 ? 4u : 6u); }
@@ -297,27 +306,33 @@ __device__ __forceinline__ void record_abort(const TcParams& P, volatile int* ab
 }
 
 struct TileCoord {
-  int slot, g, p, q, r, x0, y0, z0;
+  int cl, piece, slot, g, p, q, r, x0, y0, z0;
 };
 
 __device__ __forceinline__ TileCoord decode_tile(const TcParams& P, int64_t tt) {
   TileCoord c;
-  int64_t rest = tt;
-  const int nt = (int)(rest % P.n_nt);
-  rest /= P.n_nt;
-  const int my = (int)(rest % P.n_my);
-  rest /= P.n_my;
-  const int mx = (int)(rest % P.n_mx);
-  rest /= P.n_mx;
+  int q = 0;  // pieces are in tile order
+  while (q + 1 < P.npieces && P.pc[q + 1].tile0 <= tt) ++q;
+  const TcPiece& pc = P.pc[q];
+  const TcCl& C = P.cl[pc.cl];
+  int64_t rest = tt - pc.tile0;
+  const int nt = (int)(rest % C.n_nt);
+  rest /= C.n_nt;
+  const int my = (int)(rest % C.n_my);
+  rest /= C.n_my;
+  const int mx = (int)(rest % C.n_mx);
+  rest /= C.n_mx;
   c.g = (int)(rest % 3);
   c.slot = (int)(rest / 3);
-  const Triple T = P.triples[P.t0 + c.slot];
+  c.cl = pc.cl;
+  c.piece = q;
+  const Triple T = P.triples[pc.t0 + c.slot];
   if (c.g == 0) { c.p = T.i; c.q = T.j; c.r = T.k; }
   else if (c.g == 1) { c.p = T.j; c.q = T.k; c.r = T.i; }
   else { c.p = T.k; c.q = T.i; c.r = T.j; }
-  c.x0 = mx * P.TA;
-  c.y0 = my * P.TB;
-  c.z0 = nt * P.NT;
+  c.x0 = mx * C.TA;
+  c.y0 = my * C.TB;
+  c.z0 = nt * C.NT;
   return c;
 }
 
@@ -351,19 +366,27 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Warp roles: 0 TMA producer, 1 MMA issuer (and TMEM owner), 2..9 epilogue:
-// warp w drains TMEM lanes 32 (w % 4) .. +31 (the lane quarter its warp index
-// may access) and every other 16-column chunk, starting at chunk (w - 2) / 4.
-constexpr int GEMM_EPI_WARPS = 8;
+// Warp roles: 0 TMA producer, 1 MMA issuer (and TMEM owner), the rest
+// epilogue: warp w drains TMEM lanes 32 (w % 4) .. +31 (the lane quarter its
+// warp index may access) and every (GEMM_EPI_WARPS / 4)-th 16-column chunk,
+// starting at chunk (w - 2) / 4.
+#ifndef TE_GEMM_EPI_WARPS
+#define TE_GEMM_EPI_WARPS 8
+#endif
+constexpr int GEMM_EPI_WARPS = TE_GEMM_EPI_WARPS;
+constexpr int GEMM_EPI_GROUPS = GEMM_EPI_WARPS / 4;
 constexpr int GEMM_THREADS = (2 + GEMM_EPI_WARPS) * 32;
 
 template <int MODE>
-__global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_constant__ TcMaps maps, const TcParams P) {
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ TcMapSet maps, const __grid_constant__ TcParams P) {
   using MT = ModeTraits<MODE>;
   constexpr bool TF32 = MT::tf32;
   constexpr int NPART = MT::nparts;
   constexpr int NACC = MT::nacc;
-  constexpr int NBUF = MT::nbuf;
+  // TMEM accumulator sets: 2 when they fit (the epilogue of one tile then
+  // overlaps the MMAs of the next), else 1
+  const int NBUF = P.nbuf;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~uintptr_t(1023));
@@ -391,13 +414,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
-  if (warp == 0 && lane == 0) {
-    ptx::tma_prefetch_desc(&maps.a_nat);
-    ptx::tma_prefetch_desc(&maps.a_tr);
-    ptx::tma_prefetch_desc(&maps.l_nat);
-    ptx::tma_prefetch_desc(&maps.l_tr);
-    ptx::tma_prefetch_desc(&maps.b_t2);
-    ptx::tma_prefetch_desc(&maps.b_noo);
+  if (warp == 0 && lane < P.ncl) {
+    const TcMaps& m = maps.m[lane];
+    ptx::tma_prefetch_desc(&m.a_nat);
+    ptx::tma_prefetch_desc(&m.a_tr);
+    ptx::tma_prefetch_desc(&m.l_nat);
+    ptx::tma_prefetch_desc(&m.l_tr);
+    ptx::tma_prefetch_desc(&m.b_t2);
+    ptx::tma_prefetch_desc(&m.b_noo);
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, P.tmem_cols);
@@ -407,6 +431,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const uint32_t acc_stride = (uint32_t)(NACC * P.nt_max);  // TMEM columns between accumulator sets
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -417,12 +442,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
       bool ok = true;
       for (int64_t tt = blockIdx.x; ok && tt < P.total_tiles; tt += gridDim.x) {
         const TileCoord c = decode_tile(P, tt);
+        const TcCl& C = P.cl[c.cl];
+        const TcMaps& mp = maps.m[c.cl];
         for (int seg = 0; ok && seg < 4; ++seg) {
           const bool wide = seg < 2;
-          const int nch = wide ? P.kw_chunks : P.ko_chunks;
-          const int cb = wide ? P.cbw : P.cbo;
-          const int ce = wide ? P.kw_elems : P.ko_elems;
-          const uint32_t bytes = (uint32_t)NPART * (128u * cb + (uint32_t)P.NT * cb);
+          const int nch = wide ? C.kw_chunks : C.ko_chunks;
+          const int cb = wide ? P.cbw : C.cbo;
+          const int ce = wide ? C.kw_elems : C.ko_elems;
+          const uint32_t bytes = (uint32_t)NPART * (128u * cb + (uint32_t)C.NT * cb);
           for (int ch = 0; ch < nch; ++ch) {
             if (*abort_flag || !ptx::mbar_wait(&empty[stage], phase ^ 1u, P.wait_ns)) {
               if (!*abort_flag) record_abort(P, abort_flag, 1);
@@ -435,17 +462,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
             unsigned char* sb = sa + NPART * P.a_part_bytes;
             const int kc = ch * ce;
             if (seg == 0) {
-              ptx::tma_load_5d(sa, &maps.a_nat, &full[stage], kc, c.y0, c.x0, 0, c.p);
-              ptx::tma_load_5d(sb, &maps.b_t2, &full[stage], kc, c.z0, 0, c.q, c.r);
+              ptx::tma_load_5d(sa, &mp.a_nat, &full[stage], kc, c.y0, c.x0, 0, c.p);
+              ptx::tma_load_5d(sb, &mp.b_t2, &full[stage], kc, c.z0, 0, c.q, c.r);
             } else if (seg == 1) {
-              ptx::tma_load_5d(sa, &maps.a_tr, &full[stage], kc, c.y0, c.x0, 0, c.q);
-              ptx::tma_load_5d(sb, &maps.b_t2, &full[stage], kc, c.z0, 0, c.p, c.r);
+              ptx::tma_load_5d(sa, &mp.a_tr, &full[stage], kc, c.y0, c.x0, 0, c.q);
+              ptx::tma_load_5d(sb, &mp.b_t2, &full[stage], kc, c.z0, 0, c.p, c.r);
             } else if (seg == 2) {
-              ptx::tma_load_5d(sa, &maps.l_tr, &full[stage], kc, c.y0, c.x0, 0, c.p);
-              ptx::tma_load_5d(sb, &maps.b_noo, &full[stage], kc, c.z0, 0, c.r, c.q);
+              ptx::tma_load_5d(sa, &mp.l_tr, &full[stage], kc, c.y0, c.x0, 0, c.p);
+              ptx::tma_load_5d(sb, &mp.b_noo, &full[stage], kc, c.z0, 0, c.r, c.q);
             } else {
-              ptx::tma_load_5d(sa, &maps.l_nat, &full[stage], kc, c.y0, c.x0, 0, c.q);
-              ptx::tma_load_5d(sb, &maps.b_noo, &full[stage], kc, c.z0, 0, c.r, c.p);
+              ptx::tma_load_5d(sa, &mp.l_nat, &full[stage], kc, c.y0, c.x0, 0, c.q);
+              ptx::tma_load_5d(sb, &mp.b_noo, &full[stage], kc, c.z0, 0, c.r, c.p);
             }
             if (++stage == (uint32_t)P.stages) {
               stage = 0;
@@ -462,23 +489,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t fmt = TF32 ? 2u : 1u;
-      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(P.NT >> 3) << 17) |
-                             ((uint32_t)(128 >> 4) << 24);
       uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
       bool ok = true;
       bool issued = false;
       for (int64_t tt = blockIdx.x; ok && tt < P.total_tiles; tt += gridDim.x) {
+        const TileCoord c = decode_tile(P, tt);
+        const TcCl& C = P.cl[c.cl];
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(C.NT >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
         if (*abort_flag || !ptx::mbar_wait(&tempty[acc], acc_phase ^ 1u, P.wait_ns)) {
           if (!*abort_flag) record_abort(P, abort_flag, 2);
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t d_tmem = tmem_base + acc * (uint32_t)(NACC * P.NT);
+        const uint32_t d_tmem = tmem_base + acc * acc_stride;
         uint32_t first = 1;
         for (int seg = 0; ok && seg < 4; ++seg) {
           const bool wide = seg < 2;
-          const int nch = wide ? P.kw_chunks : P.ko_chunks;
-          const int cb = wide ? P.cbw : P.cbo;
+          const int nch = wide ? C.kw_chunks : C.ko_chunks;
+          const int cb = wide ? P.cbw : C.cbo;
           const uint32_t lay = layout_code(cb);
           const uint32_t sbo = 8u * (uint32_t)cb;
           for (int ch = 0; ch < nch; ++ch) {
@@ -497,13 +526,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
               for (int k = 0; k < NPART; ++k) {
                 // one box per operand lands the slices back to back: 128 (A) or NT (B) rows of cb bytes each
                 ad[k] = ptx::smem_desc(a0 + k * (128u * (uint32_t)cb) + ks * 32, sbo, lay);
-                bd[k] = ptx::smem_desc(b0 + k * ((uint32_t)P.NT * (uint32_t)cb) + ks * 32, sbo, lay);
+                bd[k] = ptx::smem_desc(b0 + k * ((uint32_t)C.NT * (uint32_t)cb) + ks * 32, sbo, lay);
               }
               const uint32_t acc_in = first ? 0u : 1u;
               if constexpr (is_ozaki(MODE)) {
                 // slice products a_i b_j with i + j <= NPART - 1: level i + j = 0 and
                 // level 1 each in an exact accumulator, the higher levels in a third
-                const uint32_t d2 = d_tmem, d3 = d_tmem + P.NT, dr = d_tmem + 2 * P.NT;
+                const uint32_t d2 = d_tmem, d3 = d_tmem + C.NT, dr = d_tmem + 2 * C.NT;
                 ptx::mma<false>(d2, ad[0], bd[0], idesc, acc_in);
                 ptx::mma<false>(d3, ad[0], bd[1], idesc, acc_in);
                 ptx::mma<false>(d3, ad[1], bd[0], idesc, 1);
@@ -550,13 +579,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
   } else {
     // ---------------- epilogue: TMEM -> G buffer ----------------
     const int quad = warp & 3;
-    const int chunk0 = (warp - 2) >> 2;  // 0 or 1: this warp's first 16-column chunk
+    const int chunk0 = (warp - 2) >> 2;  // this warp's first 16-column chunk
     const int row = quad * 32 + lane;
-    float gscale = 1.f;
-    if (is_ozaki(MODE)) gscale = ldexpf(1.f, P.exps[4]);
     uint32_t acc = 0, acc_phase = 0;
     for (int64_t tt = blockIdx.x; tt < P.total_tiles; tt += gridDim.x) {
       const TileCoord c = decode_tile(P, tt);
+      const TcCl& C = P.cl[c.cl];
+      const TcPiece& pc = P.pc[c.piece];
       int got = 0;
       if (!*abort_flag) got = ptx::mbar_wait(&tfull[acc], acc_phase, P.wait_ns) ? 1 : 0;
       // the decision is warp-uniform: tcgen05.ld below is a .sync.aligned instruction
@@ -565,23 +594,24 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const __grid_consta
         break;
       }
       ptx::tc_fence_after();
-      const int x = c.x0 + row / P.TB;
-      const int y = c.y0 + row % P.TB;
-      const bool valid = x < P.v && y < P.v;
+      float gscale = 1.f;
+      if (is_ozaki(MODE)) gscale = ldexpf(1.f, C.exps[4]);
+      const int x = c.x0 + row / C.TB;
+      const int y = c.y0 + row % C.TB;
+      const bool valid = x < C.v && y < C.v;
       // orbit-major G: [slot][bt][g][pid][CW planes][512], swizzled rows (see
       // energy_tc.h); this row is (x, y) = (X*8 + xl, Y*8 + yl)
-      const int nb = (P.v + 7) >> 3;
+      const int nb = (C.v + 7) >> 3;
       constexpr int CWF = is_ozaki(MODE) ? 2 : 1;
-      const int64_t slot_floats = g_slot_floats(P.v, CWF);
-      float* const gslot = P.gbuf + (int64_t)c.slot * slot_floats;
+      float* const gslot = pc.gbuf + (int64_t)c.slot * C.slot_floats;
       const int roff = cube_row(x & 7, y & 7);
       const int zx = cube_zx(x & 7, y & 7);
-      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (uint32_t)(NACC * P.NT);
-      for (int c0 = 16 * chunk0; c0 < P.NT; c0 += 32) {
+      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * acc_stride;
+      for (int c0 = 16 * chunk0; c0 < C.NT; c0 += 16 * GEMM_EPI_GROUPS) {
         const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
         if constexpr (is_ozaki(MODE)) {
           float a2[16], a3[16], ar[16];
-          ptx::tmem_ld16x3(tbase + c0, tbase + P.NT + c0, tbase + 2 * P.NT + c0, a2, a3, ar);
+          ptx::tmem_ld16x3(tbase + c0, tbase + C.NT + c0, tbase + 2 * C.NT + c0, a2, a3, ar);
           if (valid) {
             float hv[16], lv[16];
 #pragma unroll
@@ -691,6 +721,7 @@ struct TcPlan {
   int kw_chunks, ko_chunks, kw_elems, ko_elems, cbw, cbo;
   int stages;
   uint32_t stage_bytes, a_part_bytes, b_part_bytes, tmem_cols;
+  int nbuf;
   int nslots;
   int ldz;
   size_t smem;
@@ -706,7 +737,11 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.es = (mode == TC_BF16X3 || oz) ? 2 : 4;
   pl.nparts = mode == TC_TF32 ? 1 : (mode == TC_OZAKI ? 4 : (mode == TC_OZAKI6 ? 5 : 2));
   pl.cw = oz ? 2 : 1;
-  const int nacc = oz ? 3 : 1, nbuf = oz ? 1 : 2;
+  const int nacc = oz ? 3 : 1;
+  // TF32/BF16X3 (one accumulator) double-buffer at any N tile; the exact-slice
+  // modes (three accumulators) take N tiles up to 160 single-buffered, and
+  // double-buffer when 2 x 3 x NT <= 512 columns (NT <= 80)
+  const int nbuf_max = oz ? 1 : 2;
   pl.vp = round_up(v, 16);
   pl.op = round_up(o, 16);
   pl.vq = round_up(v, 4);
@@ -733,10 +768,11 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.TA = 128 / bestTB;
   pl.n_mx = (v + pl.TA - 1) / pl.TA;
   pl.n_my = (v + pl.TB - 1) / pl.TB;
-  const int ntmax = std::min(256, (512 / (nacc * nbuf)) / 16 * 16);
+  const int ntmax = std::min(256, (512 / (nacc * nbuf_max)) / 16 * 16);
   pl.n_nt = (v + ntmax - 1) / ntmax;
   if (force_nnt >= pl.n_nt) pl.n_nt = force_nnt;
   pl.NT = round_up((v + pl.n_nt - 1) / pl.n_nt, 16);
+  pl.nbuf = (2 * nacc * pl.NT <= 512) ? 2 : 1;
   pl.cbw = oz ? 64 : 128;
   pl.kw_elems = pl.cbw / pl.es;
   pl.kw_chunks = (pl.vp + pl.kw_elems - 1) / pl.kw_elems;
@@ -751,7 +787,7 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.stages = (int)std::min<size_t>(8, avail / pl.stage_bytes);
   pl.smem = (size_t)pl.stages * pl.stage_bytes + 1024 + 256;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(nacc * nbuf * pl.NT)) cols <<= 1;
+  while (cols < (uint32_t)(nacc * pl.nbuf * pl.NT)) cols <<= 1;
   pl.tmem_cols = cols;
   pl.ldz = round_up(v, 4);
   const int64_t tiles = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
@@ -764,16 +800,22 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   return pl;
 }
 
+// ---------------------------------------------------------------------------
+// host side: workspace, launch rounds
+// ---------------------------------------------------------------------------
+
+// One cluster's part of the workspace: the operand planes, the float32
+// copies the energy kernel reads, the scale exponents and the per-triple
+// shares.  The G pool and the energy partials are shared by a whole run.
 struct TcBuffers {
   void *a[MAX_PARTS], *b[MAX_PARTS], *l[MAX_PARTS], *n[MAX_PARTS];
-  float *ovs32, *t1_32, *gbuf;
-  double *eps_copy, *partials, *etri;
+  float *ovs32, *t1_32;
+  double* etri;
   unsigned long long* maxbits;
   int* exps;
 };
 
-static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64_t nbt, int64_t ntri,
-                       TcBuffers* b) {
+static size_t tc_carve_cluster(char* base, const TcPlan& pl, int64_t o, int64_t v, int64_t ntri, TcBuffers* b) {
   size_t off = 0;
   auto take = [&](size_t bytes) -> void* {
     off = (off + 1023) & ~size_t(1023);
@@ -801,13 +843,25 @@ static size_t tc_carve(char* base, const TcPlan& pl, int64_t o, int64_t v, int64
   }
   b->ovs32 = static_cast<float*>(take((size_t)o * v * o * pl.vq * 4));
   b->t1_32 = static_cast<float*>(take((size_t)o * pl.vq * 4));
-  b->eps_copy = static_cast<double*>(take((size_t)v * 8));
-  b->gbuf = static_cast<float*>(take((size_t)pl.nslots * (size_t)g_slot_floats((int)v, pl.cw) * 4));
-  b->partials = static_cast<double*>(take((size_t)pl.nslots * ENERGY_TC_WARPS * 1024 * 8));
   b->etri = static_cast<double*>(take((size_t)std::max<int64_t>(1, ntri) * 8));
   b->maxbits = static_cast<unsigned long long*>(take(4 * 8));
   b->exps = static_cast<int*>(take(8 * 4));
-  return off + 1024;
+  return (off + 1023) & ~size_t(1023);
+}
+
+// Energy items of a launch never exceed its G floats / (18 cubes x 512 x cw):
+// that bounds the partials (one double per item).
+static int64_t partial_items_of(int64_t pool_floats, int cw) { return pool_floats / (18 * 512 * cw) + 1; }
+
+// Workspace of one run: the clusters' parts, then the G pool, then the partials.
+struct TcPool {
+  int64_t pool_floats;
+  int64_t partial_items;
+};
+
+static size_t tc_shared_bytes(const TcPool& q) {
+  const size_t g = ((size_t)q.pool_floats * 4 + 1023) & ~size_t(1023);
+  return g + (size_t)q.partial_items * 8 + 1024;
 }
 
 static te_status encode(TcState* st, CUtensorMap* m, const void* base, CUtensorMapDataType dt, int rank,
@@ -876,7 +930,7 @@ struct EnergyMapsHost {
   CUtensorMap ovs, t1;
 };
 
-static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, int nslots, const TcBuffers& b,
+static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, const TcBuffers& b,
                                    EnergyMapsHost* E) {
   std::memset(E, 0, sizeof(*E));
   const uint64_t V = v, O = o, vq = pl.vq;
@@ -920,17 +974,266 @@ static cudaError_t launch_prep_tc(const te_cluster* c, const TcPlan& pl, const T
   k_split_t2L<MODE><<<gridn((int64_t)o * v * v * pl.op), 256, 0, s>>>(c->t2, Lp, o, v, pl.op, ex, 2);
   k_split_noo<MODE><<<gridn((int64_t)o * o * v * pl.op), 256, 0, s>>>(c->ooov, N, o, v, pl.op, ex, 3);
   k_ovs32<<<gridn((int64_t)o * v * o * pl.vq), 256, 0, s>>>(c->ovov, b.ovs32, o, v, pl.vq);
-  k_small_copies<<<gridn((int64_t)o * pl.vq + v), 256, 0, s>>>(c->t1, c->eps_v, b.t1_32, b.eps_copy, o, v, pl.vq);
+  k_small_copies<<<gridn((int64_t)o * pl.vq), 256, 0, s>>>(c->t1, b.t1_32, o, v, pl.vq);
   return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_gemm_tc(const Handle* h, const TcMaps& M, const TcParams& P, size_t smem, cudaStream_t s) {
+static cudaError_t launch_gemm_tc(const TcMapSet& M, const TcParams& P, size_t smem, int grid_cap, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t grid = std::min<int64_t>(P.total_tiles, h->num_sms);
+  const int64_t grid = std::min<int64_t>(P.total_tiles, grid_cap);
   k_gemm_tc<MODE><<<(unsigned)grid, GEMM_THREADS, smem, s>>>(M, P);
   return cudaGetLastError();
+}
+
+static cudaError_t launch_gemm_any(int mode, const TcMapSet& M, const TcParams& P, size_t smem, int grid_cap,
+                                   cudaStream_t s) {
+  if (mode == TC_BF16X3) return launch_gemm_tc<TC_BF16X3>(M, P, smem, grid_cap, s);
+  if (mode == TC_TF32X3) return launch_gemm_tc<TC_TF32X3>(M, P, smem, grid_cap, s);
+  if (mode == TC_TF32) return launch_gemm_tc<TC_TF32>(M, P, smem, grid_cap, s);
+  if (mode == TC_OZAKI) return launch_gemm_tc<TC_OZAKI>(M, P, smem, grid_cap, s);
+  return launch_gemm_tc<TC_OZAKI6>(M, P, smem, grid_cap, s);
+}
+
+static cudaError_t launch_prep_any(int mode, const te_cluster* c, const TcPlan& pl, const TcBuffers& b,
+                                   cudaStream_t s) {
+  if (mode == TC_BF16X3) return launch_prep_tc<TC_BF16X3>(c, pl, b, s);
+  if (mode == TC_TF32X3) return launch_prep_tc<TC_TF32X3>(c, pl, b, s);
+  if (mode == TC_TF32) return launch_prep_tc<TC_TF32>(c, pl, b, s);
+  if (mode == TC_OZAKI) return launch_prep_tc<TC_OZAKI>(c, pl, b, s);
+  return launch_prep_tc<TC_OZAKI6>(c, pl, b, s);
+}
+
+// One cluster of a run: its plan, buffers, tensor maps and triple range.
+struct TcJob {
+  const te_cluster* c = nullptr;
+  TcPlan pl{};
+  TcBuffers b{};
+  TcMaps maps{};
+  EnergyMapsHost em{};
+  int o = 0, v = 0;
+  int64_t t_begin = 0, t_end = 0;
+  int64_t nbt = 0, slot_floats = 0, tiles_per_triple = 0;
+  double* shares = nullptr;  // share of triple t at shares[t - t_begin]
+  double* e_out = nullptr;   // sum of the shares (nullable)
+};
+
+static void fill_cluster(const TcJob& J, TcCl* C) {
+  C->o = J.o;
+  C->v = J.v;
+  C->TA = J.pl.TA;
+  C->TB = J.pl.TB;
+  C->NT = J.pl.NT;
+  C->n_mx = J.pl.n_mx;
+  C->n_my = J.pl.n_my;
+  C->n_nt = J.pl.n_nt;
+  C->kw_chunks = J.pl.kw_chunks;
+  C->ko_chunks = J.pl.ko_chunks;
+  C->kw_elems = J.pl.kw_elems;
+  C->ko_elems = J.pl.ko_elems;
+  C->cbo = J.pl.cbo;
+  C->slot_floats = J.slot_floats;
+  C->exps = J.b.exps;
+}
+
+// Contraction parameters of one launch over the clusters jl[0..ncl) of `jobs`
+// and the given pieces; *smem receives the dynamic shared memory.
+static te_status gemm_params(const Handle* h, const std::vector<TcJob>& jobs, const int* jl, int ncl,
+                             const TcPiece* pcs, int npieces, int64_t tiles, int mode, TcParams* P, TcMapSet* M,
+                             size_t* smem) {
+  std::memset(P, 0, sizeof(*P));
+  std::memset(M, 0, sizeof(*M));
+  uint32_t stage_max = 0;
+  int nt_max = 0;
+  for (int q = 0; q < ncl; ++q) {
+    const TcJob& J = jobs[jl[q]];
+    fill_cluster(J, &P->cl[q]);
+    M->m[q] = J.maps;
+    stage_max = std::max(stage_max, J.pl.stage_bytes);
+    nt_max = std::max(nt_max, J.pl.NT);
+  }
+  const TcPlan& p0 = jobs[jl[0]].pl;
+  const int nacc = is_ozaki(mode) ? 3 : 1;
+  P->ncl = ncl;
+  P->npieces = npieces;
+  P->cbw = p0.cbw;
+  P->a_part_bytes = 128u * (uint32_t)p0.cbw;
+  P->stage_bytes = stage_max;
+  const size_t avail = h->smem_optin > 2048 ? h->smem_optin - 2048 : 0;
+  P->stages = (int)std::min<size_t>(8, avail / stage_max);
+  if (P->stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
+  P->nbuf = p0.nbuf;
+  P->nt_max = nt_max;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(nacc * P->nbuf * nt_max)) cols <<= 1;
+  P->tmem_cols = cols;
+  P->total_tiles = tiles;
+  P->triples = h->d_triples;
+  P->err = h->d_err;
+  P->wait_ns = h->wait_limit_ns;
+  for (int q = 0; q < npieces; ++q) P->pc[q] = pcs[q];
+  *smem = (size_t)P->stages * stage_max + 1024 + 256;
+  return TE_OK;
+}
+
+// Runs the jobs' triples in rounds: each round fills the G pool with pieces
+// (up to TC_MAX_CL clusters, TC_MAX_PIECES pieces, one TMEM buffering), then
+// launches the contraction, the energy epilogue and the share reduction once.
+// Then each job's total.  Pieces follow the jobs' order.
+static te_status run_rounds(Handle* h, std::vector<TcJob>& jobs, int mode, float* pool, const TcPool& pq,
+                            double* partials, cudaStream_t s) {
+  const double nprod = (mode == TC_TF32) ? 1.0 : (mode == TC_OZAKI ? 10.0 : (mode == TC_OZAKI6 ? 15.0 : 3.0));
+  const int cw = is_ozaki(mode) ? 2 : 1;
+  size_t j = 0;
+  int64_t t = jobs.empty() ? 0 : jobs[0].t_begin;
+  std::vector<TcPiece> pcs;
+  TcMapSet* MS = new TcMapSet;
+  TcParams* P = new TcParams;
+  EnergyLaunch* EL = new EnergyLaunch;
+  te_status st = TE_OK;
+  while (st == TE_OK) {
+    while (j < jobs.size() && t >= jobs[j].t_end) {
+      ++j;
+      if (j < jobs.size()) t = jobs[j].t_begin;
+    }
+    if (j >= jobs.size()) break;
+    int jl[TC_MAX_CL];
+    int ncl = 0, nbuf = -1, nslots = 0;
+    int64_t used = 0, tiles = 0, items = 0;
+    double flops = 0.0;
+    pcs.clear();
+    while (j < jobs.size() && (int)pcs.size() < TC_MAX_PIECES) {
+      TcJob& J = jobs[j];
+      if (t >= J.t_end) {
+        ++j;
+        if (j < jobs.size()) t = jobs[j].t_begin;
+        continue;
+      }
+      int cl = -1;
+      for (int q = 0; q < ncl; ++q)
+        if (jl[q] == (int)j) cl = q;
+      if (cl < 0) {
+        if (ncl == TC_MAX_CL || (nbuf >= 0 && J.pl.nbuf != nbuf)) break;
+        cl = ncl;
+      }
+      const int64_t fit = std::min((pq.pool_floats - used) / J.slot_floats, (pq.partial_items - items) / J.nbt);
+      if (fit <= 0) break;
+      if (cl == ncl) {
+        jl[ncl++] = (int)j;
+        nbuf = J.pl.nbuf;
+      }
+      const int ns = (int)std::min<int64_t>(fit, J.t_end - t);
+      TcPiece pc{};
+      pc.cl = cl;
+      pc.ns = ns;
+      pc.slot0 = nslots;
+      pc.t0 = t;
+      pc.tile0 = tiles;
+      pc.item0 = items;
+      pc.nbt = J.nbt;
+      pc.gbuf = pool + used;
+      pc.shares = J.shares + (t - J.t_begin);
+      pcs.push_back(pc);
+      used += (int64_t)ns * J.slot_floats;
+      nslots += ns;
+      tiles += (int64_t)ns * J.tiles_per_triple;
+      items += (int64_t)ns * J.nbt;
+      t += ns;
+      const double kpad = 2.0 * J.pl.kw_chunks * J.pl.kw_elems + 2.0 * J.pl.ko_chunks * J.pl.ko_elems;
+      flops += 2.0 * nprod * (double)ns * J.tiles_per_triple * 128.0 * J.pl.NT * kpad;
+    }
+    if (pcs.empty()) {
+      st = fail(TE_ENOMEM, "G pool smaller than one triple's G blocks");
+      break;
+    }
+    size_t smem = 0;
+    st = gemm_params(h, jobs, jl, ncl, pcs.data(), (int)pcs.size(), tiles, mode, P, MS, &smem);
+    if (st != TE_OK) break;
+    std::memset(EL, 0, sizeof(*EL));
+    EL->ncl = ncl;
+    EL->npieces = (int)pcs.size();
+    EL->cw = cw;
+    EL->num_sms = h->num_sms;
+    EL->nslots = nslots;
+    EL->items = items;
+    for (int q = 0; q < ncl; ++q) {
+      const TcJob& J = jobs[jl[q]];
+      EL->cl[q] = EnergyCl{J.o, J.v, (int)energy_num_blocks(J.v), J.nbt, J.c->eps_o, J.c->eps_v};
+      EL->map_ovs[q] = &J.em.ovs;
+      EL->map_t1[q] = &J.em.t1;
+    }
+    for (size_t q = 0; q < pcs.size(); ++q) EL->pc[q] = pcs[q];
+    EL->triples = h->d_triples;
+    EL->partials = partials;
+    EL->err = h->d_err;
+    EL->wait_ns = h->wait_limit_ns;
+    if (h->log)
+      std::fprintf(stderr, "[tenergy] round: %d clusters, %zu pieces, %d triples, %lld tiles, %lld energy items\n",
+                   ncl, pcs.size(), nslots, (long long)tiles, (long long)items);
+    size_t pm = prof_begin(h, 0, s);
+    cudaError_t e = launch_gemm_any(mode, *MS, *P, smem, h->num_sms, s);
+    prof_end(h, pm, s);
+    h->gemm_flops += flops;
+    if (e == cudaSuccess) {
+      pm = prof_begin(h, 1, s);
+      e = launch_energy_tc(*EL, s);
+      prof_end(h, pm, s);
+    }
+    if (e == cudaSuccess) e = launch_reduce_pieces(partials, h->d_triples, pcs.data(), (int)pcs.size(), nslots, s);
+    h->n_launches += 3;
+    if (e != cudaSuccess) st = fail(TE_ECUDA, "tensor-core path launch: %s", cudaGetErrorString(e));
+  }
+  delete MS;
+  delete P;
+  delete EL;
+  if (st != TE_OK) return st;
+  for (const TcJob& J : jobs) {
+    if (!J.e_out) continue;
+    ++h->n_launches;
+    cudaError_t e = J.t_end > J.t_begin ? launch_reduce_total(J.shares, J.t_end - J.t_begin, J.e_out, s)
+                                        : cudaMemsetAsync(J.e_out, 0, sizeof(double), s);
+    if (e != cudaSuccess) return fail(TE_ECUDA, "reduction launch: %s", cudaGetErrorString(e));
+  }
+  return TE_OK;
+}
+
+// Plan, buffers (carved from base), operand preparation and maps of one job.
+static te_status setup_job(Handle* h, TcState* st, const te_cluster* c, int mode, int64_t t_begin, int64_t t_end,
+                           const TcPlan& pl, char* base, TcJob* J, cudaStream_t s) {
+  J->c = c;
+  J->pl = pl;
+  J->o = (int)c->nocc;
+  J->v = (int)c->nvir;
+  J->t_begin = t_begin;
+  J->t_end = t_end;
+  J->nbt = energy_num_block_triples(J->v);
+  J->slot_floats = g_slot_floats(J->v, pl.cw);
+  J->tiles_per_triple = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
+  tc_carve_cluster(base, pl, J->o, J->v, num_unique_triples(J->o), &J->b);
+  J->shares = J->b.etri;
+  const cudaError_t e = launch_prep_any(mode, c, pl, J->b, s);
+  h->n_launches += is_ozaki(mode) ? 7 : 5;
+  if (e != cudaSuccess) return fail(TE_ECUDA, "operand split launch: %s", cudaGetErrorString(e));
+  te_status rs = build_maps(st, pl, J->o, J->v, J->b, &J->maps);
+  if (rs != TE_OK) return rs;
+  return build_energy_maps(st, pl, J->o, J->v, J->b, &J->em);
+}
+
+static te_status check_k(int mode, int o, int v) {
+  // exact level-0/1 sums: K = 2 (v + o) products of at most 2^(2 beta) units stay below 2^24
+  if (mode == TC_OZAKI6 && 2 * (v + o) > OZ_K_MAX6)
+    return fail(TE_EUNSUPPORTED, "OZAKI mode needs 2 (nvir + nocc) <= %d for exact accumulation", OZ_K_MAX6);
+  if (mode == TC_OZAKI && 2 * (v + o) > OZ_K_MAX7)
+    return fail(TE_EUNSUPPORTED, "7-bit OZAKI slices need 2 (nvir + nocc) <= %d (use 6-bit slices)", OZ_K_MAX7);
+  return TE_OK;
+}
+
+static TcPool single_pool(const TcPlan& pl, int v) {
+  TcPool q;
+  q.pool_floats = (int64_t)pl.nslots * g_slot_floats(v, pl.cw);
+  q.partial_items = partial_items_of(q.pool_floats, pl.cw);
+  return q;
 }
 
 size_t tc_slices_bytes(int o, int v) {
@@ -999,11 +1302,10 @@ te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, cu
 }
 
 te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, size_t* bytes) {
-  const TcPlan pl = make_plan(h, (int)c->nocc, (int)c->nvir, tc_mode_of(p, (int)c->nocc, (int)c->nvir, h->ozaki_bits),
-                              num_unique_triples(c->nocc));
+  const int o = (int)c->nocc, v = (int)c->nvir;
+  const TcPlan pl = make_plan(h, o, v, tc_mode_of(p, o, v, h->ozaki_bits), num_unique_triples(c->nocc));
   TcBuffers b;
-  *bytes = tc_carve(nullptr, pl, c->nocc, c->nvir, energy_num_block_triples(c->nvir),
-                    num_unique_triples(c->nocc), &b);
+  *bytes = tc_carve_cluster(nullptr, pl, o, v, num_unique_triples(o), &b) + tc_shared_bytes(single_pool(pl, v));
   return TE_OK;
 }
 
@@ -1014,8 +1316,7 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
   const int o = (int)c->nocc, v = (int)c->nvir, mode = tc_mode_of(p, o, v, h->ozaki_bits);
   const auto key = std::make_tuple(o, v, mode);
   if (h->tuned.count(key)) return TE_OK;
-  if ((mode == TC_OZAKI6 && 2 * (v + o) > OZ_K_MAX6) || (mode == TC_OZAKI && 2 * (v + o) > OZ_K_MAX7))
-    return TE_OK;  // run_tc reports it
+  if (check_k(mode, o, v) != TE_OK) return TE_OK;  // run_tc reports it
   const int64_t nt = num_unique_triples(o);
   if (nt == 0) return TE_OK;
   // candidate M tiles: padding within 15% of the least; candidate N splits: the fewest and one more
@@ -1032,7 +1333,9 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
     const int64_t rows = (int64_t)round_up(v, TA) * round_up(v, TB);
     if (rows * 100 > best_rows * 115) continue;
     cand.emplace_back(TB, base.n_nt);
-    if (round_up((v + base.n_nt) / (base.n_nt + 1), 16) >= 64) cand.emplace_back(TB, base.n_nt + 1);
+    // one more N split: smaller N tiles re-read the A operand more often, but
+    // in the exact-slice modes N <= 80 double-buffers the accumulators
+    if (round_up((v + base.n_nt) / (base.n_nt + 1), 16) >= 32) cand.emplace_back(TB, base.n_nt + 1);
   }
   if (cand.size() <= 1) {
     if (!cand.empty()) h->tuned[key] = cand[0];
@@ -1048,12 +1351,11 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
   if (rs != TE_OK) return rs;
   rs = ensure_triples_public(h, o);
   if (rs != TE_OK) return rs;
-  const int64_t nbt = energy_num_block_triples(v);
   size_t need = 0;
   for (const auto& cd : cand) {
     const TcPlan pl = make_plan(h, o, v, mode, nt, cd.first, cd.second);
     TcBuffers b;
-    need = std::max(need, tc_carve(nullptr, pl, o, v, nbt, num_unique_triples(o), &b));
+    need = std::max(need, tc_carve_cluster(nullptr, pl, o, v, nt, &b) + tc_shared_bytes(single_pool(pl, v)));
   }
   rs = ensure_workspace_public(h, need);
   if (rs != TE_OK) return rs;
@@ -1064,56 +1366,65 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
   float best_ms = 1e30f;
   std::pair<int, int> best = cand[0];
   bool prepped = false;
+  std::vector<TcJob> jobs(1);
+  TcMapSet* MS = new TcMapSet;
+  TcParams* P = new TcParams;
   for (const auto& cd : cand) {
     const TcPlan pl = make_plan(h, o, v, mode, nt, cd.first, cd.second);
     if (pl.stages < 2) continue;
-    TcBuffers b;
-    tc_carve(wbase, pl, o, v, nbt, num_unique_triples(o), &b);
+    TcJob& J = jobs[0];
+    J = TcJob{};
+    J.c = c;
+    J.pl = pl;
+    J.o = o;
+    J.v = v;
+    J.nbt = energy_num_block_triples(v);
+    J.slot_floats = g_slot_floats(v, pl.cw);
+    J.tiles_per_triple = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
+    const size_t cbytes = tc_carve_cluster(wbase, pl, o, v, nt, &J.b);
     cudaError_t e = cudaSuccess;
     if (!prepped) {  // the operand planes sit first in the workspace for every candidate
-      if (mode == TC_BF16X3) e = launch_prep_tc<TC_BF16X3>(c, pl, b, s);
-      else if (mode == TC_TF32X3) e = launch_prep_tc<TC_TF32X3>(c, pl, b, s);
-      else if (mode == TC_TF32) e = launch_prep_tc<TC_TF32>(c, pl, b, s);
-      else if (mode == TC_OZAKI) e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
-      else e = launch_prep_tc<TC_OZAKI6>(c, pl, b, s);
+      e = launch_prep_any(mode, c, pl, J.b, s);
       prepped = true;
     }
-    TcMaps M;
-    if (e != cudaSuccess || build_maps(st, pl, o, v, b, &M) != TE_OK) continue;
-    TcParams P{};
-    P.o = o; P.v = v; P.TA = pl.TA; P.TB = pl.TB; P.NT = pl.NT;
-    P.n_mx = pl.n_mx; P.n_my = pl.n_my; P.n_nt = pl.n_nt;
-    P.kw_chunks = pl.kw_chunks; P.ko_chunks = pl.ko_chunks; P.kw_elems = pl.kw_elems; P.ko_elems = pl.ko_elems;
-    P.cbw = pl.cbw; P.cbo = pl.cbo; P.stages = pl.stages; P.stage_bytes = pl.stage_bytes;
-    P.a_part_bytes = pl.a_part_bytes; P.b_part_bytes = pl.b_part_bytes; P.tmem_cols = pl.tmem_cols;
-    P.triples = h->d_triples; P.gbuf = b.gbuf; P.ldz = pl.ldz; P.exps = b.exps; P.err = h->d_err;
-    P.wait_ns = h->wait_limit_ns; P.t0 = 0;
+    if (e != cudaSuccess || build_maps(st, pl, o, v, J.b, &J.maps) != TE_OK) continue;
     const int ns = (int)std::min<int64_t>(pl.nslots, nt);
-    P.total_tiles = 3LL * ns * pl.n_mx * pl.n_my * pl.n_nt;
+    TcPiece pc{};
+    pc.cl = 0;
+    pc.ns = ns;
+    pc.nbt = J.nbt;
+    pc.gbuf = reinterpret_cast<float*>(wbase + cbytes);
+    const int jl[1] = {0};
+    size_t smem = 0;
+    if (gemm_params(h, jobs, jl, 1, &pc, 1, (int64_t)ns * J.tiles_per_triple, mode, P, MS, &smem) != TE_OK) continue;
     float ms = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
       cudaEventRecord(e0, s);
-      if (mode == TC_BF16X3) e = launch_gemm_tc<TC_BF16X3>(h, M, P, pl.smem, s);
-      else if (mode == TC_TF32X3) e = launch_gemm_tc<TC_TF32X3>(h, M, P, pl.smem, s);
-      else if (mode == TC_TF32) e = launch_gemm_tc<TC_TF32>(h, M, P, pl.smem, s);
-      else if (mode == TC_OZAKI) e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
-      else e = launch_gemm_tc<TC_OZAKI6>(h, M, P, pl.smem, s);
+      e = launch_gemm_any(mode, *MS, *P, smem, h->num_sms, s);
       cudaEventRecord(e1, s);
       h->n_launches += 1;
       if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
-      float t = 0.f;
-      cudaEventElapsedTime(&t, e0, e1);
-      ms = std::min(ms, t / (float)ns);  // per triple
+      float tms = 0.f;
+      cudaEventElapsedTime(&tms, e0, e1);
+      ms = std::min(ms, tms / (float)ns);  // per triple
     }
+    if (h->log)
+      std::fprintf(stderr, "[tenergy] autotune nocc=%d nvir=%d mode=%d: TB=%d n_nt=%d %.4f ms per triple\n", o, v,
+                   mode, cd.first, cd.second, (double)ms);
     if (ms < best_ms) {
       best_ms = ms;
       best = cd;
     }
   }
+  delete MS;
+  delete P;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess) return fail(TE_ECUDA, "autotune launch failed");
   h->tuned[key] = best;
+  if (h->log)
+    std::fprintf(stderr, "[tenergy] autotune nocc=%d nvir=%d mode=%d: picked TB=%d n_nt=%d\n", o, v, mode,
+                 best.first, best.second);
   tune_save(h);
   return TE_OK;
 }
@@ -1129,115 +1440,126 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   const int o = (int)c->nocc, v = (int)c->nvir;
   const int mode = tc_mode_of(p, o, v, h->ozaki_bits);
   const int64_t ntri = num_unique_triples(o);
-  const int64_t nt = t_end - t_begin;
-  const TcPlan pl = make_plan(h, o, v, mode, nt);
+  const TcPlan pl = make_plan(h, o, v, mode, t_end - t_begin);
   if (pl.stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
-  // exact level-0/1 sums: K = 2 (v + o) products of at most 2^(2 beta) units stay below 2^24
-  if (mode == TC_OZAKI6 && 2 * (v + o) > OZ_K_MAX6)
-    return fail(TE_EUNSUPPORTED, "OZAKI mode needs 2 (nvir + nocc) <= %d for exact accumulation", OZ_K_MAX6);
-  if (mode == TC_OZAKI && 2 * (v + o) > OZ_K_MAX7)
-    return fail(TE_EUNSUPPORTED, "7-bit OZAKI slices need 2 (nvir + nocc) <= %d (use 6-bit slices)", OZ_K_MAX7);
-  const int64_t nbt = energy_num_block_triples(v);
+  rs = check_k(mode, o, v);
+  if (rs != TE_OK) return rs;
   TcBuffers b;
-  const size_t bytes = tc_carve(nullptr, pl, o, v, nbt, ntri, &b);
+  const TcPool pq = single_pool(pl, v);
+  const size_t cbytes = tc_carve_cluster(nullptr, pl, o, v, ntri, &b);
+  const size_t bytes = cbytes + tc_shared_bytes(pq);
+  if (h->log)
+    std::fprintf(stderr,
+                 "[tenergy] plan nocc=%d nvir=%d mode=%d: M tile %d x %d, N tile %d (%d per row block), %d stages "
+                 "of %u bytes, %d triples per launch, %u TMEM columns (%d accumulator sets), workspace %zu bytes\n",
+                 o, v, mode, pl.TA, pl.TB, pl.NT, pl.n_nt, pl.stages, pl.stage_bytes, pl.nslots, pl.tmem_cols,
+                 pl.nbuf, bytes);
   rs = ensure_workspace_public(h, bytes);
   if (rs != TE_OK) return rs;
   rs = ensure_triples_public(h, o);
   if (rs != TE_OK) return rs;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023));
-  tc_carve(base, pl, o, v, nbt, ntri, &b);
-
-  cudaError_t e;
-  if (mode == TC_BF16X3) e = launch_prep_tc<TC_BF16X3>(c, pl, b, s);
-  else if (mode == TC_TF32X3) e = launch_prep_tc<TC_TF32X3>(c, pl, b, s);
-  else if (mode == TC_TF32) e = launch_prep_tc<TC_TF32>(c, pl, b, s);
-  else if (mode == TC_OZAKI) e = launch_prep_tc<TC_OZAKI>(c, pl, b, s);
-  else e = launch_prep_tc<TC_OZAKI6>(c, pl, b, s);
-  h->n_launches += is_ozaki(mode) ? 8 : 6;
-  if (e != cudaSuccess) return fail(TE_ECUDA, "operand split launch: %s", cudaGetErrorString(e));
-
-  TcMaps M;
-  rs = build_maps(st, pl, o, v, b, &M);
+  std::vector<TcJob> jobs(1);
+  rs = setup_job(h, st, c, mode, t_begin, t_end, pl, base, &jobs[0], s);
   if (rs != TE_OK) return rs;
-  EnergyMapsHost EM;
-  rs = build_energy_maps(st, pl, o, v, pl.nslots, b, &EM);
-  if (rs != TE_OK) return rs;
+  if (e_tri_out) jobs[0].shares = e_tri_out;  // shares[t - t_begin]
+  else jobs[0].shares = jobs[0].b.etri;
+  jobs[0].e_out = e_total_out;
+  float* pool = reinterpret_cast<float*>(base + cbytes);
+  double* partials = reinterpret_cast<double*>(base + cbytes + (((size_t)pq.pool_floats * 4 + 1023) & ~size_t(1023)));
+  return run_rounds(h, jobs, mode, pool, pq, partials, s);
+}
 
-  TcParams P{};
-  P.o = o;
-  P.v = v;
-  P.TA = pl.TA;
-  P.TB = pl.TB;
-  P.NT = pl.NT;
-  P.n_mx = pl.n_mx;
-  P.n_my = pl.n_my;
-  P.n_nt = pl.n_nt;
-  P.kw_chunks = pl.kw_chunks;
-  P.ko_chunks = pl.ko_chunks;
-  P.kw_elems = pl.kw_elems;
-  P.ko_elems = pl.ko_elems;
-  P.cbw = pl.cbw;
-  P.cbo = pl.cbo;
-  P.stages = pl.stages;
-  P.stage_bytes = pl.stage_bytes;
-  P.a_part_bytes = pl.a_part_bytes;
-  P.b_part_bytes = pl.b_part_bytes;
-  P.tmem_cols = pl.tmem_cols;
-  P.triples = h->d_triples;
-  P.gbuf = b.gbuf;
-  P.ldz = pl.ldz;
-  P.exps = b.exps;
-  P.err = h->d_err;
-  P.wait_ns = h->wait_limit_ns;
+// Batches: every member's operands prepared up front, then rounds that mix
+// members (largest first), so the whole batch takes a few launches per round
+// instead of three per member per slot group.
+static constexpr int64_t BATCH_POOL_BYTES = int64_t(16) << 30;
 
-  EnergyLaunch EL{};
-  EL.o = o;
-  EL.v = v;
-  EL.cw = pl.cw;
-  EL.num_sms = h->num_sms;
-  EL.nbt = nbt;
-  EL.gbuf = b.gbuf;
-  EL.map_ovs = &EM.ovs;
-  EL.map_t1 = &EM.t1;
-  EL.triples = h->d_triples;
-  EL.eps_o = c->eps_o;
-  EL.eps_v = b.eps_copy;
-  EL.partials = b.partials;
-  EL.err = h->d_err;
-  EL.wait_ns = h->wait_limit_ns;
-
-  double* out = e_tri_out ? e_tri_out : b.etri;
-  const double nprod = (mode == TC_TF32) ? 1.0 : (mode == TC_OZAKI ? 10.0 : (mode == TC_OZAKI6 ? 15.0 : 3.0));
-  const double kpad = 2.0 * pl.kw_chunks * pl.kw_elems + 2.0 * pl.ko_chunks * pl.ko_elems;
-  for (int64_t t0 = t_begin; t0 < t_end; t0 += pl.nslots) {
-    const int ns = (int)std::min<int64_t>(pl.nslots, t_end - t0);
-    P.t0 = t0;
-    P.total_tiles = 3LL * ns * pl.n_mx * pl.n_my * pl.n_nt;
-    size_t pm = prof_begin(h, 0, s);
-    if (mode == TC_BF16X3) e = launch_gemm_tc<TC_BF16X3>(h, M, P, pl.smem, s);
-    else if (mode == TC_TF32X3) e = launch_gemm_tc<TC_TF32X3>(h, M, P, pl.smem, s);
-    else if (mode == TC_TF32) e = launch_gemm_tc<TC_TF32>(h, M, P, pl.smem, s);
-    else if (mode == TC_OZAKI) e = launch_gemm_tc<TC_OZAKI>(h, M, P, pl.smem, s);
-    else e = launch_gemm_tc<TC_OZAKI6>(h, M, P, pl.smem, s);
-    prof_end(h, pm, s);
-    h->gemm_flops += 2.0 * nprod * (double)P.total_tiles * 128.0 * pl.NT * kpad;
-    if (e == cudaSuccess) {
-      EL.nslots = ns;
-      EL.t0 = t0;
-      pm = prof_begin(h, 1, s);
-      e = launch_energy_tc(EL, s);
-      prof_end(h, pm, s);
-    }
-    if (e == cudaSuccess)
-      e = launch_reduce_triples(b.partials, energy_tc_grid(h->num_sms, (int64_t)ns * nbt) * ENERGY_TC_WARPS,
-                                h->d_triples, t0, ns, out + (t0 - t_begin), s);
-    h->n_launches += 3;
-    if (e != cudaSuccess) return fail(TE_ECUDA, "tensor-core path launch: %s", cudaGetErrorString(e));
+static TcPool batch_pool(Handle* h, const te_cluster* cs, int64_t n, int mode_p) {
+  int64_t need = 0, biggest = 0;
+  int cw = 1;
+  for (int64_t x = 0; x < n; ++x) {
+    const int o = (int)cs[x].nocc, v = (int)cs[x].nvir;
+    const int mode = tc_mode_of((te_precision)mode_p, o, v, h->ozaki_bits);
+    cw = is_ozaki(mode) ? 2 : 1;
+    const int64_t sf = g_slot_floats(v, cw);
+    need += num_unique_triples(o) * sf;
+    biggest = std::max(biggest, sf);
   }
-  if (e_total_out) {
-    ++h->n_launches;
-    e = launch_reduce_total(out, nt, e_total_out, s);
-    if (e != cudaSuccess) return fail(TE_ECUDA, "reduction launch: %s", cudaGetErrorString(e));
+  TcPool q;
+  q.pool_floats = std::max(biggest, std::min<int64_t>(need, BATCH_POOL_BYTES / 4));
+  q.partial_items = partial_items_of(q.pool_floats, cw);
+  return q;
+}
+
+te_status tc_batched_bytes(Handle* h, const te_cluster* cs, int64_t n, te_precision p, size_t* bytes) {
+  size_t b = 0;
+  for (int64_t x = 0; x < n; ++x) {
+    const int o = (int)cs[x].nocc, v = (int)cs[x].nvir;
+    const TcPlan pl = make_plan(h, o, v, tc_mode_of(p, o, v, h->ozaki_bits), num_unique_triples(o));
+    TcBuffers bb;
+    b += tc_carve_cluster(nullptr, pl, o, v, num_unique_triples(o), &bb);
+  }
+  *bytes = b + tc_shared_bytes(batch_pool(h, cs, n, (int)p)) + 1024;
+  return TE_OK;
+}
+
+te_status run_tc_batched(Handle* h, const te_cluster* cs, int64_t n, te_precision p, double* e_out, cudaStream_t s) {
+  if (h->cc_major != 10 && h->cc_major != 11)
+    return fail(TE_EUNSUPPORTED, "tensor-core modes need an sm_100-family GPU (found sm_%d%d)", h->cc_major,
+                h->cc_minor);
+  TcState* st = tc_state(h);
+  te_status rs = get_encoder(st);
+  if (rs != TE_OK) return rs;
+  size_t bytes = 0;
+  tc_batched_bytes(h, cs, n, p, &bytes);
+  rs = ensure_workspace_public(h, bytes);
+  if (rs != TE_OK) return rs;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023));
+  // longest first: the rounds' last pieces are the small members
+  std::vector<int64_t> order(n);
+  for (int64_t x = 0; x < n; ++x) order[x] = x;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    const double fa = (double)num_unique_triples(cs[a].nocc) * cs[a].nvir * cs[a].nvir * cs[a].nvir * (cs[a].nvir + cs[a].nocc);
+    const double fb = (double)num_unique_triples(cs[b].nocc) * cs[b].nvir * cs[b].nvir * cs[b].nvir * (cs[b].nvir + cs[b].nocc);
+    return fa > fb;
+  });
+  std::vector<TcJob> jobs;
+  std::vector<int> modes;
+  jobs.reserve(n);
+  size_t off = 0;
+  for (int64_t x : order) {
+    const int o = (int)cs[x].nocc, v = (int)cs[x].nvir;
+    const int mode = tc_mode_of(p, o, v, h->ozaki_bits);
+    rs = check_k(mode, o, v);
+    if (rs != TE_OK) return rs;
+    const int64_t nt = num_unique_triples(o);
+    if (nt == 0) {
+      if (cudaMemsetAsync(e_out + x, 0, sizeof(double), s) != cudaSuccess) return fail(TE_ECUDA, "memset failed");
+      ++h->n_launches;
+      continue;
+    }
+    const TcPlan pl = make_plan(h, o, v, mode, nt);
+    TcJob J;
+    rs = setup_job(h, st, cs + x, mode, 0, nt, pl, base + off, &J, s);
+    if (rs != TE_OK) return rs;
+    TcBuffers bb;
+    off += tc_carve_cluster(nullptr, pl, o, v, nt, &bb);
+    J.e_out = e_out + x;
+    jobs.push_back(J);
+    modes.push_back(mode);
+  }
+  const TcPool pq = batch_pool(h, cs, n, (int)p);
+  float* pool = reinterpret_cast<float*>(base + off);
+  double* partials = reinterpret_cast<double*>(base + off + (((size_t)pq.pool_floats * 4 + 1023) & ~size_t(1023)));
+  // one kernel per mode: the members of each slice width run in their own rounds
+  for (int mode : {TC_TF32, TC_BF16X3, TC_TF32X3, TC_OZAKI, TC_OZAKI6}) {
+    std::vector<TcJob> group;
+    for (size_t q = 0; q < jobs.size(); ++q)
+      if (modes[q] == mode) group.push_back(jobs[q]);
+    if (group.empty()) continue;
+    rs = run_rounds(h, group, mode, pool, pq, partials, s);
+    if (rs != TE_OK) return rs;
   }
   return TE_OK;
 }

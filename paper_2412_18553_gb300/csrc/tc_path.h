@@ -6,6 +6,12 @@ namespace te {
 te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin, int64_t t_end,
                  double* e_tri_out, double* e_total_out, cudaStream_t s);
 te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, size_t* bytes);
+// n clusters in rounds of multi-cluster launches (every member's operands
+// prepared first); e_out[x] = E(T) of cluster x.  tc_batched_bytes: the
+// workspace it needs (the tuned tile shapes must be known already).
+te_status tc_batched_bytes(Handle* h, const te_cluster* cs, int64_t n, te_precision p, size_t* bytes);
+te_status run_tc_batched(Handle* h, const te_cluster* cs, int64_t n, te_precision p, double* e_out,
+                         cudaStream_t s);
 void destroy_tc_state(Handle* h);
 // Time the candidate tile shapes of the contraction for this cluster's (nocc,
 // nvir, mode) on its first triples and remember the fastest in the handle.
