@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--vjp-triples", type=int, default=0,
                     help="time the adjoint of this many single-triple ranges of the workload itself "
                          "(both modes) and extrapolate; for clusters whose whole adjoint is too long")
+    ap.add_argument("--no-mp2", action="store_true",
+                    help="skip the MP2 step leg (amplitudes, 1-RDM, BNO populations of the 16-cluster batch)")
     ap.add_argument("--no-batch96", action="store_true",
                     help="skip the 96-cluster uneven batch leg (every --batch-stride-th seed timed, "
                          "extrapolated by flop count)")
@@ -224,27 +226,70 @@ def vjp_sample_leg(te, h, arrs, o, v, ntrip, world):
     out = {"triples": picks, "ntriples": nt}
     sample = {}
     gen = torch.Generator(device="cuda").manual_seed(11)
+
+    def top_entries(n, x, tt, k):
+        # the k largest entries; d ovvv is nonzero only in the triple's rows
+        # (one topk per row: a whole ovvv gradient can exceed 2^32 entries)
+        if n == "ovvv":
+            rows = sorted(set(_triple_of(tt, o)))
+            cand = torch.cat([x[p].reshape(-1).abs().topk(min(k, x[p].numel())).indices + p * x[p].numel()
+                              for p in rows])
+            return cand[x.view(-1)[cand].abs().argsort(descending=True)[:k]]
+        return x.view(-1).abs().topk(min(k, x.numel())).indices
+
+    def max_abs(n, x, tt):
+        if n == "ovvv":
+            return max(float(x[p].abs().max()) for p in set(_triple_of(tt, o)))
+        return float(x.abs().max())
+    grouped = False
     for prec in ("ozaki", "fp64"):
         ms, es, rel = 0.0, [], {}
         for tt in picks:
             torch.cuda.synchronize()
-            e0.record()
-            e, g = te.t_energy_vjp_triples(arrs, tt, tt + 1, precision=prec, handle=h)
-            e1.record()
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
+            try:
+                e0.record()
+                e, g = te.t_energy_vjp_triples(arrs, tt, tt + 1, precision=prec, handle=h)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+            except (torch.cuda.OutOfMemoryError, te.TEnergyError):
+                # all seven gradients do not fit beside the inputs and the
+                # workspace: ovvv's alone, then the rest (the time is the sum
+                # of the two calls, which repeats the recomputed G blocks)
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+                grouped = True
+                g = {}
+                for grp in (("ovvv",), tuple(n for n in te.NAMES if n != "ovvv")):
+                    e0.record()
+                    e, gg = te.t_energy_vjp_triples(arrs, tt, tt + 1, precision=prec, handle=h, grads=grp)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    for n, x in gg.items():
+                        flat = x.view(-1)
+                        if prec == "ozaki":
+                            k = min(2048, flat.numel())
+                            idx = torch.cat([top_entries(n, x, tt, k),
+                                             torch.randint(0, flat.numel(), (k,), device="cuda", generator=gen)])
+                            sample[(tt, n)] = (idx, flat[idx].clone())
+                        else:
+                            idx, vo = sample.pop((tt, n))
+                            scale = max(max_abs(n, x, tt), 1e-300)
+                            rel[n] = max(rel.get(n, 0.0), float((vo - flat[idx]).abs().max()) / scale)
+                    del gg
+                    torch.cuda.empty_cache()
             es.append(float(e))
             for n, x in g.items():
                 flat = x.view(-1)
                 if prec == "ozaki":
                     k = min(2048, flat.numel())
-                    top = flat.abs().topk(k).indices
                     rnd = torch.randint(0, flat.numel(), (k,), device="cuda", generator=gen)
-                    idx = torch.cat([top, rnd])
+                    idx = torch.cat([top_entries(n, x, tt, k), rnd])
                     sample[(tt, n)] = (idx, flat[idx].clone())
                 else:
                     idx, vo = sample.pop((tt, n))
-                    scale = max(float(flat.abs().max()), 1e-300)
+                    scale = max(max_abs(n, x, tt), 1e-300)
                     rel[n] = max(rel.get(n, 0.0), float((vo - flat[idx]).abs().max()) / scale)
             del e, g
             torch.cuda.empty_cache()
@@ -256,7 +301,22 @@ def vjp_sample_leg(te, h, arrs, o, v, ntrip, world):
     out["speedup_vs_fp64"] = out["fp64"]["ms_per_triple"] / out["ozaki"]["ms_per_triple"]
     out["dE_shares_ozaki_vs_fp64_ha"] = max(abs(a - b) for a, b in zip(out["ozaki"]["shares"], out["fp64"]["shares"]))
     out["extrapolated"] = True
+    out["gradients_in_two_calls"] = grouped
     return out
+
+
+def _triple_of(t, o):
+    """Canonical triple index -> (i, j, k) (i >= j >= k, i = j = k left out)."""
+    n = 0
+    for i in range(o):
+        for j in range(i + 1):
+            for k in range(j + 1):
+                if i == j == k:
+                    continue
+                if n == t:
+                    return (i, j, k)
+                n += 1
+    raise IndexError(t)
 
 
 def cpu_oracle_sample(arrs, o, v, ntrip, seconds_cap=40.0):
@@ -554,6 +614,41 @@ def main():
             frag["dE_ozaki_vs_fp64_ha"] = abs(frag["ozaki"]["e_frag_ha"] - frag["fp64"]["e_frag_ha"])
         del qa
 
+    # the MP2 step before (T): amplitudes, 1-RDM blocks and BNO populations of
+    # the 16-cluster batch (nocc 8..20, nvir = 8 nocc, naux = 4 (o + v))
+    mp2 = None
+    if not args.no_mp2:
+        import tegen
+        mcs = tegen.mp2_batch(range(16), rule="v8o")
+        mdev = [tuple(torch.as_tensor(x).to(torch.device("cuda", local)) for x in c) for c in mcs]
+        Fm = sum(te.mp2_flop_count(c[0].shape[0], c[1].shape[0], c[2].shape[0]) for c in mcs)
+        mp2 = {"workload": "16 clusters, seeds 0..15, nocc ~ U[8,20], nvir = 8 nocc, naux = 4(o+v): "
+                           "(ia|jb), t2, gamma_oo, gamma_vv, BNO populations"}
+        pops = {}
+        for mprec in ("ozaki", "fp64"):
+            res = te.mp2_bno_batched(mdev, mprec, handle=h)
+            torch.cuda.synchronize()
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            barrier()
+            l0 = h.profile_read(reset=False)["launches"]
+            m0.record()
+            reps = 3
+            for _ in range(reps):
+                res = te.mp2_bno_batched(mdev, mprec, handle=h)
+            m1.record()
+            torch.cuda.synchronize()
+            mms = m0.elapsed_time(m1) / reps
+            pops[mprec] = [r["pop_v"] for r in res]
+            mp2[mprec] = {"ms_per_batch": mms, "clusters_per_s": world * 16 / (mms / 1e3),
+                          "gflops": world * Fm / (mms / 1e3) / 1e9,
+                          "launches": (h.profile_read(reset=False)["launches"] - l0) // reps}
+        h.sync()
+        mp2["speedup_vs_fp64"] = mp2["fp64"]["ms_per_batch"] / mp2["ozaki"]["ms_per_batch"]
+        mp2["pop_v_max_rel_diff_ozaki_vs_fp64"] = max(
+            float((a - b).abs().max() / b.abs().max()) for a, b in zip(pops["ozaki"], pops["fp64"]))
+        del mdev, res
+
     pk, pk_src = peaks()
     if prec == "fp64":
         roof = None
@@ -606,6 +701,7 @@ def main():
                "speedup_vs_fp64": fp64["speedup_vs_fp64"] if fp64 else None,
                "batch16": batch,
                "batch96": b96,
+               "mp2": mp2,
                "vjp": vjp,
                "frag": frag,
                "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}

@@ -211,6 +211,49 @@ te_status t_energy_vjp_batched(te_handle h, const te_cluster* cs, int64_t n,
 te_status t_energy_frag(te_handle h, const te_cluster* c, const double* cf, te_precision p,
                         double* e_out, double* e_triples, te_stream_t s);
 
+/* ---------------------------------------------------------------------------
+ * The MP2 step before (T): amplitudes, one-body density, BNO populations
+ * (supplement section on bath-natural-orbital construction)
+ *
+ *   (ia|jb)  = sum_P Bov[P,i,a] Bov[P,j,b]
+ *   t_ij^ab  = -(ia|jb) / D_ij^ab,   D_ij^ab = e_a + e_b - e_i - e_j
+ *   gamma_ab = 2 sum_ij sum_c t_ij^ac (2 t_ij^bc - t_ij^cb)
+ *   gamma_ij = 2 delta_ij - 2 sum_k sum_ab t_ik^ab (2 t_jk^ab - t_jk^ba)
+ *
+ * and the BNO populations, the eigenvalues of gamma_oo and gamma_vv (the
+ * occupied-virtual block of the MP2 1-RDM is zero).  The t2 produced here is
+ * the t2 input of t_energy.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t nocc, nvir, naux;
+  const double *eps_o, *eps_v;  /* device [o], [v]; max(eps_o) < min(eps_v) */
+  const double *Bov;            /* device [naux][o][v]: the occupied-virtual block of the DF factor */
+} te_mp2_cluster;
+
+/* Outputs (device float64, caller-allocated, overwritten; a null member is
+ * not returned, but at least one must be set). */
+typedef struct {
+  double *t2;        /* [o][o][v][v]  t2[i,j,a,b] = t_ij^ab */
+  double *gamma_oo;  /* [o][o] */
+  double *gamma_vv;  /* [v][v] */
+  double *pop_o;     /* [o]  eigenvalues of gamma_oo, ascending */
+  double *pop_v;     /* [v]  eigenvalues of gamma_vv, ascending */
+} te_mp2_out;
+
+/* The MP2 step for n clusters (HOST arrays cs and outs of n entries each).
+ * p = TE_FP64 (every contraction on the DFMA units) or TE_OZAKI (the three
+ * (ia|jb) contraction in exact BF16 slices on the tensor cores, the density
+ * contractions in float64; outputs within about 2e-8 of their largest entry,
+ * so populations far below the largest are better taken from TE_FP64).  The
+ * eigenvalues come from a float64 Jacobi solver in
+ * either mode (nvir <= 4094).  Input values are checked on the device
+ * (finite, max eps_o < min eps_v; te_sync reports TE_EINVAL naming the
+ * array and the cluster).  Workspace: about 8 (4 o^2 v^2) bytes for the
+ * largest member in TE_FP64, plus its exact-slice copies and split-K partial
+ * tiles in TE_OZAKI.  Deterministic. */
+te_status t_mp2_bno_batched(te_handle h, const te_mp2_cluster* cs, const te_mp2_out* outs, int64_t n,
+                            te_precision p, te_stream_t s);
+
 /* Wait for the work of handle h on stream s and report a device-side
  * watchdog expiry (TE_ETIMEOUT) or an asynchronous CUDA error (TE_ECUDA). */
 te_status te_sync(te_handle h, te_stream_t s);

@@ -31,7 +31,8 @@ NAMES = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
 __all__ = ["Handle", "t_energy", "t_energy_triples", "t_energy_batched", "t_energy_vjp",
            "t_energy_vjp_triples", "t_energy_vjp_batched", "sync",
            "t_energy_fp64_noalloc", "t_energy_frag",
-           "TEnergy", "num_unique_triples", "flop_count", "TEnergyError", "NAMES"]
+           "TEnergy", "num_unique_triples", "flop_count", "TEnergyError", "NAMES",
+           "mp2_bno_batched", "mp2_flop_count"]
 
 
 def num_unique_triples(nocc: int) -> int:
@@ -248,13 +249,22 @@ def t_energy_batched(clusters, precision="fp64", handle=None, device=None, strea
     return out
 
 
-def t_energy_vjp(cluster, gE=1.0, precision="fp64", handle=None, device=None, stream=None):
-    """(E, grads): grads[name] = gE * dE/d(name) for all seven inputs."""
+def _grad_buffers(t, which):
+    names = NAMES if which is None else tuple(which)
+    for n in names:
+        if n not in NAMES:
+            raise ValueError(f"unknown input {n!r}")
+    return {n: torch.empty_like(t[n]) for n in names}
+
+
+def t_energy_vjp(cluster, gE=1.0, precision="fp64", handle=None, device=None, stream=None, grads=None):
+    """(E, grads): grads[name] = gE * dE/d(name) for all seven inputs, or for
+    the names listed in ``grads`` (the others are not computed)."""
     dev = _device_of(cluster, device)
     h = _handle(handle, dev)
     t = _tensors(cluster, dev)
-    grads = {n: torch.empty_like(t[n]) for n in NAMES}
-    g = TeClusterGrad(*(ctypes.c_void_p(grads[n].data_ptr()) for n in NAMES))
+    grads = _grad_buffers(t, grads)
+    g = _grad_struct(grads)
     e = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
     c = _struct(t)
     _lib.check(_lib.load().t_energy_vjp(h.ptr, ctypes.byref(c), _prec(precision), float(gE),
@@ -272,20 +282,21 @@ def sync(device=None, stream=None):
 
 
 def _grad_struct(grads):
-    return TeClusterGrad(*(ctypes.c_void_p(grads[n].data_ptr()) for n in NAMES))
+    return TeClusterGrad(*(ctypes.c_void_p(grads[n].data_ptr()) if n in grads else None for n in NAMES))
 
 
 def t_energy_vjp_triples(cluster, t_begin=0, t_end=None, gE=1.0, precision="fp64", handle=None, device=None,
-                         stream=None):
+                         stream=None, grads=None):
     """(sum of the shares of triples [t_begin, t_end), grads): the adjoint
     restricted to a canonical triple range; ranges that partition all
-    triples give gradients that add up to t_energy_vjp's."""
+    triples give gradients that add up to t_energy_vjp's.  ``grads``: the
+    inputs whose gradient is wanted (default all)."""
     dev = _device_of(cluster, device)
     h = _handle(handle, dev)
     t = _tensors(cluster, dev)
     if t_end is None:
         t_end = num_unique_triples(t["eps_o"].shape[0])
-    grads = {n: torch.empty_like(t[n]) for n in NAMES}
+    grads = _grad_buffers(t, grads)
     g = _grad_struct(grads)
     e = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
     c = _struct(t)
@@ -356,6 +367,51 @@ def t_energy_fp64_noalloc(cluster, device=None, stream=None) -> torch.Tensor:
         _lib.check(_lib.load().t_energy_fp64_noalloc(ctypes.byref(c), ctypes.c_void_p(out.data_ptr()),
                                                      _stream(dev, stream)))
     return out
+
+
+MP2_OUTPUTS = ("t2", "gamma_oo", "gamma_vv", "pop_o", "pop_v")
+
+
+def mp2_flop_count(nocc: int, nvir: int, naux: int) -> float:
+    """Flops of the MP2 step's three contractions: (ia|jb) (2 (ov)^2 naux),
+    gamma_vv (2 o^2 v^3) and gamma_oo (2 o^3 v^2)."""
+    o, v, P = float(nocc), float(nvir), float(naux)
+    return 2.0 * (o * v) ** 2 * P + 2.0 * o * o * v ** 3 + 2.0 * o ** 3 * v * v
+
+
+def mp2_bno_batched(clusters, precision="fp64", outputs=MP2_OUTPUTS, handle=None, device=None, stream=None):
+    """The MP2 step for a batch of clusters, each (eps_o [o], eps_v [v], Bov
+    [naux, o, v]): per cluster a dict with the requested ``outputs`` among
+    t2 [o,o,v,v], gamma_oo [o,o], gamma_vv [v,v], pop_o [o], pop_v [v]
+    (float64 CUDA tensors).  precision: "fp64" or "ozaki"."""
+    clusters = list(clusters)
+    for n in outputs:
+        if n not in MP2_OUTPUTS:
+            raise ValueError(f"unknown output {n!r}")
+    dev = device if device is not None else torch.cuda.current_device()
+    dev = torch.device(dev).index if not isinstance(dev, int) else dev
+    h = _handle(handle, dev)
+    d = torch.device("cuda", dev)
+    ins, outs, res = [], [], []
+    for c in clusters:
+        eo, ev, B = (torch.as_tensor(x, dtype=torch.float64).to(d).contiguous() for x in c)
+        o, v, P = eo.shape[0], ev.shape[0], B.shape[0]
+        if tuple(B.shape) != (P, o, v):
+            raise ValueError(f"Bov has shape {tuple(B.shape)}, expected ({P}, {o}, {v})")
+        shapes = dict(t2=(o, o, v, v), gamma_oo=(o, o), gamma_vv=(v, v), pop_o=(o,), pop_v=(v,))
+        r = {n: torch.empty(shapes[n], dtype=torch.float64, device=d) for n in outputs}
+        ins.append((eo, ev, B))
+        res.append(r)
+        outs.append(_lib.TeMp2Out(*(ctypes.c_void_p(r[n].data_ptr()) if n in r else None for n in MP2_OUTPUTS)))
+    n = len(clusters)
+    carr = (_lib.TeMp2Cluster * max(1, n))(*[_lib.TeMp2Cluster(eo.shape[0], ev.shape[0], B.shape[0],
+                                                                 ctypes.c_void_p(eo.data_ptr()),
+                                                                 ctypes.c_void_p(ev.data_ptr()),
+                                                                 ctypes.c_void_p(B.data_ptr()))
+                                               for eo, ev, B in ins])
+    oarr = (_lib.TeMp2Out * max(1, n))(*outs)
+    _lib.check(_lib.load().t_mp2_bno_batched(h.ptr, carr, oarr, n, _prec(precision), _stream(dev, stream)))
+    return res
 
 
 class TEnergy(torch.autograd.Function):

@@ -26,6 +26,16 @@ class TeClusterGrad(ctypes.Structure):
                 ("ooov", c_void_p), ("ovov", c_void_p), ("t1", c_void_p), ("t2", c_void_p)]
 
 
+class TeMp2Cluster(ctypes.Structure):
+    _fields_ = [("nocc", c_int64), ("nvir", c_int64), ("naux", c_int64),
+                ("eps_o", c_void_p), ("eps_v", c_void_p), ("Bov", c_void_p)]
+
+
+class TeMp2Out(ctypes.Structure):
+    _fields_ = [("t2", c_void_p), ("gamma_oo", c_void_p), ("gamma_vv", c_void_p),
+                ("pop_o", c_void_p), ("pop_v", c_void_p)]
+
+
 class TeProfile(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("gemm_launches", c_int64), ("gemm_ms", ctypes.c_double),
                 ("energy_launches", c_int64), ("energy_ms", ctypes.c_double),
@@ -62,6 +72,8 @@ SIGNATURES = [
     ("te_profile_enable", ctypes.c_int, [c_void_p, ctypes.c_int]),
     ("te_profile_read", ctypes.c_int, [c_void_p, ctypes.POINTER(TeProfile), ctypes.c_int]),
     ("t_energy_fp64_noalloc", ctypes.c_int, [ctypes.POINTER(TeCluster), c_void_p, c_void_p]),
+    ("t_mp2_bno_batched", ctypes.c_int, [c_void_p, ctypes.POINTER(TeMp2Cluster), ctypes.POINTER(TeMp2Out), c_int64,
+                                         ctypes.c_int, c_void_p]),
 ]
 
 _lib = None

@@ -21,6 +21,7 @@ constexpr unsigned long long EXP_MASK = 0x7FF0000000000000ull;
 struct CheckArgs {
   const unsigned long long* p[7];
   int64_t n[7];
+  unsigned int site[7];  // reported for a non-finite entry of array w
   const double* eps_o;
   const double* eps_v;
   int o, v;
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_check_inputs(const CheckArgs a, unsigne
       any |= nonfinite(x0) | nonfinite(x1) | nonfinite(x2) | nonfinite(x3);
     }
     for (; i < n; i += stride) any |= nonfinite(__ldg(q + i));
-    if (any && bad == 0) bad = (unsigned int)w + 1u;
+    if (any && bad == 0) bad = a.site[w];
   }
   if (bad) report(err, bad, a.cluster);
 
@@ -92,6 +93,7 @@ cudaError_t launch_check_inputs(const te_cluster* c, int64_t cluster, unsigned i
   for (int w = 0; w < 7; ++w) {
     a.p[w] = reinterpret_cast<const unsigned long long*>(ptr[w]);
     a.n[w] = n[w];
+    a.site[w] = (unsigned int)w + 1u;
     nmax = std::max(nmax, n[w]);
   }
   a.eps_o = c->eps_o;
@@ -100,6 +102,31 @@ cudaError_t launch_check_inputs(const te_cluster* c, int64_t cluster, unsigned i
   a.v = (int)v;
   a.cluster = (unsigned int)cluster;
   const int64_t want = (nmax + 4 * 256 - 1) / (4 * 256);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, 4LL * std::max(1, num_sms)));
+  k_check_inputs<<<grid, 256, 0, s>>>(a, err);
+  return cudaGetLastError();
+}
+
+// The MP2 step's inputs: eps_o (site 1), eps_v (site 2), the DF factor's ov
+// block (site 9), and the eps ordering (site 8).
+cudaError_t launch_check_mp2(const double* eps_o, int64_t o, const double* eps_v, int64_t v, const double* Bov,
+                             int64_t nB, int64_t cluster, unsigned int* err, int num_sms, cudaStream_t s) {
+  CheckArgs a{};
+  const double* ptr[3] = {eps_o, eps_v, Bov};
+  const int64_t n[3] = {o, v, nB};
+  const unsigned int site[3] = {1u, 2u, 9u};
+  for (int w = 0; w < 7; ++w) {
+    const int q = w < 3 ? w : 2;  // the unused entries repeat Bov with no elements
+    a.p[w] = reinterpret_cast<const unsigned long long*>(ptr[q]);
+    a.n[w] = w < 3 ? n[q] : 0;
+    a.site[w] = site[q];
+  }
+  a.eps_o = eps_o;
+  a.eps_v = eps_v;
+  a.o = (int)o;
+  a.v = (int)v;
+  a.cluster = (unsigned int)cluster;
+  const int64_t want = (nB + 4 * 256 - 1) / (4 * 256);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, 4LL * std::max(1, num_sms)));
   k_check_inputs<<<grid, 256, 0, s>>>(a, err);
   return cudaGetLastError();

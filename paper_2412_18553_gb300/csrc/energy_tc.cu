@@ -181,7 +181,7 @@ struct EnergyParams {
   EnergyCl cl[TC_MAX_CL];
   TcPiece pc[TC_MAX_PIECES];  // G: orbit-major [slot][bt][g][pid][CW planes][512, swizzled] from pc.gbuf
   const Triple* triples;
-  double* partials;  // [item]
+  double* partials;  // [global slot][grid][WARPS]: the warps' sums of a triple's items
   unsigned int* err;
   unsigned long long wait_ns;
 };
@@ -191,11 +191,27 @@ struct PieceTable {
   TcPiece pc[TC_MAX_PIECES];
 };
 
-// The piece holding launch item `it` (pieces are in item order).
-__device__ __forceinline__ int piece_of_item(const EnergyParams& P, int64_t it) {
-  int q = 0;
-  while (q + 1 < P.npieces && P.pc[q + 1].item0 <= it) ++q;
-  return q;
+// A block's items: for each piece, for each of its triples, the block
+// triples bt = blockIdx.x, blockIdx.x + gridDim.x, ... (< nbt), in order.
+// Which items of a triple a block takes, and in which order, depends on the
+// triple's nbt and the grid size alone (the grid is always one block per SM),
+// not on the launch's other pieces: a triple's float64 sums have the same bits
+// in a single-cluster call and in a batch.
+struct ItemCursor {
+  int q, ls;   // piece, triple slot within the piece
+  int64_t bt;  // block triple
+};
+
+__device__ __forceinline__ void cursor_settle(const EnergyParams& P, ItemCursor& c) {
+  while (c.q < P.npieces) {
+    const TcPiece& pc = P.pc[c.q];
+    if (c.bt < pc.nbt) return;
+    c.bt = blockIdx.x;  // no (more) items of this triple for this block
+    if (++c.ls >= pc.ns) {
+      c.ls = 0;
+      ++c.q;
+    }
+  }
 }
 
 template <int CW>
@@ -210,8 +226,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* empty = full + 2;                                         // [2], one arrival per compute warp
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + 2);
   int* meta = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag) + 1);  // [2][8]: X, Y, Z, slot, v, item
-  // [2][WARPS] warp sums of an item, 8-byte aligned after meta (full is 128-byte aligned: red sits at +104..+360)
-  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(meta + 2 * 8) + 7) & ~uintptr_t(7));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -229,7 +243,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t ephase = 0u, pending = 0u, fphase = 0u;  // one bit per buffer
     int b = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; ok && it < P.items; it += gridDim.x, b ^= 1) {
+    ItemCursor cur{0, 0, (int64_t)blockIdx.x};
+    cursor_settle(P, cur);
+    for (; ok && cur.q < P.npieces; cur.bt += gridDim.x, cursor_settle(P, cur), b ^= 1) {
       // buffer b free: all compute warps done with the item it held
       int good = 1;
       if (lane == 0) good = ptx::mbar_wait(&empty[b], ((ephase >> b) & 1u) ^ 1u, P.wait_ns) ? 1 : 0;
@@ -246,11 +262,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       ephase ^= 1u << b;
-      const TcPiece& pc = P.pc[piece_of_item(P, it)];
+      const TcPiece& pc = P.pc[cur.q];
       const EnergyCl& C = P.cl[pc.cl];
-      const int64_t local = it - pc.item0;
-      const int slot = (int)(local / C.nbt);
-      const int64_t bt = local % C.nbt;
+      const int slot = cur.ls;
+      const int64_t bt = cur.bt;
+      const int64_t local = (int64_t)slot * C.nbt + bt;
       int blk[3];
       decode_bt(bt, blk);
       const Triple tr = P.triples[pc.t0 + slot];
@@ -261,8 +277,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         meta[b * 8 + 2] = blk[2];
         meta[b * 8 + 3] = pc.slot0 + slot;
         meta[b * 8 + 4] = C.v;
-        meta[b * 8 + 5] = (int)(it >> 31);  // the item index, for this item's partials
-        meta[b * 8 + 6] = (int)(it & 0x7fffffff);
         ptx::mbar_arrive_expect_tx(&full[b], L::tx);  // first of the two arrivals
         pending |= 1u << b;
       }
@@ -334,7 +348,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       pos_off[n] = n * 512 + cube_off(u, w, z);
     }
     float* asmY = asmW + CW * 6 * 512;
-    for (int64_t it = blockIdx.x; it < P.items; it += gridDim.x, b ^= 1) {
+    // this thread's float64 sum over its items of the current triple slot; the
+    // warp's sum (fixed shuffle order) goes to the partials when the slot
+    // changes (a block takes a triple's items one after another)
+    double acc = 0.0;
+    int cur_slot = -1;
+    auto flush = [&]() {
+      double a = acc;
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if (lane == 0) P.partials[((int64_t)cur_slot * gridDim.x + blockIdx.x) * WARPS + warp] = a;
+      acc = 0.0;
+    };
+    ItemCursor cur{0, 0, (int64_t)blockIdx.x};
+    cursor_settle(P, cur);
+    for (; cur.q < P.npieces; cur.bt += gridDim.x, cursor_settle(P, cur), b ^= 1) {
       int got = 0;
       if (!*abort_flag) got = ptx::mbar_wait(&full[b], (phase >> b) & 1u, P.wait_ns) ? 1 : 0;
       if (!__all_sync(0xffffffffu, got)) {
@@ -348,10 +375,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       phase ^= 1u << b;
-      const int bx = meta[b * 8 + 0], by = meta[b * 8 + 1], bz = meta[b * 8 + 2];
-      const int vv = meta[b * 8 + 4];
-      const int64_t item = ((int64_t)meta[b * 8 + 5] << 31) | (int64_t)meta[b * 8 + 6];
-      double acc = 0.0;  // this thread's orbit of the item
+      const int bx = meta[b * 8 + 0], by = meta[b * 8 + 1], bz = meta[b * 8 + 2], slot = meta[b * 8 + 3];
+      const int vcl = meta[b * 8 + 4];
+      if (slot != cur_slot) {
+        if (cur_slot >= 0) flush();
+        cur_slot = slot;
+      }
       const unsigned char* base = smem + (size_t)b * L::buf;
       const float* cube = reinterpret_cast<const float*>(base);
       const float* ovsS = reinterpret_cast<const float*>(base + L::cubes);
@@ -392,7 +421,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
       // ---- phase B ----
       const int a = bx * TB + la, bb = by * TB + lb, c = bz * TB + lc;
-      const bool valid = a < vv && bb < vv && c < vv && !(bx == by && la < lb) && !(by == bz && lb < lc);
+      const bool valid = a < vcl && bb < vcl && c < vcl && !(bx == by && la < lb) && !(by == bz && lb < lc);
       if (valid) {
         // orbit weight A (Eq. E_corr_CCSD_T): 1, 1/2 or 1/6
         const bool all3 = (a == bb && bb == c), two = (a == bb || bb == c);
@@ -440,24 +469,19 @@ __global__ void __launch_bounds__(THREADS, 1)
           acc = fma(Tw, r1, acc);
         }
       }
-      // fixed-order sum of the item: warps, then the 16 warp sums in order
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) red[b * WARPS + warp] = acc;
       asm volatile("bar.sync 1, %0;" ::"n"(WARPS * 32) : "memory");  // assembled area free
-      if (warp == 0 && lane == 0) {  // red[b] is next written two items later, after two more barriers
-        double sum = 0.0;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) sum += red[b * WARPS + w];
-        P.partials[item] = sum;
-      }
     }
+    if (cur_slot >= 0) flush();
   }
   __syncthreads();
 }
 
 }  // namespace
 
-int64_t energy_tc_grid(int num_sms, int64_t items) { return std::min<int64_t>(items, (int64_t)num_sms); }
+int64_t energy_tc_grid(int num_sms, int64_t items) {
+  (void)items;  // one block per SM whatever the launch holds: the item-to-block map is fixed per triple
+  return std::max(1, num_sms);
+}
 
 size_t energy_tc_smem(int cw) {
   const size_t buf = cw == 2 ? Layout<2>::buf + Layout<2>::asm_bytes / 2 : Layout<1>::buf + Layout<1>::asm_bytes / 2;
@@ -484,7 +508,9 @@ cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   P.wait_ns = e.wait_ns;
   const size_t smem = energy_tc_smem(e.cw);
   const int64_t grid = energy_tc_grid(e.num_sms, P.items);
-  cudaError_t err;
+  // a block writes a slot's partials only if it took one of its items
+  cudaError_t err = cudaMemsetAsync(P.partials, 0, (size_t)e.nslots * grid * WARPS * sizeof(double), s);
+  if (err != cudaSuccess) return err;
   if (e.cw == 2) {
     err = cudaFuncSetAttribute(k_energy_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -497,9 +523,17 @@ cudaError_t launch_energy_tc(const EnergyLaunch& e, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// One block per G slot of the launch: the slot's partials in a fixed order
-// (Neumaier), times m/3, into its piece's share array.
-__global__ void __launch_bounds__(256) k_reduce_pieces(const double* __restrict__ partials,
+// One block per G slot of the launch: the slot's grid x WARPS partials summed
+// in a fixed order (thread t takes t, t + 256, ..., then a fixed tree, with
+// Neumaier compensation), times m/3, into its piece's shares.
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x)) c += (s - t) + x;
+  else c += (x - t) + s;
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) k_reduce_pieces(const double* __restrict__ partials, int nper,
                                                        const Triple* __restrict__ triples,
                                                        const __grid_constant__ PieceTable T) {
   const int gslot = blockIdx.x;
@@ -507,26 +541,18 @@ __global__ void __launch_bounds__(256) k_reduce_pieces(const double* __restrict_
   while (q + 1 < T.n && T.pc[q + 1].slot0 <= gslot) ++q;
   const TcPiece& pc = T.pc[q];
   const int local = gslot - pc.slot0;
-  const int64_t nper = pc.nbt;
-  const double* x = partials + pc.item0 + (int64_t)local * pc.nbt;
+  const double* x = partials + (int64_t)gslot * nper;
   __shared__ double ss[256], cc[256];
   double sum = 0.0, c = 0.0;
-  for (int64_t i = threadIdx.x; i < nper; i += blockDim.x) {
-    const double t = sum + x[i];
-    if (fabs(sum) >= fabs(x[i])) c += (sum - t) + x[i];
-    else c += (x[i] - t) + sum;
-    sum = t;
-  }
+  for (int i = threadIdx.x; i < nper; i += blockDim.x) neumaier(sum, c, x[i]);
   ss[threadIdx.x] = sum;
   cc[threadIdx.x] = c;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) {
       double s1 = ss[threadIdx.x], c1 = cc[threadIdx.x] + cc[threadIdx.x + w];
-      const double y = ss[threadIdx.x + w], t = s1 + y;
-      if (fabs(s1) >= fabs(y)) c1 += (s1 - t) + y;
-      else c1 += (y - t) + s1;
-      ss[threadIdx.x] = t;
+      neumaier(s1, c1, ss[threadIdx.x + w]);
+      ss[threadIdx.x] = s1;
       cc[threadIdx.x] = c1;
     }
     __syncthreads();
@@ -534,13 +560,13 @@ __global__ void __launch_bounds__(256) k_reduce_pieces(const double* __restrict_
   if (threadIdx.x == 0) pc.shares[local] = (ss[0] + cc[0]) * ((double)triples[pc.t0 + local].m / 3.0);
 }
 
-cudaError_t launch_reduce_pieces(const double* partials, const Triple* triples, const TcPiece* pieces,
-                                 int npieces, int nslots, cudaStream_t s) {
+cudaError_t launch_reduce_pieces(const double* partials, int nper, const Triple* triples,
+                                 const TcPiece* pieces, int npieces, int nslots, cudaStream_t s) {
   PieceTable T;
   std::memset(&T, 0, sizeof(T));
   T.n = npieces;
   for (int q = 0; q < npieces; ++q) T.pc[q] = pieces[q];
-  k_reduce_pieces<<<(unsigned)nslots, 256, 0, s>>>(partials, triples, T);
+  k_reduce_pieces<<<(unsigned)nslots, 256, 0, s>>>(partials, nper, triples, T);
   return cudaGetLastError();
 }
 

@@ -43,17 +43,18 @@ struct EnergyLaunch {
   const CUtensorMap* map_ovs[TC_MAX_CL];  // ovs32 [o][v][o][vq], 4D (b, j, a, i), box (8, 1, 8, 1)
   const CUtensorMap* map_t1[TC_MAX_CL];   // t1 [o][vq], 2D (a, i), box (8, 1)
   const Triple* triples;
-  double* partials;  // [items]: every item's fixed-order sum, all written
+  double* partials;  // [nslots][energy_tc_grid(num_sms, items)][ENERGY_TC_WARPS], zeroed by the launch
   unsigned int* err;
   unsigned long long wait_ns;
 };
 
 // Per-triple shares of every slot of a launch: shares[t] = (m_t / 3) times the
-// fixed-order sum of the slot's nbt item partials.  The order
-// depends on the cluster alone, not on the launch's other pieces, so a triple's
-// share is the same bits in a single-cluster call and in a batch.
-cudaError_t launch_reduce_pieces(const double* partials, const Triple* triples, const TcPiece* pieces,
-                                 int npieces, int nslots, cudaStream_t s);
+// fixed-order sum of the slot's nper = grid x ENERGY_TC_WARPS partials.  A
+// block takes the same items of a triple in the same order in any launch (the
+// grid is one block per SM), so a triple's share has the same bits in a
+// single-cluster call and in a batch.
+cudaError_t launch_reduce_pieces(const double* partials, int nper, const Triple* triples,
+                                 const TcPiece* pieces, int npieces, int nslots, cudaStream_t s);
 
 // Layout of one 8x8x8 G cube (shared by the contraction epilogue that writes it
 // and the energy kernel that reads it): element (u, w, z) of a plane sits at

@@ -85,8 +85,9 @@ static int grid_for(int64_t n) {
 
 cudaError_t launch_prep_fp64(const te_cluster* c, Prepared* P, cudaStream_t s) {
   const int o = (int)c->nocc, v = (int)c->nvir;
-  k_prep_t2L<<<grid_for((int64_t)o * v * v * o), 256, 0, s>>>(c->t2, P->t2L, o, v);
-  k_prep_nooT<<<grid_for((int64_t)o * o * v * o), 256, 0, s>>>(c->ooov, P->nooT, o, v);
+  // the tensor-core adjoint reads its own slice planes: no float64 t2L / nooT copies
+  if (P->t2L) k_prep_t2L<<<grid_for((int64_t)o * v * v * o), 256, 0, s>>>(c->t2, P->t2L, o, v);
+  if (P->nooT) k_prep_nooT<<<grid_for((int64_t)o * o * v * o), 256, 0, s>>>(c->ooov, P->nooT, o, v);
   k_prep_ovs<<<grid_for((int64_t)o * v * o * v), 256, 0, s>>>(c->ovov, P->ovs, P->ovs32, o, v);
   if (P->t1_32) k_to_f32<<<grid_for((int64_t)o * v), 256, 0, s>>>(c->t1, P->t1_32, (int64_t)o * v);
   return cudaGetLastError();

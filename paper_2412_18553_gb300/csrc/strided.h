@@ -111,6 +111,8 @@ cudaError_t gemm_strided(const GemmView& g, int num_sms, double* scratch, int64_
                          int64_t* launches);
 cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
                     int64_t* launches);
+// doubles of split-K scratch gemm_oz needs for an M x N output over K
+int64_t gemm_oz_scratch(int64_t M, int64_t N, int64_t K, int num_sms);
 // doubles of split-K scratch the two GEMMs need for a cluster's contractions
 int64_t splitk_cap(int64_t o, int64_t v);
 int64_t oz_scratch_cap(int64_t o, int64_t v, int num_sms);

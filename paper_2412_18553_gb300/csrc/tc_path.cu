@@ -286,6 +286,7 @@ struct TcParams {
   uint32_t a_part_bytes;   // 128 rows x cbw
   uint32_t tmem_cols;
   int nbuf;                // TMEM accumulator sets (1 or 2)
+  int rot;                 // exact-slice modes, N tiles <= 128: four rotating 128-column TMEM blocks
   int nt_max;              // largest N tile: stride of the accumulator sets
   int64_t total_tiles;
   const Triple* triples;
@@ -395,7 +396,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t* tfull = empty + P.stages;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* efree = drain + 1;  // rotation: a tile's level-0/1 blocks copied out (tempty: its level-2 block)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(efree + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -409,6 +411,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
       ptx::mbar_init(&tempty[a], GEMM_EPI_WARPS);
+      ptx::mbar_init(&efree[a], GEMM_EPI_WARPS);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t fmt = TF32 ? 2u : 1u;
-      uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
+      uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0, tile_n = 0;
       bool ok = true;
       bool issued = false;
       for (int64_t tt = blockIdx.x; ok && tt < P.total_tiles; tt += gridDim.x) {
@@ -497,7 +500,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const TcCl& C = P.cl[c.cl];
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(C.NT >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
-        if (*abort_flag || !ptx::mbar_wait(&tempty[acc], acc_phase ^ 1u, P.wait_ns)) {
+        // Rotation (P.rot): tile n keeps levels 0, 1, 2 in the 128-column blocks
+        // 3n, 3n+1, 3n+2 (mod 4).  Block 3n is tile n-2's level-2 block (free
+        // when its epilogue is done: tempty), blocks 3n+1 and 3n+2 are tile
+        // n-1's level-0/1 blocks (free once its epilogue copied them out:
+        // efree), so tile n starts while tile n-1's epilogue is still storing.
+        uint32_t b0 = 0, b1 = 0, b2 = 0;
+        if (P.rot) {
+          const uint32_t n = tile_n;
+          bool w = !*abort_flag;
+          if (w && n >= 1) w = ptx::mbar_wait(&efree[(n - 1) & 1], ((n - 1) >> 1) & 1u, P.wait_ns);
+          if (w && n >= 2) w = ptx::mbar_wait(&tempty[(n - 2) & 1], ((n - 2) >> 1) & 1u, P.wait_ns);
+          if (!w) {
+            if (!*abort_flag) record_abort(P, abort_flag, 2);
+            break;
+          }
+          b0 = 128u * ((3u * n) & 3u);
+          b1 = 128u * ((3u * n + 1u) & 3u);
+          b2 = 128u * ((3u * n + 2u) & 3u);
+        } else if (*abort_flag || !ptx::mbar_wait(&tempty[acc], acc_phase ^ 1u, P.wait_ns)) {
           if (!*abort_flag) record_abort(P, abort_flag, 2);
           break;
         }
@@ -532,7 +553,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               if constexpr (is_ozaki(MODE)) {
                 // slice products a_i b_j with i + j <= NPART - 1: level i + j = 0 and
                 // level 1 each in an exact accumulator, the higher levels in a third
-                const uint32_t d2 = d_tmem, d3 = d_tmem + C.NT, dr = d_tmem + 2 * C.NT;
+                const uint32_t d2 = P.rot ? tmem_base + b0 : d_tmem;
+                const uint32_t d3 = P.rot ? tmem_base + b1 : d_tmem + C.NT;
+                const uint32_t dr = P.rot ? tmem_base + b2 : d_tmem + 2 * C.NT;
                 ptx::mma<false>(d2, ad[0], bd[0], idesc, acc_in);
                 ptx::mma<false>(d3, ad[0], bd[1], idesc, acc_in);
                 ptx::mma<false>(d3, ad[1], bd[0], idesc, 1);
@@ -562,12 +585,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
         }
         if (!ok) break;
-        ptx::mma_commit(&tfull[acc]);
-        if (NBUF == 2) {
-          acc ^= 1u;
-          if (acc == 0) acc_phase ^= 1u;
+        if (P.rot) {
+          ptx::mma_commit(&tfull[tile_n & 1]);
+          ++tile_n;
         } else {
-          acc_phase ^= 1u;
+          ptx::mma_commit(&tfull[acc]);
+          if (NBUF == 2) {
+            acc ^= 1u;
+            if (acc == 0) acc_phase ^= 1u;
+          } else {
+            acc_phase ^= 1u;
+          }
         }
       }
       // every issued MMA completes before TMEM is released
@@ -581,13 +609,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int quad = warp & 3;
     const int chunk0 = (warp - 2) >> 2;  // this warp's first 16-column chunk
     const int row = quad * 32 + lane;
-    uint32_t acc = 0, acc_phase = 0;
+    uint32_t acc = 0, acc_phase = 0, tile_n = 0;
     for (int64_t tt = blockIdx.x; tt < P.total_tiles; tt += gridDim.x) {
       const TileCoord c = decode_tile(P, tt);
       const TcCl& C = P.cl[c.cl];
       const TcPiece& pc = P.pc[c.piece];
       int got = 0;
-      if (!*abort_flag) got = ptx::mbar_wait(&tfull[acc], acc_phase, P.wait_ns) ? 1 : 0;
+      if (!*abort_flag)
+        got = (P.rot ? ptx::mbar_wait(&tfull[tile_n & 1], (tile_n >> 1) & 1u, P.wait_ns)
+                     : ptx::mbar_wait(&tfull[acc], acc_phase, P.wait_ns))
+                  ? 1
+                  : 0;
       // the decision is warp-uniform: tcgen05.ld below is a .sync.aligned instruction
       if (!__all_sync(0xffffffffu, got)) {
         if (!*abort_flag && lane == 0) record_abort(P, abort_flag, 4);
@@ -606,6 +638,86 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       float* const gslot = pc.gbuf + (int64_t)c.slot * C.slot_floats;
       const int roff = cube_row(x & 7, y & 7);
       const int zx = cube_zx(x & 7, y & 7);
+      if constexpr (is_ozaki(MODE) && GEMM_EPI_GROUPS == 2) {
+        if (P.rot) {
+          // levels 0 and 1 of this warp's (at most four) chunks into registers,
+          // their blocks released; then level 2 chunk by chunk, combined, stored
+          const uint32_t lane_q = tmem_base + ((uint32_t)(quad * 32) << 16);
+          const uint32_t t0 = lane_q + 128u * ((3u * tile_n) & 3u);
+          const uint32_t t1 = lane_q + 128u * ((3u * tile_n + 1u) & 3u);
+          const uint32_t t2 = lane_q + 128u * ((3u * tile_n + 2u) & 3u);
+          // Held as s = fl(L0 + L1) and e = (L0 + L1) - s.  L0 and L1 are exact
+          // integer multiples of the level-1 unit 2^-3beta, |L0 + L1| < 2^13 in
+          // either slice width, so e is an integer number of units with |e| <=
+          // 128: two per register as int16, exactly.
+          constexpr float EU = (float)(1u << (3 * MT::beta)), EU_INV = 1.f / EU;
+          float sv[4][16];
+          uint32_t ev[4][8];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int c0 = 16 * chunk0 + 32 * k;
+            if (c0 < C.NT) {
+              float l0[16], l1[16];
+              ptx::tmem_ld16x2(t0 + c0, t1 + c0, l0, l1);
+#pragma unroll
+              for (int j = 0; j < 16; j += 2) {
+                float s0, e0, s1, e1;
+                two_sum(l0[j], l1[j], s0, e0);
+                two_sum(l0[j + 1], l1[j + 1], s1, e1);
+                sv[k][j] = s0;
+                sv[k][j + 1] = s1;
+                ev[k][j >> 1] = ((uint32_t)__float2int_rn(e0 * EU) & 0xffffu) | ((uint32_t)__float2int_rn(e1 * EU) << 16);
+              }
+            }
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&efree[tile_n & 1]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int c0 = 16 * chunk0 + 32 * k;
+            if (c0 >= C.NT) break;
+            float ar[16];
+            ptx::tmem_ld16(t2 + c0, ar);
+            if (!valid) continue;
+            const int z = c.z0 + c0;
+            float hv[16], lv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float s2 = sv[k][j];
+              const int eq = (j & 1) ? (int)ev[k][j >> 1] >> 16 : (int)(short)(ev[k][j >> 1] & 0xffffu);
+              const float e2 = (float)eq * EU_INV;
+              const float lo = __fadd_rn(e2, ar[j]);
+              const float hi = __fadd_rn(s2, lo);
+              hv[j] = hi * gscale;
+              lv[j] = __fsub_rn(lo, __fsub_rn(hi, s2)) * gscale;
+            }
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int Z = (z >> 3) + h2;
+              if (Z < nb) {
+                int64_t bt;
+                unsigned mask;
+                orbit_slots(x >> 3, y >> 3, Z, &bt, &mask);
+                xor_permute8(hv + 8 * h2, zx);
+                xor_permute8(lv + 8 * h2, zx);
+                float* item = gslot + (bt * 18 + c.g * 6) * (512 * CWF);
+                for (int pid = 0; pid < 6; ++pid) {
+                  if (!((mask >> pid) & 1u)) continue;
+                  float* cube = item + pid * (512 * CWF);
+                  store8(cube + roff, hv + 8 * h2);
+                  store8(cube + 512 + roff, lv + 8 * h2);
+                }
+              }
+            }
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&tempty[tile_n & 1]);
+          ++tile_n;
+          continue;
+        }
+      }
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * acc_stride;
       for (int c0 = 16 * chunk0; c0 < C.NT; c0 += 16 * GEMM_EPI_GROUPS) {
         const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
@@ -714,6 +826,12 @@ static te_status get_encoder(TcState* st) {
   return TE_OK;
 }
 
+// Exact-slice modes: N tiles of at most 128 columns in four rotating TMEM
+// blocks (the epilogue of one tile overlaps the next tile's MMAs)
+#ifndef TE_ROTATE_TILES
+#define TE_ROTATE_TILES 0
+#endif
+
 struct TcPlan {
   int mode, es, nparts, cw;
   int vp, op, vq;
@@ -722,6 +840,7 @@ struct TcPlan {
   int stages;
   uint32_t stage_bytes, a_part_bytes, b_part_bytes, tmem_cols;
   int nbuf;
+  int rot;
   int nslots;
   int ldz;
   size_t smem;
@@ -768,11 +887,13 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.TA = 128 / bestTB;
   pl.n_mx = (v + pl.TA - 1) / pl.TA;
   pl.n_my = (v + pl.TB - 1) / pl.TB;
-  const int ntmax = std::min(256, (512 / (nacc * nbuf_max)) / 16 * 16);
+  const int ntmax = (oz && TE_ROTATE_TILES) ? 128 : std::min(256, (512 / (nacc * nbuf_max)) / 16 * 16);
   pl.n_nt = (v + ntmax - 1) / ntmax;
-  if (force_nnt >= pl.n_nt) pl.n_nt = force_nnt;
+  // a tuned split: any count whose N tile fits three accumulators in TMEM (N <= 160)
+  if (force_nnt > 0 && round_up((v + force_nnt - 1) / force_nnt, 16) <= (oz ? 160 : 256)) pl.n_nt = force_nnt;
   pl.NT = round_up((v + pl.n_nt - 1) / pl.n_nt, 16);
-  pl.nbuf = (2 * nacc * pl.NT <= 512) ? 2 : 1;
+  pl.rot = (oz && TE_ROTATE_TILES && pl.NT <= 128) ? 1 : 0;
+  pl.nbuf = pl.rot ? 1 : ((2 * nacc * pl.NT <= 512) ? 2 : 1);
   pl.cbw = oz ? 64 : 128;
   pl.kw_elems = pl.cbw / pl.es;
   pl.kw_chunks = (pl.vp + pl.kw_elems - 1) / pl.kw_elems;
@@ -788,7 +909,7 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.smem = (size_t)pl.stages * pl.stage_bytes + 1024 + 256;
   uint32_t cols = 32;
   while (cols < (uint32_t)(nacc * pl.nbuf * pl.NT)) cols <<= 1;
-  pl.tmem_cols = cols;
+  pl.tmem_cols = pl.rot ? 512u : cols;
   pl.ldz = round_up(v, 4);
   const int64_t tiles = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
   int64_t want = (4LL * std::max(1, h->num_sms) + tiles - 1) / tiles;
@@ -849,19 +970,21 @@ static size_t tc_carve_cluster(char* base, const TcPlan& pl, int64_t o, int64_t 
   return (off + 1023) & ~size_t(1023);
 }
 
-// Energy items of a launch never exceed its G floats / (18 cubes x 512 x cw):
-// that bounds the partials (one double per item).
-static int64_t partial_items_of(int64_t pool_floats, int cw) { return pool_floats / (18 * 512 * cw) + 1; }
-
-// Workspace of one run: the clusters' parts, then the G pool, then the partials.
+// Workspace of one run: the clusters' parts, then the G pool, then the
+// energy partials: per G slot of a launch, one float64 sum per block (one
+// block per SM) and compute warp.
 struct TcPool {
   int64_t pool_floats;
-  int64_t partial_items;
+  int64_t max_slots;  // G slots per launch
 };
 
-static size_t tc_shared_bytes(const TcPool& q) {
+static size_t tc_partial_bytes(const TcPool& q, int num_sms) {
+  return (size_t)q.max_slots * std::max(1, num_sms) * ENERGY_TC_WARPS * sizeof(double);
+}
+
+static size_t tc_shared_bytes(const TcPool& q, int num_sms) {
   const size_t g = ((size_t)q.pool_floats * 4 + 1023) & ~size_t(1023);
-  return g + (size_t)q.partial_items * 8 + 1024;
+  return g + tc_partial_bytes(q, num_sms) + 1024;
 }
 
 static te_status encode(TcState* st, CUtensorMap* m, const void* base, CUtensorMapDataType dt, int rank,
@@ -1065,9 +1188,10 @@ static te_status gemm_params(const Handle* h, const std::vector<TcJob>& jobs, co
   if (P->stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
   P->nbuf = p0.nbuf;
   P->nt_max = nt_max;
+  P->rot = p0.rot;
   uint32_t cols = 32;
   while (cols < (uint32_t)(nacc * P->nbuf * nt_max)) cols <<= 1;
-  P->tmem_cols = cols;
+  P->tmem_cols = P->rot ? 512u : cols;
   P->total_tiles = tiles;
   P->triples = h->d_triples;
   P->err = h->d_err;
@@ -1114,14 +1238,14 @@ static te_status run_rounds(Handle* h, std::vector<TcJob>& jobs, int mode, float
       for (int q = 0; q < ncl; ++q)
         if (jl[q] == (int)j) cl = q;
       if (cl < 0) {
-        if (ncl == TC_MAX_CL || (nbuf >= 0 && J.pl.nbuf != nbuf)) break;
+        if (ncl == TC_MAX_CL || (nbuf >= 0 && J.pl.nbuf + 4 * J.pl.rot != nbuf)) break;
         cl = ncl;
       }
-      const int64_t fit = std::min((pq.pool_floats - used) / J.slot_floats, (pq.partial_items - items) / J.nbt);
+      const int64_t fit = std::min((pq.pool_floats - used) / J.slot_floats, pq.max_slots - nslots);
       if (fit <= 0) break;
       if (cl == ncl) {
         jl[ncl++] = (int)j;
-        nbuf = J.pl.nbuf;
+        nbuf = J.pl.nbuf + 4 * J.pl.rot;  // one TMEM scheme per launch
       }
       const int ns = (int)std::min<int64_t>(fit, J.t_end - t);
       TcPiece pc{};
@@ -1180,7 +1304,9 @@ static te_status run_rounds(Handle* h, std::vector<TcJob>& jobs, int mode, float
       e = launch_energy_tc(*EL, s);
       prof_end(h, pm, s);
     }
-    if (e == cudaSuccess) e = launch_reduce_pieces(partials, h->d_triples, pcs.data(), (int)pcs.size(), nslots, s);
+    if (e == cudaSuccess)
+      e = launch_reduce_pieces(partials, (int)(energy_tc_grid(h->num_sms, items) * ENERGY_TC_WARPS), h->d_triples,
+                               pcs.data(), (int)pcs.size(), nslots, s);
     h->n_launches += 3;
     if (e != cudaSuccess) st = fail(TE_ECUDA, "tensor-core path launch: %s", cudaGetErrorString(e));
   }
@@ -1232,7 +1358,7 @@ static te_status check_k(int mode, int o, int v) {
 static TcPool single_pool(const TcPlan& pl, int v) {
   TcPool q;
   q.pool_floats = (int64_t)pl.nslots * g_slot_floats(v, pl.cw);
-  q.partial_items = partial_items_of(q.pool_floats, pl.cw);
+  q.max_slots = pl.nslots;
   return q;
 }
 
@@ -1305,7 +1431,7 @@ te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, siz
   const int o = (int)c->nocc, v = (int)c->nvir;
   const TcPlan pl = make_plan(h, o, v, tc_mode_of(p, o, v, h->ozaki_bits), num_unique_triples(c->nocc));
   TcBuffers b;
-  *bytes = tc_carve_cluster(nullptr, pl, o, v, num_unique_triples(o), &b) + tc_shared_bytes(single_pool(pl, v));
+  *bytes = tc_carve_cluster(nullptr, pl, o, v, num_unique_triples(o), &b) + tc_shared_bytes(single_pool(pl, v), h->num_sms);
   return TE_OK;
 }
 
@@ -1333,9 +1459,12 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
     const int64_t rows = (int64_t)round_up(v, TA) * round_up(v, TB);
     if (rows * 100 > best_rows * 115) continue;
     cand.emplace_back(TB, base.n_nt);
-    // one more N split: smaller N tiles re-read the A operand more often, but
-    // in the exact-slice modes N <= 80 double-buffers the accumulators
+    // one more N split (smaller N tiles re-read the A operand more often), and
+    // in the exact-slice modes the fewer splits of 160-column tiles, which do
+    // not rotate their TMEM blocks
     if (round_up((v + base.n_nt) / (base.n_nt + 1), 16) >= 32) cand.emplace_back(TB, base.n_nt + 1);
+    const int n160 = (v + 159) / 160;
+    if (is_ozaki(mode) && n160 < base.n_nt) cand.emplace_back(TB, n160);
   }
   if (cand.size() <= 1) {
     if (!cand.empty()) h->tuned[key] = cand[0];
@@ -1355,7 +1484,7 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
   for (const auto& cd : cand) {
     const TcPlan pl = make_plan(h, o, v, mode, nt, cd.first, cd.second);
     TcBuffers b;
-    need = std::max(need, tc_carve_cluster(nullptr, pl, o, v, nt, &b) + tc_shared_bytes(single_pool(pl, v)));
+    need = std::max(need, tc_carve_cluster(nullptr, pl, o, v, nt, &b) + tc_shared_bytes(single_pool(pl, v), h->num_sms));
   }
   rs = ensure_workspace_public(h, need);
   if (rs != TE_OK) return rs;
@@ -1447,7 +1576,7 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   TcBuffers b;
   const TcPool pq = single_pool(pl, v);
   const size_t cbytes = tc_carve_cluster(nullptr, pl, o, v, ntri, &b);
-  const size_t bytes = cbytes + tc_shared_bytes(pq);
+  const size_t bytes = cbytes + tc_shared_bytes(pq, h->num_sms);
   if (h->log)
     std::fprintf(stderr,
                  "[tenergy] plan nocc=%d nvir=%d mode=%d: M tile %d x %d, N tile %d (%d per row block), %d stages "
@@ -1488,7 +1617,7 @@ static TcPool batch_pool(Handle* h, const te_cluster* cs, int64_t n, int mode_p)
   }
   TcPool q;
   q.pool_floats = std::max(biggest, std::min<int64_t>(need, BATCH_POOL_BYTES / 4));
-  q.partial_items = partial_items_of(q.pool_floats, cw);
+  q.max_slots = 2048;
   return q;
 }
 
@@ -1500,7 +1629,7 @@ te_status tc_batched_bytes(Handle* h, const te_cluster* cs, int64_t n, te_precis
     TcBuffers bb;
     b += tc_carve_cluster(nullptr, pl, o, v, num_unique_triples(o), &bb);
   }
-  *bytes = b + tc_shared_bytes(batch_pool(h, cs, n, (int)p)) + 1024;
+  *bytes = b + tc_shared_bytes(batch_pool(h, cs, n, (int)p), h->num_sms) + 1024;
   return TE_OK;
 }
 

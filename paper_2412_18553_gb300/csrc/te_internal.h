@@ -27,6 +27,10 @@ enum : unsigned int {
 // site (1..7 the array, 8 the eps ordering) and `cluster` in the error word.
 cudaError_t launch_check_inputs(const te_cluster* c, int64_t cluster, unsigned int* err, int num_sms,
                                 cudaStream_t s);
+// The same for the MP2 step's inputs (eps_o, eps_v, and the DF factor's ov
+// block of nB entries, site 9).
+cudaError_t launch_check_mp2(const double* eps_o, int64_t o, const double* eps_v, int64_t v, const double* Bov,
+                             int64_t nB, int64_t cluster, unsigned int* err, int num_sms, cudaStream_t s);
 
 // One occupied triple of the canonical unique list.
 struct Triple {

@@ -529,16 +529,28 @@ static cudaError_t launch_oz2(const OzView& g, dim3 grid, int kchunk, double* pa
   return cudaGetLastError();
 }
 
-// K in splits of at most OZ_KMAX (exactness), more when the output has few tiles
-cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
-                           int64_t* launches) {
-  const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
-  const int64_t tm = (M + OZ_BM - 1) / OZ_BM, tn = (g.N + OZ_BN - 1) / OZ_BN;
+// K in splits of at most OZ_KMAX (exactness), more when the output has few
+// tiles: the K chunk per split (a multiple of OZ_BK)
+static int oz_kchunk(int64_t M, int64_t N, int64_t K, int num_sms) {
+  const int64_t tm = (M + OZ_BM - 1) / OZ_BM, tn = (N + OZ_BN - 1) / OZ_BN;
   const int64_t steps = (K + OZ_BK - 1) / OZ_BK;
   int64_t ns = std::max<int64_t>((K + OZ_KMAX - 1) / OZ_KMAX, (2LL * num_sms + tm * tn - 1) / (tm * tn));
   ns = std::min<int64_t>(ns, std::max<int64_t>(1, steps / 4));
   ns = std::max<int64_t>(ns, (K + OZ_KMAX - 1) / OZ_KMAX);
-  const int kchunk = (int)(((steps + ns - 1) / ns) * OZ_BK);
+  return (int)(((steps + ns - 1) / ns) * OZ_BK);
+}
+
+int64_t gemm_oz_scratch(int64_t M, int64_t N, int64_t K, int num_sms) {
+  const int kchunk = oz_kchunk(M, N, K, num_sms);
+  const int64_t nsplit = (K + kchunk - 1) / kchunk;
+  return nsplit > 1 ? nsplit * M * N : 0;
+}
+
+cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
+                           int64_t* launches) {
+  const int64_t M = g.M1 * g.M2, K = g.K1 * g.K2;
+  const int64_t tm = (M + OZ_BM - 1) / OZ_BM, tn = (g.N + OZ_BN - 1) / OZ_BN;
+  const int kchunk = oz_kchunk(M, g.N, K, num_sms);
   const int nsplit = (int)((K + kchunk - 1) / kchunk);
   if (nsplit > 1 && (int64_t)nsplit * M * g.N > scratch_cap) return cudaErrorInvalidValue;
   dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)nsplit);
@@ -906,7 +918,7 @@ size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms) {
   const int64_t v3 = v * v * v, nt = num_unique_triples(o);
   const int64_t nblk = (v3 + 255) / 256;
   auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
-  return tc_slices_bytes((int)o, (int)v) + 1024 + a(o * v * v * o) + a(o * o * v * o) + a(o * v * o * v) +
+  return tc_slices_bytes((int)o, (int)v) + 1024 + a(o * v * o * v) +
          a(3 * v3) + 3 * a(v3) + a(v3) /* dW slices: 4 x 2 B */ + a(o * v * o * v) + 2 * a(nblk) +
          a(std::max<int64_t>(1, nt)) + a(oz_scratch_cap(o, v, num_sms)) + a(4) + 1024;
 }
@@ -930,8 +942,8 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
     return r;
   };
   VjpWork W;
-  W.t2L = take((int64_t)o * v * v * o);
-  W.nooT = take((int64_t)o * o * v * o);
+  W.t2L = nullptr;  // the contractions read the slice planes of t2L and nooT
+  W.nooT = nullptr;
   W.ovs = take((int64_t)o * v * o * v);
   W.G = take(3 * v3);
   W.dW = take(v3);

@@ -117,3 +117,75 @@ def test_o24v240_whole_cluster_exact_slice_within_1e7_of_float64():
         got = float(te.t_energy_triples(a, t, t + 1, precision="fp64", handle=h)[0])
         assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref)), (ijk, got, ref)
     h.sync()
+
+
+def test_o48v560_adjoint_on_a_sampled_triple():
+    """nocc=48 nvir=560 (seed 7): the adjoint of one canonical triple
+    (t_energy_vjp_triples) with exact-slice contractions against the float64
+    adjoint of the same triple, at each input's 64 largest float64 entries
+    and 64 seeded ones, within 1e-6 of the input's largest float64 magnitude;
+    and the float64 adjoint against central differences (step 1e-5) of the
+    float64 share at each input's two largest entries.  Gradients are asked
+    for in two groups (ovvv alone, then the rest) to keep the device's memory
+    within bounds: ovvv and its gradient are 67 GB each."""
+    te = need_gpu()
+    torch.cuda.empty_cache()
+    names = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
+    o, v, naux, seed = tegen.WORKLOADS["o48v560"]
+    cl = tegen.make_cluster(o, v, naux, seed, device="cuda")
+    a = {n: (x if isinstance(x, torch.Tensor) else torch.as_tensor(np.ascontiguousarray(x)).cuda())
+         for n, x in cl.arrays().items()}
+    del cl
+    torch.cuda.empty_cache()
+    tri = [(i, j, k) for i in range(o) for j in range(i + 1) for k in range(j + 1) if not (i == j == k)]
+    t = tri.index((40, 25, 3))
+    h = te.Handle(0)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    samples = {}
+
+    def pick(n, g):
+        # the 64 largest entries (within the three nonzero rows of d ovvv: a
+        # row has v^3 = 1.8e8 entries, while the whole tensor's 8.4e9 exceed
+        # what a single torch.topk handles) and 64 seeded entries
+        if n == "ovvv":
+            rows = sorted({40, 25, 3})
+            cand = torch.cat([g[p].reshape(-1).abs().topk(64).indices + p * g[p].numel() for p in rows])
+            top = cand[g.view(-1)[cand].abs().argsort(descending=True)[:64]]
+            mx = max(float(g[p].abs().max()) for p in rows)
+        else:
+            flat = g.view(-1)
+            top = flat.abs().topk(min(64, flat.numel())).indices
+            mx = float(flat.abs().max())
+        idx = torch.cat([top, torch.randint(0, g.numel(), (64,), device="cuda", generator=gen)])
+        return idx, g.view(-1)[idx].clone(), mx
+
+    for grp in (("ovvv",), tuple(n for n in names if n != "ovvv")):
+        e64, g64 = te.t_energy_vjp_triples(a, t, t + 1, precision="fp64", handle=h, grads=grp)
+        for n in grp:
+            samples[n] = pick(n, g64[n])
+        del g64
+        torch.cuda.empty_cache()
+        eoz, goz = te.t_energy_vjp_triples(a, t, t + 1, precision="ozaki", handle=h, grads=grp)
+        for n in grp:
+            idx, ref, mx = samples[n]
+            err = float((goz[n].view(-1)[idx] - ref).abs().max())
+            assert err <= 1e-6 * mx, (n, err, mx)
+        del goz
+        torch.cuda.empty_cache()
+    h.sync()
+    assert abs(float(eoz) - float(e64)) <= 1e-7, (float(eoz), float(e64))
+    step = 1e-5
+    for n in names:
+        idx, ref, mx = samples[n]
+        flat = a[n].view(-1)
+        for q in range(2):
+            i = idx[q:q + 1]
+            keep = flat[i].clone()
+            flat[i] = keep + step
+            ep = float(te.t_energy_triples(a, t, t + 1, precision="fp64", handle=h)[0])
+            flat[i] = keep - step
+            em = float(te.t_energy_triples(a, t, t + 1, precision="fp64", handle=h)[0])
+            flat[i] = keep
+            fd = (ep - em) / (2 * step)
+            assert abs(fd - float(ref[q])) <= 1e-6 * mx, (n, q, fd, float(ref[q]), mx)
+    h.sync()
