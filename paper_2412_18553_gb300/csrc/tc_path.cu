@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         // when its epilogue is done: tempty), blocks 3n+1 and 3n+2 are tile
         // n-1's level-0/1 blocks (free once its epilogue copied them out:
         // efree), so tile n starts while tile n-1's epilogue is still storing.
-        uint32_t b0 = 0, b1 = 0, b2 = 0;
+        uint32_t tb0 = 0, tb1 = 0, tb2 = 0;  // TMEM column offsets of the three levels
         if (P.rot) {
           const uint32_t n = tile_n;
           bool w = !*abort_flag;
@@ -515,9 +515,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             if (!*abort_flag) record_abort(P, abort_flag, 2);
             break;
           }
-          b0 = 128u * ((3u * n) & 3u);
-          b1 = 128u * ((3u * n + 1u) & 3u);
-          b2 = 128u * ((3u * n + 2u) & 3u);
+          tb0 = 128u * ((3u * n) & 3u);
+          tb1 = 128u * ((3u * n + 1u) & 3u);
+          tb2 = 128u * ((3u * n + 2u) & 3u);
         } else if (*abort_flag || !ptx::mbar_wait(&tempty[acc], acc_phase ^ 1u, P.wait_ns)) {
           if (!*abort_flag) record_abort(P, abort_flag, 2);
           break;
@@ -553,9 +553,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               if constexpr (is_ozaki(MODE)) {
                 // slice products a_i b_j with i + j <= NPART - 1: level i + j = 0 and
                 // level 1 each in an exact accumulator, the higher levels in a third
-                const uint32_t d2 = P.rot ? tmem_base + b0 : d_tmem;
-                const uint32_t d3 = P.rot ? tmem_base + b1 : d_tmem + C.NT;
-                const uint32_t dr = P.rot ? tmem_base + b2 : d_tmem + 2 * C.NT;
+                const uint32_t d2 = P.rot ? tmem_base + tb0 : d_tmem;
+                const uint32_t d3 = P.rot ? tmem_base + tb1 : d_tmem + C.NT;
+                const uint32_t dr = P.rot ? tmem_base + tb2 : d_tmem + 2 * C.NT;
                 ptx::mma<false>(d2, ad[0], bd[0], idesc, acc_in);
                 ptx::mma<false>(d3, ad[0], bd[1], idesc, acc_in);
                 ptx::mma<false>(d3, ad[1], bd[0], idesc, 1);
