@@ -60,6 +60,8 @@ class Cluster:
     t1: np.ndarray
     t2: np.ndarray
     meta: dict = field(default_factory=dict)
+    Bov: object = None  # [naux][o][v] density-fitting factor blocks (with_df=True)
+    Bvv: object = None  # [naux][v][v]
 
     def arrays(self):
         return dict(eps_o=self.eps_o, eps_v=self.eps_v, ovvv=self.ovvv,
@@ -119,11 +121,14 @@ def _ovvv_cuda(Bov, Bvv):
 
 
 def make_cluster(nocc: int, nvir: int, naux: int, seed: int, device: str = "cpu",
-                 rng=None, host_flop_limit: float = HOST_FLOP_LIMIT) -> Cluster:
+                 rng=None, host_flop_limit: float = HOST_FLOP_LIMIT, with_df: bool = False,
+                 form_ovvv: bool = True) -> Cluster:
     """Draw one synthetic cluster.  ``device="cuda"`` forms ovvv on the GPU
     (returned as a CUDA float64 tensor) when it costs more than
     ``host_flop_limit`` flops; smaller ones are formed on the host in FP64 and
-    returned as numpy arrays."""
+    returned as numpy arrays.  ``with_df`` attaches the factor blocks Bov
+    [naux][o][v] and Bvv [naux][v][v] (numpy, C-contiguous); ``form_ovvv=False``
+    leaves ovvv as None (the factors then stand for it)."""
     if rng is None:
         rng = np.random.default_rng(seed)
     eps_o, eps_v, B, t1 = _draw(nocc, nvir, naux, rng)
@@ -137,7 +142,9 @@ def make_cluster(nocc: int, nvir: int, naux: int, seed: int, device: str = "cpu"
           - eps_v[None, None, :, None] - eps_v[None, None, None, :])
     t2 = ovov.transpose(0, 2, 1, 3) / d2
     flops = 2.0 * o * v ** 3 * naux
-    if device == "cuda" and flops > host_flop_limit:
+    if not form_ovvv:
+        ovvv, how = None, "not formed"
+    elif device == "cuda" and flops > host_flop_limit:
         ovvv = _ovvv_cuda(Bov, Bvv)
         how = "gpu-split-bf16x3"
     else:
@@ -145,7 +152,8 @@ def make_cluster(nocc: int, nvir: int, naux: int, seed: int, device: str = "cpu"
         how = "host-fp64"
     return Cluster(o, v, eps_o, eps_v, ovvv, ooov, ovov, t1,
                    np.ascontiguousarray(t2),
-                   meta=dict(naux=naux, seed=seed, ovvv_formed=how))
+                   meta=dict(naux=naux, seed=seed, ovvv_formed=how),
+                   Bov=Bov if with_df else None, Bvv=Bvv if with_df else None)
 
 
 def mp2_inputs(nocc: int, nvir: int, naux: int, seed: int, rng=None):
