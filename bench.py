@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--check-triples", type=int, default=8,
                     help="triples checked against the FP64 GPU path for |dE|")
     ap.add_argument("--cpu-triples", type=int, default=2)
+    ap.add_argument("--batch96-df", action="store_true",
+                    help="run the 96-cluster batch leg through t_energy_df (each cluster given by its "
+                         "density-fitting factors; no ovvv formed anywhere)")
     ap.add_argument("--batch-stride", type=int, default=8,
                     help="with --workload batch96: time every s-th seed of the 96 (extrapolated by flop count)")
     ap.add_argument("--no-vjp", action="store_true",
@@ -59,6 +62,9 @@ def parse():
     ap.add_argument("--vjp-triples", type=int, default=0,
                     help="time the adjoint of this many single-triple ranges of the workload itself "
                          "(both modes) and extrapolate; for clusters whose whole adjoint is too long")
+    ap.add_argument("--no-df", action="store_true",
+                    help="skip the density-fitted leg (t_energy_df on this cluster: ovvv formed on the device "
+                         "from the DF factors)")
     ap.add_argument("--no-mp2", action="store_true",
                     help="skip the MP2 step leg (amplitudes, 1-RDM, BNO populations of the 16-cluster batch)")
     ap.add_argument("--no-batch96", action="store_true",
@@ -135,7 +141,50 @@ def make_workload(name, device):
     return (o, v, naux, seed), arrs
 
 
-def batch96_leg(te, h, prec, stride, local, fp64_seeds=1):
+def df_leg(te, h, arrs, o, v, naux, seed, prec, local, per_step_ms):
+    """t_energy_df on the workload's cluster: ovvv formed on the device from the
+    density-fitting factors Bov, Bvv of the same draw (no float64 ovvv read).
+    One warm call, then one CUDA-event-timed call.  Its E(T) is compared with
+    the same mode on the float64 DF product (a cuBLAS float64 GEMM, untimed):
+    that difference is the formation's alone.  (The timed step's ovvv is the
+    generator's split-BF16 GPU product, a slightly different input.)"""
+    import tegen
+    cl = tegen.make_cluster(o, v, naux, seed, with_df=True, form_ovvv=False)
+    dev = torch.device("cuda", local)
+    bov, bvv = torch.from_numpy(cl.Bov).to(dev), torch.from_numpy(cl.Bvv).to(dev)
+    del cl
+    a = {n: x for n, x in arrs.items() if n != "ovvv"}
+    te.t_energy_df(a, bov, bvv, prec, handle=h)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = h.profile_read(reset=False)["launches"]
+    e0.record()
+    edf = te.t_energy_df(a, bov, bvv, prec, handle=h)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = h.profile_read(reset=False)["launches"] - l0
+    out = {"workload": f"nocc={o} nvir={v} naux={naux} seed={seed}, ovvv from Bov [naux,o,v] and Bvv [naux,v,v]",
+           "precision": prec, "ms": ms, "gflops": te.flop_count(o, v) / (ms / 1e3) / 1e9, "e_t_ha": float(edf),
+           "time_vs_ovvv_input": ms / per_step_ms, "gpu_launches": launches,
+           "workspace_gb": h.df_workspace_bytes(o, v, naux, prec) / 1e9,
+           "float64_ovvv_gb_not_needed": o * v ** 3 * 8 / 1e9,
+           "factor_gb": naux * (o * v + v * v) * 8 / 1e9}
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free > 3 * o * v ** 3 * 8:
+        full = dict(a)
+        full["ovvv"] = (bov.reshape(naux, o * v).T @ bvv.reshape(naux, v * v)).reshape(o, v, v, v).contiguous()
+        e_same = float(te.t_energy(full, prec, handle=h))
+        out["dE_vs_same_mode_on_float64_df_product_ha"] = abs(float(edf) - e_same)
+        del full
+    h.sync()
+    del bov, bvv
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch96_leg(te, h, prec, stride, local, fp64_seeds=1, df=False):
     """The 96-cluster uneven batch (seeds 0..95: nocc ~ [10,40], nvir = round(nocc
     U[8,12]), naux = 4 (o + v)).  Its float64 ovvv totals 709 GB, more than one
     GPU (or the host) holds, so clusters are formed one after another on the
@@ -143,7 +192,10 @@ def batch96_leg(te, h, prec, stride, local, fp64_seeds=1):
     is timed on its own after an untimed call that warms and tunes it.  Seeds 0,
     s, 2s, ... are timed; clusters/s of the whole batch is extrapolated by flop
     count and says so.  The float64 GPU path is timed the same way on the
-    ``fp64_seeds`` timed seeds of least work, with |dE| of those clusters."""
+    ``fp64_seeds`` timed seeds of least work, with |dE| of those clusters.
+    With ``df``, no ovvv exists at all: each cluster is given by its
+    density-fitting factors and timed through t_energy_df; the float64
+    reference then runs on the float64 DF product (untimed cuBLAS GEMM)."""
     import tegen
     seeds = list(range(0, 96, max(1, stride)))
     F_all = sum(te.flop_count(*tegen.batch_sizes(s)[:2]) for s in range(96))
@@ -153,23 +205,37 @@ def batch96_leg(te, h, prec, stride, local, fp64_seeds=1):
     f64_ms, f64_F, dE = 0.0, 0.0, []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    dev = torch.device("cuda", local)
     for s in seeds:
-        c = tegen.make_batch([s], rule="uneven", device="cuda", host_flop_limit=0.0)[0]
+        if df:
+            o_, v_, naux_, rng = tegen.batch_sizes(s, "uneven")
+            c = tegen.make_cluster(o_, v_, naux_, s, rng=rng, with_df=True, form_ovvv=False)
+            bov, bvv = torch.from_numpy(c.Bov).to(dev), torch.from_numpy(c.Bvv).to(dev)
+        else:
+            c = tegen.make_batch([s], rule="uneven", device="cuda", host_flop_limit=0.0)[0]
         a = {n: (x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))).to(
-            torch.device("cuda", local)).contiguous() for n, x in c.arrays().items()}
+            dev).contiguous() for n, x in c.arrays().items() if x is not None}
         del c
         torch.cuda.empty_cache()
-        te.t_energy(a, prec, handle=h)
+
+        def run():
+            return te.t_energy_df(a, bov, bvv, prec, handle=h) if df else te.t_energy(a, prec, handle=h)
+        run()
         torch.cuda.synchronize()
         l0 = h.profile_read(reset=False)["launches"]
         e0.record()
-        eb = te.t_energy(a, prec, handle=h)
+        eb = run()
         e1.record()
         torch.cuda.synchronize()
         tot_ms += e0.elapsed_time(e1)
         launches += h.profile_read(reset=False)["launches"] - l0
         F_run += F_of[s]
         if s in f64_pick:
+            if df:
+                naux_ = bov.shape[0]
+                o_, v_ = a["t1"].shape
+                a["ovvv"] = (bov.reshape(naux_, o_ * v_).T @ bvv.reshape(naux_, v_ * v_)).reshape(
+                    o_, v_, v_, v_).contiguous()
             e0.record()
             e64 = te.t_energy(a, "fp64", handle=h)
             e1.record()
@@ -178,10 +244,13 @@ def batch96_leg(te, h, prec, stride, local, fp64_seeds=1):
             f64_F += F_of[s]
             dE.append({"seed": s, "dE_ha": abs(float(eb) - float(e64)), "e_t_ha": float(e64)})
         del a
+        if df:
+            del bov, bvv
         torch.cuda.empty_cache()
     h.sync()
     t_all = tot_ms / 1e3 * (F_all / F_run)
-    out = {"workload": "batch96: seeds 0..95, nocc ~ [10,40], nvir = round(nocc U[8,12]), naux = 4(o+v)",
+    out = {"workload": "batch96: seeds 0..95, nocc ~ [10,40], nvir = round(nocc U[8,12]), naux = 4(o+v)"
+                       + ("; ovvv formed on the device from Bov, Bvv (t_energy_df)" if df else ""),
            "precision": prec, "clusters_per_s": 96.0 / t_all, "gflops": F_run / (tot_ms / 1e3) / 1e9,
            "timed_seeds": seeds, "seconds_timed": tot_ms / 1e3, "flop_batch": F_all, "flop_timed": F_run,
            "extrapolated": len(seeds) < 96, "gpu_launches": launches}
@@ -201,7 +270,7 @@ def run_batch96(args):
     torch.cuda.set_device(local)
     h = te.Handle(local)
     clocks = Clocks(local)
-    leg = batch96_leg(te, h, args.precision, args.batch_stride, local)
+    leg = batch96_leg(te, h, args.precision, args.batch_stride, local, df=args.batch96_df)
     clk = clocks.stop()
     out = {"metric": "clusters/s of the 96-cluster uneven batch", "value": leg["clusters_per_s"],
            "unit": "clusters/s", "n_gpus": 1, "higher_is_better": True, "clocks": clk,
@@ -466,6 +535,11 @@ def main():
         fp64 = {"ms": fms, "gflops": F / (fms / 1e3) / 1e9, "e_t_ha": float(e64),
                 "dE_total_vs_fp64_ha": abs(e_val - float(e64)), "speedup_vs_fp64": fms / per_step}
 
+    # ovvv formed on the device from the density-fitting factors
+    dfl = None
+    if not args.no_df and prec != "fp64" and world == 1:
+        dfl = df_leg(te, h, arrs, o, v, naux, seed, prec, local, per_step)
+
     # end to end through the public API with host (pinned) buffers
     e2e = None
     if not args.no_e2e:
@@ -534,7 +608,7 @@ def main():
     # the 96-cluster uneven batch: a timed subset of seeds, extrapolated by flop count
     b96 = None
     if not args.no_batch96 and world == 1:
-        b96 = batch96_leg(te, h, prec, args.batch_stride, local)
+        b96 = batch96_leg(te, h, prec, args.batch_stride, local, df=args.batch96_df)
 
     # adjoint on a sample of triples of this cluster (when the whole-cluster
     # adjoint is too long to run here: every triple does the same contraction
@@ -701,6 +775,7 @@ def main():
                "speedup_vs_fp64": fp64["speedup_vs_fp64"] if fp64 else None,
                "batch16": batch,
                "batch96": b96,
+               "df": dfl,
                "mp2": mp2,
                "vjp": vjp,
                "frag": frag,

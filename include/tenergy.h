@@ -212,6 +212,55 @@ te_status t_energy_frag(te_handle h, const te_cluster* c, const double* cf, te_p
                         double* e_out, double* e_triples, te_stream_t s);
 
 /* ---------------------------------------------------------------------------
+ * E(T) with the (ov|vv) block formed on the fly from density-fitting factors
+ * (the integrals of the clusters are density-fitted, (pq|rs) = sum_P B[P,p,q]
+ * B[P,r,s]; by the supplement's remark on the divisibility of the (T)
+ * contraction, the energy never needs a whole six-index tensor, and with
+ * these factors it needs no float64 ovvv either)
+ *
+ *   ovvv[i,a,b,d] = sum_P Bov[P,i,a] Bvv[P,b,d]
+ *
+ * The slabs ovvv[i] are formed in groups on the tensor cores (Bov and Bvv cut
+ * into five 7-bit BF16 slices with one power-of-two scale each, fifteen slice
+ * products with exact level-0/1 sums over K blocks of at most 1024, float64
+ * across blocks: each entry within naux 2^(ea + eb - 34) of the float64
+ * product, where 2^ea > max |Bov| and 2^eb > max |Bvv|) and written straight
+ * into the contraction's operand form.  The
+ * exact-slice modes need max |ovvv| before slicing, so the slabs are formed
+ * twice (once for the maximum, once for the slices); the two passes give the
+ * same bits.  No float64 ovvv is allocated or read.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t naux;
+  const double *Bov;  /* device [naux][nocc][nvir], float64, C-contiguous */
+  const double *Bvv;  /* device [naux][nvir][nvir], float64, C-contiguous */
+} te_df;
+
+/* E(T) of one cluster whose ovvv comes from df (c->ovvv is not read and may
+ * be NULL; the other arrays as for t_energy).  p: a tensor-core mode
+ * (TE_OZAKI, TE_BF16X3, TE_TF32X3, TE_TF32); TE_FP64 gives TE_EUNSUPPORTED.
+ * The result equals t_energy's with ovvv = the float64 DF product, within the
+ * mode's accuracy class.  Input values (including Bov and Bvv) are checked on
+ * the device and reported by te_sync.  Workspace: the contraction operands of
+ * t_energy (about 8 nocc nvir^3 bytes of ovvv slices in TE_OZAKI) plus the
+ * larger of the G pool and the formation's scratch (five slices of Bov and
+ * Bvv, 10 naux (nocc nvir + nvir^2) bytes, and a staging block of at most
+ * 2 GiB of float64 slabs); te_df_workspace_bytes gives it.  Asynchronous,
+ * deterministic. */
+te_status t_energy_df(te_handle h, const te_cluster* c, const te_df* df, te_precision p, double* e_out,
+                      te_stream_t s);
+
+/* The per-triple shares of [t_begin, t_end) (t_energy_triples' canonical
+ * order) with ovvv from df; as t_energy_df otherwise. */
+te_status t_energy_df_triples(te_handle h, const te_cluster* c, const te_df* df, te_precision p,
+                              int64_t t_begin, int64_t t_end, double* e_triples, te_stream_t s);
+
+/* Device bytes of workspace t_energy_df needs for this cluster, factors and
+ * mode (only the sizes are read). */
+te_status te_df_workspace_bytes(te_handle h, const te_cluster* c, const te_df* df, te_precision p,
+                                size_t* bytes);
+
+/* ---------------------------------------------------------------------------
  * The MP2 step before (T): amplitudes, one-body density, BNO populations
  * (supplement section on bath-natural-orbital construction)
  *

@@ -24,13 +24,13 @@ import os
 import torch
 
 from . import _lib
-from ._lib import PRECISIONS, TEnergyError, TeCluster, TeClusterGrad
+from ._lib import PRECISIONS, TEnergyError, TeCluster, TeClusterGrad, TeDf
 
 NAMES = ("eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2")
 
 __all__ = ["Handle", "t_energy", "t_energy_triples", "t_energy_batched", "t_energy_vjp",
            "t_energy_vjp_triples", "t_energy_vjp_batched", "sync",
-           "t_energy_fp64_noalloc", "t_energy_frag",
+           "t_energy_fp64_noalloc", "t_energy_frag", "t_energy_df", "t_energy_df_triples",
            "TEnergy", "num_unique_triples", "flop_count", "TEnergyError", "NAMES",
            "mp2_bno_batched", "mp2_flop_count"]
 
@@ -135,6 +135,16 @@ class Handle:
                                                   ctypes.byref(out)))
         return int(out.value)
 
+    def df_workspace_bytes(self, nocc: int, nvir: int, naux: int, precision="ozaki") -> int:
+        """Workspace bytes t_energy_df needs for these sizes."""
+        c = _lib.TeCluster()
+        c.nocc, c.nvir = int(nocc), int(nvir)
+        df = TeDf(int(naux), None, None)
+        out = ctypes.c_size_t()
+        _lib.check(_lib.load().te_df_workspace_bytes(self.ptr, ctypes.byref(c), ctypes.byref(df), _prec(precision),
+                                                     ctypes.byref(out)))
+        return int(out.value)
+
 
 _DEFAULT = {}
 
@@ -172,11 +182,13 @@ def _as_dict(cluster):
     raise TypeError("cluster must be a dict, a 7-tuple or an object with .arrays()")
 
 
-def _tensors(cluster, device):
+def _tensors(cluster, device, skip=()):
     d = _as_dict(cluster)
     dev = torch.device("cuda", device)
     out = {}
     for n in NAMES:
+        if n in skip:
+            continue
         x = d[n]
         t = x if isinstance(x, torch.Tensor) else torch.as_tensor(x)
         if t.dtype != torch.float64:
@@ -188,6 +200,8 @@ def _tensors(cluster, device):
     want = dict(eps_o=(o,), eps_v=(v,), ovvv=(o, v, v, v), ooov=(o, o, o, v), ovov=(o, v, o, v),
                 t1=(o, v), t2=(o, o, v, v))
     for n, shp in want.items():
+        if n in skip:
+            continue
         if tuple(out[n].shape) != shp:
             raise ValueError(f"{n} has shape {tuple(out[n].shape)}, expected {shp}")
     return out
@@ -195,14 +209,14 @@ def _tensors(cluster, device):
 
 def _struct(t):
     return TeCluster(t["eps_o"].shape[0], t["eps_v"].shape[0],
-                     *(ctypes.c_void_p(t[n].data_ptr()) for n in NAMES))
+                     *(ctypes.c_void_p(t[n].data_ptr() if n in t else None) for n in NAMES))
 
 
 def _device_of(cluster, device):
     if device is not None:
         return torch.device(device).index if not isinstance(device, int) else device
     for n in NAMES:
-        x = _as_dict(cluster)[n]
+        x = _as_dict(cluster).get(n)
         if isinstance(x, torch.Tensor) and x.is_cuda:
             return x.device.index
     return torch.cuda.current_device()
@@ -233,6 +247,53 @@ def t_energy_triples(cluster, t_begin=0, t_end=None, precision="fp64", handle=No
     _lib.check(_lib.load().t_energy_triples(h.ptr, ctypes.byref(c), _prec(precision), int(t_begin),
                                             int(t_end), ctypes.c_void_p(out.data_ptr()),
                                             _stream(dev, stream)))
+    return out
+
+
+def _df(Bov, Bvv, o, v, device):
+    dev = torch.device("cuda", device)
+    out = []
+    for n, x in (("Bov", Bov), ("Bvv", Bvv)):
+        t = x if isinstance(x, torch.Tensor) else torch.as_tensor(x)
+        if t.dtype != torch.float64:
+            raise TypeError(f"{n} must be float64, got {t.dtype}")
+        out.append(t.to(dev, non_blocking=True).contiguous())
+    bov, bvv = out
+    naux = bov.shape[0]
+    if tuple(bov.shape) != (naux, o, v) or tuple(bvv.shape) != (naux, v, v):
+        raise ValueError(f"Bov {tuple(bov.shape)} and Bvv {tuple(bvv.shape)} must be [naux,{o},{v}] and [naux,{v},{v}]")
+    return bov, bvv, TeDf(naux, ctypes.c_void_p(bov.data_ptr()), ctypes.c_void_p(bvv.data_ptr()))
+
+
+def t_energy_df(cluster, Bov, Bvv, precision="ozaki", handle=None, device=None, stream=None) -> torch.Tensor:
+    """E(T) of one cluster with ovvv[i,a,b,d] = sum_P Bov[P,i,a] Bvv[P,b,d]
+    formed on the device from the density-fitting factors (the cluster's
+    ovvv, if any, is not read).  Tensor-core modes only."""
+    dev = _device_of(cluster, device)
+    h = _handle(handle, dev)
+    t = _tensors(cluster, dev, skip=("ovvv",))
+    bov, bvv, df = _df(Bov, Bvv, t["eps_o"].shape[0], t["eps_v"].shape[0], dev)
+    c = _struct(t)
+    out = torch.empty((), dtype=torch.float64, device=torch.device("cuda", dev))
+    _lib.check(_lib.load().t_energy_df(h.ptr, ctypes.byref(c), ctypes.byref(df), _prec(precision),
+                                       ctypes.c_void_p(out.data_ptr()), _stream(dev, stream)))
+    return out
+
+
+def t_energy_df_triples(cluster, Bov, Bvv, t_begin=0, t_end=None, precision="ozaki", handle=None, device=None,
+                        stream=None) -> torch.Tensor:
+    """Per-triple shares of [t_begin, t_end) with ovvv from the density-fitting factors."""
+    dev = _device_of(cluster, device)
+    h = _handle(handle, dev)
+    t = _tensors(cluster, dev, skip=("ovvv",))
+    bov, bvv, df = _df(Bov, Bvv, t["eps_o"].shape[0], t["eps_v"].shape[0], dev)
+    if t_end is None:
+        t_end = num_unique_triples(t["eps_o"].shape[0])
+    out = torch.empty((max(0, t_end - t_begin),), dtype=torch.float64, device=torch.device("cuda", dev))
+    c = _struct(t)
+    _lib.check(_lib.load().t_energy_df_triples(h.ptr, ctypes.byref(c), ctypes.byref(df), _prec(precision),
+                                               int(t_begin), int(t_end), ctypes.c_void_p(out.data_ptr()),
+                                               _stream(dev, stream)))
     return out
 
 

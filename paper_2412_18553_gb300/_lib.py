@@ -36,6 +36,10 @@ class TeMp2Out(ctypes.Structure):
                 ("pop_o", c_void_p), ("pop_v", c_void_p)]
 
 
+class TeDf(ctypes.Structure):
+    _fields_ = [("naux", c_int64), ("Bov", c_void_p), ("Bvv", c_void_p)]
+
+
 class TeProfile(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("gemm_launches", c_int64), ("gemm_ms", ctypes.c_double),
                 ("energy_launches", c_int64), ("energy_ms", ctypes.c_double),
@@ -61,6 +65,12 @@ SIGNATURES = [
                                             ctypes.POINTER(TeClusterGrad), c_void_p]),
     ("t_energy_frag", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), c_void_p, ctypes.c_int,
                                      c_void_p, c_void_p, c_void_p]),
+    ("t_energy_df", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.POINTER(TeDf), ctypes.c_int,
+                                   c_void_p, c_void_p]),
+    ("t_energy_df_triples", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.POINTER(TeDf), ctypes.c_int,
+                                           c_int64, c_int64, c_void_p, c_void_p]),
+    ("te_df_workspace_bytes", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.POINTER(TeDf),
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("te_sync", ctypes.c_int, [c_void_p, c_void_p]),
     ("te_workspace_bytes", ctypes.c_int, [c_void_p, ctypes.POINTER(TeCluster), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_size_t)]),

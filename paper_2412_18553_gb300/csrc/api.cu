@@ -138,14 +138,14 @@ static te_status ensure_triples(Handle* h, int nocc) {
   return TE_OK;
 }
 
-static te_status host_check(const Handle* h, const te_cluster* c, te_precision p) {
+static te_status host_check(const Handle* h, const te_cluster* c, te_precision p, bool need_ovvv = true) {
   if (!h) return fail(TE_EINVAL, "null handle");
   if (!c) return fail(TE_EINVAL, "null cluster descriptor");
   if (c->nocc < 1 || c->nvir < 1) return fail(TE_EINVAL, "nocc and nvir must be >= 1 (got %lld, %lld)",
                                               (long long)c->nocc, (long long)c->nvir);
   if (c->nocc > 2048 || c->nvir > 4096)
     return fail(TE_EUNSUPPORTED, "cluster too large (nocc <= 2048, nvir <= 4096)");
-  if (!c->eps_o || !c->eps_v || !c->ovvv || !c->ooov || !c->ovov || !c->t1 || !c->t2)
+  if (!c->eps_o || !c->eps_v || (need_ovvv && !c->ovvv) || !c->ooov || !c->ovov || !c->t1 || !c->t2)
     return fail(TE_EINVAL, "null array pointer in cluster descriptor");
   if (p != TE_FP64 && p != TE_TF32 && p != TE_BF16X3 && p != TE_TF32X3 && p != TE_OZAKI)
     return fail(TE_EINVAL, "unknown precision mode %d", (int)p);
@@ -315,6 +315,25 @@ void tune_save(Handle* h) {
 te_status ensure_workspace_public(Handle* h, size_t bytes) { return ensure_workspace(h, bytes); }
 te_status ensure_triples_public(Handle* h, int nocc) { return ensure_triples(h, nocc); }
 
+// The descriptor and factors of t_energy_df; then the device value checks
+// (Bov and Bvv instead of ovvv).
+static te_status validate_df(Handle* h, const te_cluster* c, const te_df* df, te_precision p, cudaStream_t s) {
+  te_status st = host_check(h, c, p, false);
+  if (st != TE_OK) return st;
+  if (!df) return fail(TE_EINVAL, "null density-fitting factor descriptor");
+  if (df->naux < 1 || df->naux > (1LL << 20))
+    return fail(TE_EINVAL, "naux must be in [1, 2^20] (got %lld)", (long long)df->naux);
+  if (!df->Bov || !df->Bvv) return fail(TE_EINVAL, "null density-fitting factor pointer");
+  if (p == TE_FP64)
+    return fail(TE_EUNSUPPORTED, "ovvv from density-fitting factors needs a tensor-core mode (TE_OZAKI, "
+                                 "TE_BF16X3, TE_TF32X3 or TE_TF32)");
+  if (c->nvir > 2047) return fail(TE_EUNSUPPORTED, "ovvv from density-fitting factors needs nvir <= 2047");
+  const cudaError_t e = launch_check_inputs(c, 0, h->d_err, h->num_sms, s, df);
+  ++h->n_launches;
+  if (e != cudaSuccess) return fail(TE_ECUDA, "input check launch: %s", cudaGetErrorString(e));
+  return TE_OK;
+}
+
 static te_status run_any(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin,
                          int64_t t_end, double* e_tri_out, double* e_total_out, cudaStream_t s) {
   if (p == TE_FP64) return run_fp64(h, c, t_begin, t_end, e_tri_out, e_total_out, s);
@@ -410,6 +429,49 @@ te_status t_energy(te_handle hh, const te_cluster* c, te_precision p, double* e_
     return TE_OK;
   }
   return run_any(h, c, p, 0, nt, nullptr, e_out, s);
+}
+
+te_status t_energy_df(te_handle hh, const te_cluster* c, const te_df* df, te_precision p, double* e_out,
+                      te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  if (!e_out) return fail(TE_EINVAL, "null e_out");
+  DeviceGuard g(h->device);
+  te_status st = validate_df(h, c, df, p, s);
+  if (st != TE_OK) return st;
+  const int64_t nt = num_unique_triples(c->nocc);
+  if (nt == 0) {
+    if (cudaMemsetAsync(e_out, 0, sizeof(double), s) != cudaSuccess) return fail(TE_ECUDA, "memset failed");
+    return TE_OK;
+  }
+  return run_tc(h, c, p, 0, nt, nullptr, e_out, s, df);
+}
+
+te_status t_energy_df_triples(te_handle hh, const te_cluster* c, const te_df* df, te_precision p, int64_t t_begin,
+                              int64_t t_end, double* e_triples, te_stream_t ss) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(ss);
+  if (!h) return fail(TE_EINVAL, "null handle");
+  DeviceGuard g(h->device);
+  te_status st = validate_df(h, c, df, p, s);
+  if (st != TE_OK) return st;
+  const int64_t nt = num_unique_triples(c->nocc);
+  if (t_begin < 0 || t_end > nt || t_begin > t_end)
+    return fail(TE_EINVAL, "triple range [%lld,%lld) outside [0,%lld)", (long long)t_begin, (long long)t_end,
+                (long long)nt);
+  if (t_begin == t_end) return TE_OK;
+  if (!e_triples) return fail(TE_EINVAL, "null e_triples");
+  return run_tc(h, c, p, t_begin, t_end, e_triples, nullptr, s, df);
+}
+
+te_status te_df_workspace_bytes(te_handle hh, const te_cluster* c, const te_df* df, te_precision p,
+                                size_t* bytes) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !c || !df || !bytes) return fail(TE_EINVAL, "null argument");
+  if (c->nocc < 1 || c->nvir < 1 || df->naux < 1) return fail(TE_EINVAL, "nocc, nvir and naux must be >= 1");
+  if (p == TE_FP64) return fail(TE_EUNSUPPORTED, "ovvv from density-fitting factors needs a tensor-core mode");
+  return tc_workspace_bytes(h, c, p, bytes, df);
 }
 
 te_status t_energy_batched(te_handle hh, const te_cluster* cs, int64_t n, te_precision p,
@@ -625,11 +687,11 @@ te_status te_sync(te_handle hh, te_stream_t ss) {
     if (err[0] & ERR_WAIT_TIMEOUT)
       return fail(TE_ETIMEOUT, "device wait expired (code %u, site %u, block %u)", err[0], err[1], err[2]);
     if (err[0] & ERR_BAD_INPUT) {
-      static const char* what[10] = {"?", "eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2", "", "Bov"};
+      static const char* what[11] = {"?", "eps_o", "eps_v", "ovvv", "ooov", "ovov", "t1", "t2", "", "Bov", "Bvv"};
       if (err[1] == 8)
         return fail(TE_EINVAL, "input check failed (cluster %u): max(eps_o) must be below min(eps_v)", err[2]);
       return fail(TE_EINVAL, "input check failed (cluster %u): non-finite value in %s", err[2],
-                  what[(err[1] < 10 && err[1] != 8) ? err[1] : 0]);
+                  what[(err[1] < 11 && err[1] != 8) ? err[1] : 0]);
     }
     return fail(TE_ECUDA, "device check failed (code %u, site %u, block %u)", err[0], err[1], err[2]);
   }

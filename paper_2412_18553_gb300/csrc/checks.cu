@@ -5,7 +5,8 @@
 //    negative (the orbital energies need not be sorted).
 // A violation sets ERR_BAD_INPUT in the handle's error word with the site
 // (1..7: the array, in the order eps_o, eps_v, ovvv, ooov, ovov, t1, t2;
-// 8: the ordering of the orbital energies) and the cluster index; te_sync
+// 8: the ordering of the orbital energies; 9, 10: the density-fitting
+// factors Bov, Bvv) and the cluster index; te_sync
 // reports it as TE_EINVAL.  The kernels that follow still run (they never
 // fault on such values); their results are then unspecified.
 #include <algorithm>
@@ -18,10 +19,12 @@ namespace {
 
 constexpr unsigned long long EXP_MASK = 0x7FF0000000000000ull;
 
+constexpr int kCheckArrays = 9;
+
 struct CheckArgs {
-  const unsigned long long* p[7];
-  int64_t n[7];
-  unsigned int site[7];  // reported for a non-finite entry of array w
+  const unsigned long long* p[kCheckArrays];
+  int64_t n[kCheckArrays];
+  unsigned int site[kCheckArrays];  // reported for a non-finite entry of array w (n = 0: unused)
   const double* eps_o;
   const double* eps_v;
   int o, v;
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(256) k_check_inputs(const CheckArgs a, unsigne
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned int bad = 0;
-  for (int w = 0; w < 7; ++w) {
+  for (int w = 0; w < kCheckArrays; ++w) {
     const unsigned long long* q = a.p[w];
     const int64_t n = a.n[w];
     bool any = false;
@@ -84,16 +87,19 @@ __global__ void __launch_bounds__(256) k_check_inputs(const CheckArgs a, unsigne
 }  // namespace
 
 cudaError_t launch_check_inputs(const te_cluster* c, int64_t cluster, unsigned int* err, int num_sms,
-                                cudaStream_t s) {
-  const int64_t o = c->nocc, v = c->nvir;
+                                cudaStream_t s, const te_df* df) {
+  const int64_t o = c->nocc, v = c->nvir, P = df ? df->naux : 0;
   CheckArgs a{};
-  const double* ptr[7] = {c->eps_o, c->eps_v, c->ovvv, c->ooov, c->ovov, c->t1, c->t2};
-  const int64_t n[7] = {o, v, o * v * v * v, o * o * o * v, o * v * o * v, o * v, o * o * v * v};
+  // with density-fitting factors, ovvv is not read: Bov and Bvv instead
+  const double* ptr[kCheckArrays] = {c->eps_o, c->eps_v, df ? nullptr : c->ovvv, c->ooov, c->ovov, c->t1, c->t2,
+                                     df ? df->Bov : nullptr, df ? df->Bvv : nullptr};
+  const int64_t n[kCheckArrays] = {o, v, df ? 0 : o * v * v * v, o * o * o * v, o * v * o * v, o * v, o * o * v * v,
+                                   P * o * v, P * v * v};
   int64_t nmax = 0;
-  for (int w = 0; w < 7; ++w) {
+  for (int w = 0; w < kCheckArrays; ++w) {
     a.p[w] = reinterpret_cast<const unsigned long long*>(ptr[w]);
     a.n[w] = n[w];
-    a.site[w] = (unsigned int)w + 1u;
+    a.site[w] = (unsigned int)w + 1u + (w >= 7 ? 1u : 0u);  // 1..7, then 9, 10
     nmax = std::max(nmax, n[w]);
   }
   a.eps_o = c->eps_o;
@@ -115,7 +121,7 @@ cudaError_t launch_check_mp2(const double* eps_o, int64_t o, const double* eps_v
   const double* ptr[3] = {eps_o, eps_v, Bov};
   const int64_t n[3] = {o, v, nB};
   const unsigned int site[3] = {1u, 2u, 9u};
-  for (int w = 0; w < 7; ++w) {
+  for (int w = 0; w < kCheckArrays; ++w) {
     const int q = w < 3 ? w : 2;  // the unused entries repeat Bov with no elements
     a.p[w] = reinterpret_cast<const unsigned long long*>(ptr[q]);
     a.n[w] = w < 3 ? n[q] : 0;

@@ -185,9 +185,9 @@ te_status run_frag(Handle* h, const te_cluster* c, const double* cf, te_precisio
     ca.t2 = W.t2C;
     ca.ooov = W.ooovC;
     cb.t2 = W.t2C2;
-    st = tc_prepare_slices(c, W.slices[0], &S0, s);
-    if (st == TE_OK) st = tc_prepare_slices(&ca, W.slices[1], &SA, s);
-    if (st == TE_OK) st = tc_prepare_slices(&cb, W.slices[2], &SB, s);
+    st = tc_prepare_slices(c, W.slices[0], &S0, h->num_sms, s);
+    if (st == TE_OK) st = tc_prepare_slices(&ca, W.slices[1], &SA, h->num_sms, s);
+    if (st == TE_OK) st = tc_prepare_slices(&cb, W.slices[2], &SB, h->num_sms, s);
     if (st != TE_OK) return st;
     h->n_launches += 18;
   }
@@ -244,22 +244,22 @@ te_status run_frag(Handle* h, const te_cluster* c, const double* cf, te_precisio
         // S1: rows (x, y) of ovvv[p] (K = d), columns z of t2[r,q]
         auto s1 = [&](const SliceSet& SX, const SliceSet& ST, int ov, int r, int q, double* C, double al, int ow) {
           run(OzView{ovvv_of(SX, ov), t2_of(ST, r, q), SX.ovvv_plane, ST.t2_plane, C, v, v, v, v, 1, v * vp, vp, 1,
-                     0, 1, 0, vp, v2, v, 1, al, SX.exps + 0, ST.exps + 1, ow});
+                     0, 1, 0, vp, v2, v, 1, al, SX.e_ovvv + ov, ST.e_t2 + ((int64_t)r * o + q), ow});
         };
         // S2: rows (x, y) of ovvv[q] read transposed (y, x)
         auto s2 = [&](const SliceSet& SX, const SliceSet& ST, int ov, int r, int q, double* C, double al) {
           run(OzView{ovvv_of(SX, ov), t2_of(ST, r, q), SX.ovvv_plane, ST.t2_plane, C, v, v, v, v, 1, vp, v * vp, 1,
-                     0, 1, 0, vp, v2, v, 1, al, SX.exps + 0, ST.exps + 1, 0});
+                     0, 1, 0, vp, v2, v, 1, al, SX.e_ovvv + ov, ST.e_t2 + ((int64_t)r * o + q), 0});
         };
         // S3: t2L[p][y][x][l] nooT[q][r][z][l]
         auto s3 = [&](const SliceSet& SL, const SliceSet& SN, int lp, int nq, int nr, double* C, double al) {
           run(OzView{t2L_of(SL, lp), nooT_of(SN, nq, nr), SL.t2L_plane, SN.nooT_plane, C, v, v, v, o, 1, op,
-                     v * op, 1, 0, 1, 0, op, v2, v, 1, al, SL.exps + 2, SN.exps + 3, 0});
+                     v * op, 1, 0, 1, 0, op, v2, v, 1, al, SL.e_t2L + lp, SN.e_nooT + ((int64_t)nq * o + nr), 0});
         };
         // S4: t2L[q][x][y][l] nooT[p][r][z][l]
         auto s4 = [&](const SliceSet& SL, const SliceSet& SN, int lq, int np, int nr, double* C, double al) {
           run(OzView{t2L_of(SL, lq), nooT_of(SN, np, nr), SL.t2L_plane, SN.nooT_plane, C, v, v, v, o, 1, v * op,
-                     op, 1, 0, 1, 0, op, v2, v, 1, al, SL.exps + 2, SN.exps + 3, 0});
+                     op, 1, 0, 1, 0, op, v2, v, 1, al, SL.e_t2L + lq, SN.e_nooT + ((int64_t)np * o + nr), 0});
         };
         // the G block itself (first product overwrites)
         s1(S0, S0, pp, rr, qq, Gg, 1.0, 1);

@@ -19,7 +19,9 @@
 //   gamma_vv[a,b] = 2 sum_{(ij),c} t[ij,a,c] T~[ij,b,c]
 //   gamma_oo[i,j] = 2 delta_ij - 2 sum_{k,(ab)} t[i,k,ab] T~[j,k,ab]
 // The eigenvalues come from the cyclic Jacobi method in the parallel
-// (round-robin) ordering, one block per matrix, float64 throughout.
+// (round-robin) ordering, one block per matrix, float64 throughout, with the
+// matrix in shared memory up to order 168; one launch takes the matrices of
+// up to 32 clusters, whose density blocks stay in the workspace until then.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -65,38 +67,10 @@ __global__ void k_two_identity(double* __restrict__ g, int o) {
     g[idx] = (idx / o == idx % o) ? 2.0 : 0.0;
 }
 
-// max |x| (bit patterns of non-negative doubles order as integers)
-__global__ void k_maxabs1(const double* __restrict__ x, int64_t n, unsigned long long* out) {
-  double m = 0.0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
-    m = fmax(m, fabs(x[idx]));
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
-}
-
-// four 7-bit BF16 slices of x (slice s at planes + s n): x = 2^e sum_s m_s 2^-7(s+1), 2^e > max |x|
-__global__ void k_slice4(const double* __restrict__ x, int64_t n, const unsigned long long* __restrict__ xmax,
-                         int* __restrict__ e_out, __nv_bfloat16* __restrict__ planes) {
-  const double mx = __longlong_as_double((long long)*xmax);
-  int ex = 0;
-  if (mx > 0.0) frexp(mx, &ex);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *e_out = ex;
-  const double sc = ldexp(1.0, -ex);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double t = x[i] * sc;  // |t| < 1
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      t = t * 128.0;
-      const double m = rint(t);
-      t = t - m;
-      planes[k * n + i] = __float2bfloat16_rn((float)(m * (1.0 / (double)(1ull << (7 * (k + 1))))));
-    }
-  }
-}
-
-// One symmetric matrix for the eigensolver: a working copy (m x m, m = n
-// rounded up to even; the padding row and column are zero and never rotate),
-// the source (n x n) and the output eigenvalues (n, ascending).
+// One symmetric matrix for the eigensolver: the source (n x n), the output
+// eigenvalues (n, ascending), the padded order m (n rounded up to even; the
+// padding row and column are zero and never rotate) and a global working copy
+// (m x m) for an order too large for shared memory (null otherwise).
 struct EigJob {
   double* a;
   const double* src;
@@ -104,29 +78,51 @@ struct EigJob {
   int n, m;
 };
 
+// Orders up to this one keep their working copy in shared memory:
+// 168^2 doubles plus 84 pairs' rotations fit the 227 KB of one block.
+constexpr int kJacobiSmemM = 168;
+
 struct EigJobs {
   int count;
   EigJob j[64];
 };
 
+// Shared memory of one job: rotations of its m / 2 pairs, then its working
+// copy unless it has a global one.
+__host__ __device__ inline size_t jacobi_rot_bytes(int m) { return ((size_t)(m / 2) * 20 + 15) & ~size_t(15); }
+__host__ __device__ inline size_t jacobi_smem_bytes(const EigJob& j) {
+  return jacobi_rot_bytes(j.m) + (j.a ? 0 : (size_t)j.m * j.m * 8);
+}
+
 // Parallel-order cyclic Jacobi: in step s of a sweep the index at position 0
 // stays and the others rotate; pair k is (label(k), label(m-1-k)) with
 // label(0) = 0, label(x) = 1 + (x - 1 + s) mod (m - 1).  The m/2 rotations of a
 // step act on disjoint index pairs, so they are applied at once: rows p, q of
-// every pair, then columns p, q.  Sweeps repeat until the off-diagonal mass is
-// below 1e-30 of the matrix's (or 60 sweeps).  Then the diagonal is sorted.
+// every pair, then columns p, q.  The matrix taken is the symmetric part of the
+// block ((A + A^T) / 2): a density computed in exact slices is symmetric only
+// to about 1e-9 of its scale, and an orthogonal similarity cannot remove an
+// antisymmetric part.  Sweeps repeat until the off-diagonal mass is below
+// 1e-30 of the matrix's, stops decreasing (rounding floor), or 60 sweeps have
+// run.  Then the diagonal is sorted.  Dynamic shared memory: the rotations
+// (cosines, sines, then the p and q indices, m / 2 each), then the working
+// copy when the job has no global one.
 __global__ void __launch_bounds__(512, 1) k_jacobi(const __grid_constant__ EigJobs J) {
   const EigJob& jb = J.j[blockIdx.x];
   const int n = jb.n, m = jb.m;
-  double* A = jb.a;
-  __shared__ double cs[2048], sn[2048];
-  __shared__ unsigned short pp[2048], qq[2048];  // m <= 4094
+  extern __shared__ __align__(16) unsigned char jac_smem[];
+  double* cs = reinterpret_cast<double*>(jac_smem);
+  double* sn = cs + m / 2;
+  unsigned short* pp = reinterpret_cast<unsigned short*>(sn + m / 2);
+  unsigned short* qq = pp + m / 2;
+  double* A = jb.a ? jb.a : reinterpret_cast<double*>(jac_smem + jacobi_rot_bytes(m));
   __shared__ double red[32];
   __shared__ int done;
+  __shared__ double prev_off;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) prev_off = -1.0;
   for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
     const int r = (int)(e / m), c = (int)(e % m);
-    A[e] = (r < n && c < n) ? jb.src[(int64_t)r * n + c] : 0.0;
+    A[e] = (r < n && c < n) ? 0.5 * (jb.src[(int64_t)r * n + c] + jb.src[(int64_t)c * n + r]) : 0.0;
   }
   __syncthreads();
   const int half = m / 2;
@@ -160,7 +156,8 @@ __global__ void __launch_bounds__(512, 1) k_jacobi(const __grid_constant__ EigJo
     if (tid == 0) {
       double st = 0.0;
       for (int w = 0; w < (nt >> 5); ++w) st += red[w];
-      done = (off_all <= 1e-30 * st) ? 1 : 0;
+      done = (off_all <= 1e-30 * st || (prev_off >= 0.0 && off_all >= prev_off)) ? 1 : 0;
+      prev_off = off_all;
     }
     __syncthreads();
     if (done) break;
@@ -214,15 +211,6 @@ __global__ void __launch_bounds__(512, 1) k_jacobi(const __grid_constant__ EigJo
 
 }  // namespace
 
-// Launch helpers used below.
-static cudaError_t slice_array(const double* x, int64_t n, unsigned long long* mx, int* ex, __nv_bfloat16* planes,
-                               cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(mx, 0, 8, s);
-  if (e != cudaSuccess) return e;
-  k_maxabs1<<<std::min(grid_of(n), 1024), 256, 0, s>>>(x, n, mx);
-  k_slice4<<<grid_of(n), 256, 0, s>>>(x, n, mx, ex, planes);
-  return cudaGetLastError();
-}
 
 // Doubles of split-K partial tiles for the three contractions.  The
 // exact-slice GEMM splits K into blocks of at most 1024 (exactness) and, for
@@ -235,17 +223,40 @@ static int64_t mp2_scratch(int64_t o, int64_t v, int64_t naux, bool oz, int num_
   return std::max({gemm_oz_scratch(ov, ov, naux, num_sms), f64, (int64_t)1});  // (ia|jb) split K
 }
 
-// Bytes of workspace for one cluster of the batch (the largest is allocated).
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Bytes of workspace one cluster uses while its contractions run (the largest
+// is allocated; the next cluster reuses it).
 static size_t mp2_bytes(int64_t o, int64_t v, int64_t naux, bool oz, int num_sms) {
-  auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t ovov = (size_t)o * v * o * v, t2n = (size_t)o * o * v * v;
-  size_t b = a(ovov * 8) + 2 * a(t2n * 8);                            // ovov, t2 (own copy), T~
-  b += a((size_t)o * o * 8) + a((size_t)v * v * 8);                    // gamma blocks (own copies)
+  size_t b = al256(ovov * 8) + 2 * al256(t2n * 8);                       // ovov, t2 (own copy), T~
+  b += al256((size_t)mp2_scratch(o, v, naux, oz, num_sms) * 8);          // split-K partial tiles
+  if (oz) b += al256((size_t)naux * o * v * 8) + al256(64);              // slices of Bov (4 x 2 B per element), scale
+  return b;
+}
+
+// Bytes one cluster keeps until its group's eigensolver launch: the gamma
+// blocks (when the caller did not ask for them) and global working copies for
+// orders above kJacobiSmemM.
+static size_t mp2_keep_bytes(int64_t o, int64_t v) {
   const int64_t mo = (o + 1) / 2 * 2, mv = (v + 1) / 2 * 2;
-  b += a((size_t)mo * mo * 8) + a((size_t)mv * mv * 8);                // eigensolver copies
-  b += a((size_t)mp2_scratch(o, v, naux, oz, num_sms) * 8);          // split-K partial tiles
-  if (oz) b += a((size_t)naux * o * v * 8) + a(64);                 // slices of Bov (4 x 2 B per element), scale
-  return b + 1024;
+  size_t b = al256((size_t)o * o * 8) + al256((size_t)v * v * 8);
+  if (mo > kJacobiSmemM) b += al256((size_t)mo * mo * 8);
+  if (mv > kJacobiSmemM) b += al256((size_t)mv * mv * 8);
+  return b;
+}
+
+// Clusters per eigensolver launch: two matrices each, 64 jobs.
+constexpr int64_t kMp2Group = 32;
+
+static cudaError_t launch_jacobi(EigJobs* jobs, cudaStream_t s) {
+  size_t bytes = 16;
+  for (int k = 0; k < jobs->count; ++k) bytes = std::max(bytes, jacobi_smem_bytes(jobs->j[k]));
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  k_jacobi<<<jobs->count, 512, bytes, s>>>(*jobs);
+  jobs->count = 0;
+  return cudaGetLastError();
 }
 
 }  // namespace te
@@ -266,7 +277,7 @@ extern "C" te_status t_mp2_bno_batched(te_handle hh, const te_mp2_cluster* cs, c
   if (p == TE_OZAKI && h->cc_major != 10 && h->cc_major != 11)
     return fail(TE_EUNSUPPORTED, "exact-slice contractions need an sm_100-family GPU");
   const bool oz = p == TE_OZAKI;
-  size_t need = 0;
+  size_t need_tr = 0, need_keep = 0, group_keep = 0;
   for (int64_t x = 0; x < n; ++x) {  // every descriptor before any launch
     const te_mp2_cluster& c = cs[x];
     if (c.nocc < 1 || c.nvir < 1 || c.naux < 1)
@@ -277,8 +288,12 @@ extern "C" te_status t_mp2_bno_batched(te_handle hh, const te_mp2_cluster* cs, c
     const te_mp2_out& q = outs[x];
     if (!q.t2 && !q.gamma_oo && !q.gamma_vv && !q.pop_o && !q.pop_v)
       return fail(TE_EINVAL, "cluster %lld: no output requested", (long long)x);
-    need = std::max(need, mp2_bytes(c.nocc, c.nvir, c.naux, oz, h->num_sms));
+    need_tr = std::max(need_tr, mp2_bytes(c.nocc, c.nvir, c.naux, oz, h->num_sms));
+    if (x % kMp2Group == 0) group_keep = 0;
+    group_keep += mp2_keep_bytes(c.nocc, c.nvir);
+    need_keep = std::max(need_keep, group_keep);
   }
+  const size_t need = need_keep + need_tr + 1024;
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
@@ -293,25 +308,30 @@ extern "C" te_status t_mp2_bno_batched(te_handle hh, const te_mp2_cluster* cs, c
   EigJobs* jobs = new EigJobs;
   std::memset(jobs, 0, sizeof(*jobs));
   cudaError_t e = cudaSuccess;
+  char* const ws0 = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 255) & ~uintptr_t(255));
+  char* keep = ws0;                       // kept blocks of the current group
+  char* const transient = ws0 + need_keep;  // one cluster's contractions
   for (int64_t x = 0; x < n && e == cudaSuccess; ++x) {
     const te_mp2_cluster& c = cs[x];
     const te_mp2_out& q = outs[x];
     const int64_t o = c.nocc, v = c.nvir, P = c.naux;
     const int64_t ov = o * v, t2n = o * o * v * v;
-    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 255) & ~uintptr_t(255));
-    auto take = [&](size_t bytes) {
+    if (x % kMp2Group == 0) keep = ws0;
+    auto take_from = [](char*& base, size_t bytes) {
       char* r = base;
-      base += (bytes + 255) & ~size_t(255);
+      base += al256(bytes);
       return r;
     };
+    char* base = transient;
+    auto take = [&](size_t bytes) { return take_from(base, bytes); };
     double* ovov = reinterpret_cast<double*>(take((size_t)ov * ov * 8));
     double* t2 = reinterpret_cast<double*>(take((size_t)t2n * 8));
     double* tt = reinterpret_cast<double*>(take((size_t)t2n * 8));
-    double* goo = reinterpret_cast<double*>(take((size_t)o * o * 8));
-    double* gvv = reinterpret_cast<double*>(take((size_t)v * v * 8));
+    double* goo = reinterpret_cast<double*>(take_from(keep, (size_t)o * o * 8));
+    double* gvv = reinterpret_cast<double*>(take_from(keep, (size_t)v * v * 8));
     const int mo = (int)((o + 1) / 2 * 2), mv = (int)((v + 1) / 2 * 2);
-    double* eo_work = reinterpret_cast<double*>(take((size_t)mo * mo * 8));
-    double* ev_work = reinterpret_cast<double*>(take((size_t)mv * mv * 8));
+    double* eo_work = mo > kJacobiSmemM ? reinterpret_cast<double*>(take_from(keep, (size_t)mo * mo * 8)) : nullptr;
+    double* ev_work = mv > kJacobiSmemM ? reinterpret_cast<double*>(take_from(keep, (size_t)mv * mv * 8)) : nullptr;
     const int64_t cap = mp2_scratch(o, v, P, oz, h->num_sms);
     const int64_t cap64 = std::min(cap, mp2_scratch(o, v, P, false, h->num_sms));
     double* scratch = reinterpret_cast<double*>(take((size_t)cap * 8));
@@ -331,8 +351,7 @@ extern "C" te_status t_mp2_bno_batched(te_handle hh, const te_mp2_cluster* cs, c
       __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(take((size_t)P * ov * 8));
       unsigned long long* mx = reinterpret_cast<unsigned long long*>(take(64));
       int* ex = reinterpret_cast<int*>(mx + 3);
-      if (e == cudaSuccess) e = slice_array(c.Bov, P * ov, mx, ex, bs, s);
-      h->n_launches += 2;
+      if (e == cudaSuccess) e = slice_planes(c.Bov, P * ov, 4, mx, ex, bs, s, &h->n_launches);
       if (e == cudaSuccess)
         e = gemm_oz(OzView{bs, bs, P * ov, P * ov, ovov, o, v, ov, P, 1, v, 1, ov, 0, ov, 0, 1, v * ov, ov, 1, 1.0,
                            ex, ex, 0},
@@ -361,14 +380,15 @@ extern "C" te_status t_mp2_bno_batched(te_handle hh, const te_mp2_cluster* cs, c
             GemmView{t2, tt, goo, o, 1, o, o, v * v, o * v * v, 0, v * v, 1, v * v, 1, o * v * v, o, 0, 1, -2.0},
             h->num_sms, scratch, cap64, s, &h->n_launches);
     }
-    // populations: one eigensolver block per requested matrix, launched per cluster
-    if (e == cudaSuccess && (q.pop_o || q.pop_v)) {
-      jobs->count = 0;
+    // populations: one eigensolver block per requested matrix, launched
+    // once per group of clusters (their blocks stay in the kept region)
+    if (e == cudaSuccess) {
       if (q.pop_o) jobs->j[jobs->count++] = EigJob{eo_work, goo, q.pop_o, (int)o, mo};
       if (q.pop_v) jobs->j[jobs->count++] = EigJob{ev_work, gvv, q.pop_v, (int)v, mv};
-      k_jacobi<<<jobs->count, 512, 0, s>>>(*jobs);
-      ++h->n_launches;
-      e = cudaGetLastError();
+      if (jobs->count > 0 && ((x + 1) % kMp2Group == 0 || x + 1 == n)) {
+        e = launch_jacobi(jobs, s);
+        ++h->n_launches;
+      }
     }
   }
   delete jobs;

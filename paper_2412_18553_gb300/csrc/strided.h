@@ -90,8 +90,9 @@ struct GemmView {
   double alpha;
 };
 
-// the same over four BF16 slice planes per operand (slice s at base + s *
-// plane), C (+)= alpha 2^(ea + eb) sum_k A B (exact-slice products on mma.sync)
+// the same over NS BF16 slice planes per operand (slice s at base + s *
+// plane; NS = ns, 4 when 0), C (+)= alpha 2^(ea + eb) sum_k A B (exact-slice
+// products on mma.sync)
 struct OzView {
   const __nv_bfloat16* A;
   const __nv_bfloat16* B;
@@ -105,12 +106,18 @@ struct OzView {
   const int* ea;  // device scale exponents of A's and B's slices
   const int* eb;
   int overwrite;  // store instead of accumulate (single K split only)
+  int ns;         // slices per operand: 4 (also when 0) or 5
 };
 
 cudaError_t gemm_strided(const GemmView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
                          int64_t* launches);
 cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scratch_cap, cudaStream_t s,
                     int64_t* launches);
+// NS (4 or 5) 7-bit slice planes of x[0..n) with one power-of-two scale:
+// *ex = e with 2^e > max |x| (the max's bits go to *mx), slice s at planes +
+// s n.  Two launches.
+cudaError_t slice_planes(const double* x, int64_t n, int ns, unsigned long long* mx, int* ex,
+                         __nv_bfloat16* planes, cudaStream_t s, int64_t* launches);
 // doubles of split-K scratch gemm_oz needs for an M x N output over K
 int64_t gemm_oz_scratch(int64_t M, int64_t N, int64_t K, int num_sms);
 // doubles of split-K scratch the two GEMMs need for a cluster's contractions

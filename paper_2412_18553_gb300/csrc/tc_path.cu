@@ -34,6 +34,7 @@
 
 #include "energy_tc.h"
 #include "ptx_sm100.cuh"
+#include "strided.h"
 #include "tc_path.h"
 
 namespace te {
@@ -41,7 +42,9 @@ namespace te {
 // TC_OZAKI: four 7-bit slices, ten slice products (K = 2 (v + o) <= 1024).
 // TC_OZAKI6: five 6-bit slices, fifteen slice products (K <= 4096); chosen
 // for the same user mode when the K axis is too long for 7-bit slices.
-enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2, TC_OZAKI = 3, TC_OZAKI6 = 4 };
+// TC_SLICE5: five 7-bit slices (35 bits), an operand form of the strided
+// exact-slice GEMMs only (no contraction kernel of its own).
+enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2, TC_OZAKI = 3, TC_OZAKI6 = 4, TC_SLICE5 = 5 };
 
 constexpr int OZ_K_MAX7 = 1024;  // K * 2^14 < 2^24: exact level-2/3 sums with 7-bit slices
 constexpr int OZ_K_MAX6 = 4096;  // K * 2^12 < 2^24 with 6-bit slices
@@ -59,12 +62,15 @@ static int tc_mode_of(te_precision p, int o, int v, int ozaki_bits) {
   }
 }
 
-__host__ __device__ constexpr bool is_ozaki(int mode) { return mode == TC_OZAKI || mode == TC_OZAKI6; }
+__host__ __device__ constexpr bool is_ozaki(int mode) {
+  return mode == TC_OZAKI || mode == TC_OZAKI6 || mode == TC_SLICE5;
+}
 
 template <int MODE>
 struct ModeTraits {
   static constexpr bool tf32 = (MODE == TC_TF32 || MODE == TC_TF32X3);
-  static constexpr int nparts = (MODE == TC_TF32) ? 1 : (MODE == TC_OZAKI ? 4 : (MODE == TC_OZAKI6 ? 5 : 2));
+  static constexpr int nparts =
+      (MODE == TC_TF32) ? 1 : (MODE == TC_OZAKI ? 4 : ((MODE == TC_OZAKI6 || MODE == TC_SLICE5) ? 5 : 2));
   static constexpr int nacc = is_ozaki(MODE) ? 3 : 1;   // accumulators per tile
   static constexpr int beta = MODE == TC_OZAKI6 ? 6 : 7;  // bits per slice
 };
@@ -126,10 +132,12 @@ __device__ __forceinline__ int64_t slice_index(int64_t row, int64_t k, int64_t G
   return (row / G) * (NS * G * Kp) + (row % G) * Kp + k;
 }
 
-// dst[row][kp] = src[row][k] (k < K) or 0, rows x Kp, slice-interleaved by groups of G rows
+// dst[row][kp] = src[row][k] (k < K) or 0, rows x Kp, slice-interleaved by
+// groups of G rows; gexp (nullable): one scale exponent per group instead of
+// exps[which]
 template <int MODE>
 __global__ void k_split_rows(const double* __restrict__ src, Parts parts, int64_t rows, int K, int Kp, int64_t G,
-                             const int* exps, int which) {
+                             const int* exps, int which, const int* __restrict__ gexp = nullptr) {
   const double sc = scale_of(exps, which);
   const int64_t n = rows * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
@@ -137,14 +145,16 @@ __global__ void k_split_rows(const double* __restrict__ src, Parts parts, int64_
     const int k = (int)(idx % Kp);
     const int64_t row = idx / Kp;
     const double x = k < K ? src[row * K + k] : 0.0;
-    split_store<MODE>(x, parts, slice_index(row, k, G, ModeTraits<MODE>::nparts, Kp), sc);
+    split_store<MODE>(x, parts, slice_index(row, k, G, ModeTraits<MODE>::nparts, Kp),
+                      gexp ? ldexp(1.0, -gexp[row / G]) : sc);
   }
 }
 
-// t2L[q][x][y][l] = t2[l][q][x][y], l padded to op
+// t2L[q][x][y][l] = t2[l][q][x][y], l padded to op; gexp (nullable): one
+// exponent per q
 template <int MODE>
 __global__ void k_split_t2L(const double* __restrict__ t2, Parts parts, int o, int v, int op, const int* exps,
-                            int which) {
+                            int which, const int* __restrict__ gexp = nullptr) {
   const double sc = scale_of(exps, which);
   const int64_t n = (int64_t)o * v * v * op;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
@@ -156,14 +166,16 @@ __global__ void k_split_t2L(const double* __restrict__ t2, Parts parts, int o, i
     const int x = (int)(rest % v);
     const int q = (int)(rest / v);
     const double val = l < o ? t2[(((int64_t)l * o + q) * v + x) * v + y] : 0.0;
-    split_store<MODE>(val, parts, slice_index(idx / op, l, (int64_t)v * v, ModeTraits<MODE>::nparts, op), sc);
+    split_store<MODE>(val, parts, slice_index(idx / op, l, (int64_t)v * v, ModeTraits<MODE>::nparts, op),
+                      gexp ? ldexp(1.0, -gexp[q]) : sc);
   }
 }
 
-// nooT[p][r][z][l] = -ooov[p][l][r][z], l padded to op
+// nooT[p][r][z][l] = -ooov[p][l][r][z], l padded to op; gexp (nullable): one
+// exponent per (p, r), at p o + r
 template <int MODE>
 __global__ void k_split_noo(const double* __restrict__ ooov, Parts parts, int o, int v, int op, const int* exps,
-                            int which) {
+                            int which, const int* __restrict__ gexp = nullptr) {
   const double sc = scale_of(exps, which);
   const int64_t n = (int64_t)o * o * v * op;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
@@ -175,7 +187,8 @@ __global__ void k_split_noo(const double* __restrict__ ooov, Parts parts, int o,
     const int r = (int)(rest % o);
     const int p = (int)(rest / o);
     const double val = l < o ? -ooov[(((int64_t)p * o + l) * o + r) * v + z] : 0.0;
-    split_store<MODE>(val, parts, slice_index(idx / op, l, v, ModeTraits<MODE>::nparts, op), sc);
+    split_store<MODE>(val, parts, slice_index(idx / op, l, v, ModeTraits<MODE>::nparts, op),
+                      gexp ? ldexp(1.0, -gexp[p * o + r]) : sc);
   }
 }
 
@@ -243,6 +256,55 @@ __global__ void k_exponents(const unsigned long long* maxbits, int* exps) {
   exps[4] = U;
 }
 
+// max |x| per row group of the strided GEMMs' operands, one bit pattern per
+// group (atomicMax of non-negative doubles).  Elements are enumerated group
+// by group, in chunks of `chunk` per block iteration:
+//   mode 0 ovvv[p][x][y][d]   group p       (groups of v^3)
+//   mode 1 t2[r][q][z][d]     group r o + q (groups of v^2)
+//   mode 2 t2[l][q][x][y]     group q       (the t2L view; groups of o v^2)
+//   mode 3 ooov[p][l][r][z]   group p o + r (the nooT view; groups of o v)
+__global__ void __launch_bounds__(256) k_group_maxabs(const double* __restrict__ src, int mode, int o, int v,
+                                                      int64_t gsize, int64_t ngroups, int64_t chunk,
+                                                      unsigned long long* __restrict__ out) {
+  const int64_t cpg = (gsize + chunk - 1) / chunk;
+  const int64_t v2 = (int64_t)v * v;
+  __shared__ double red[8];
+  for (int64_t cid = blockIdx.x; cid < ngroups * cpg; cid += gridDim.x) {
+    const int64_t g = cid / cpg, i0 = (cid % cpg) * chunk, i1 = min(gsize, i0 + chunk);
+    double m = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      int64_t a;
+      if (mode <= 1) {
+        a = g * gsize + i;
+      } else if (mode == 2) {  // i = l v^2 + xy
+        a = ((i / v2) * o + g) * v2 + i % v2;
+      } else {                 // g = p o + r, i = l v + z
+        const int64_t p = g / o, r = g % o;
+        a = (((p * o) + i / v) * o + r) * v + i % v;
+      }
+      m = fmax(m, fabs(src[a]));
+    }
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+      if (m > 0.0) atomicMax(out + g, (unsigned long long)__double_as_longlong(m));
+    }
+    __syncthreads();
+  }
+}
+
+// exps[g] = e with 2^e > max of group g (0 for an all-zero group)
+__global__ void k_group_exps(const unsigned long long* __restrict__ bits, int64_t n, int* __restrict__ exps) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double m = __longlong_as_double((long long)bits[g]);
+    int ex = 0;
+    if (m > 0.0) frexp(m, &ex);
+    exps[g] = ex;
+  }
+}
+
 static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 16384); }
 
 // ---------------------------------------------------------------------------
@@ -286,7 +348,6 @@ struct TcParams {
   uint32_t a_part_bytes;   // 128 rows x cbw
   uint32_t tmem_cols;
   int nbuf;                // TMEM accumulator sets (1 or 2)
-  int rot;                 // exact-slice modes, N tiles <= 128: four rotating 128-column TMEM blocks
   int nt_max;              // largest N tile: stride of the accumulator sets
   int64_t total_tiles;
   const Triple* triples;
@@ -396,8 +457,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t* tfull = empty + P.stages;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
-  uint64_t* efree = drain + 1;  // rotation: a tile's level-0/1 blocks copied out (tempty: its level-2 block)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(efree + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -411,7 +471,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
       ptx::mbar_init(&tempty[a], GEMM_EPI_WARPS);
-      ptx::mbar_init(&efree[a], GEMM_EPI_WARPS);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -492,7 +551,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t fmt = TF32 ? 2u : 1u;
-      uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0, tile_n = 0;
+      uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
       bool ok = true;
       bool issued = false;
       for (int64_t tt = blockIdx.x; ok && tt < P.total_tiles; tt += gridDim.x) {
@@ -500,25 +559,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const TcCl& C = P.cl[c.cl];
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(C.NT >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
-        // Rotation (P.rot): tile n keeps levels 0, 1, 2 in the 128-column blocks
-        // 3n, 3n+1, 3n+2 (mod 4).  Block 3n is tile n-2's level-2 block (free
-        // when its epilogue is done: tempty), blocks 3n+1 and 3n+2 are tile
-        // n-1's level-0/1 blocks (free once its epilogue copied them out:
-        // efree), so tile n starts while tile n-1's epilogue is still storing.
-        uint32_t tb0 = 0, tb1 = 0, tb2 = 0;  // TMEM column offsets of the three levels
-        if (P.rot) {
-          const uint32_t n = tile_n;
-          bool w = !*abort_flag;
-          if (w && n >= 1) w = ptx::mbar_wait(&efree[(n - 1) & 1], ((n - 1) >> 1) & 1u, P.wait_ns);
-          if (w && n >= 2) w = ptx::mbar_wait(&tempty[(n - 2) & 1], ((n - 2) >> 1) & 1u, P.wait_ns);
-          if (!w) {
-            if (!*abort_flag) record_abort(P, abort_flag, 2);
-            break;
-          }
-          tb0 = 128u * ((3u * n) & 3u);
-          tb1 = 128u * ((3u * n + 1u) & 3u);
-          tb2 = 128u * ((3u * n + 2u) & 3u);
-        } else if (*abort_flag || !ptx::mbar_wait(&tempty[acc], acc_phase ^ 1u, P.wait_ns)) {
+        if (*abort_flag || !ptx::mbar_wait(&tempty[acc], acc_phase ^ 1u, P.wait_ns)) {
           if (!*abort_flag) record_abort(P, abort_flag, 2);
           break;
         }
@@ -553,9 +594,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               if constexpr (is_ozaki(MODE)) {
                 // slice products a_i b_j with i + j <= NPART - 1: level i + j = 0 and
                 // level 1 each in an exact accumulator, the higher levels in a third
-                const uint32_t d2 = P.rot ? tmem_base + tb0 : d_tmem;
-                const uint32_t d3 = P.rot ? tmem_base + tb1 : d_tmem + C.NT;
-                const uint32_t dr = P.rot ? tmem_base + tb2 : d_tmem + 2 * C.NT;
+                const uint32_t d2 = d_tmem, d3 = d_tmem + C.NT, dr = d_tmem + 2 * C.NT;
                 ptx::mma<false>(d2, ad[0], bd[0], idesc, acc_in);
                 ptx::mma<false>(d3, ad[0], bd[1], idesc, acc_in);
                 ptx::mma<false>(d3, ad[1], bd[0], idesc, 1);
@@ -585,17 +624,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
         }
         if (!ok) break;
-        if (P.rot) {
-          ptx::mma_commit(&tfull[tile_n & 1]);
-          ++tile_n;
+        ptx::mma_commit(&tfull[acc]);
+        if (NBUF == 2) {
+          acc ^= 1u;
+          if (acc == 0) acc_phase ^= 1u;
         } else {
-          ptx::mma_commit(&tfull[acc]);
-          if (NBUF == 2) {
-            acc ^= 1u;
-            if (acc == 0) acc_phase ^= 1u;
-          } else {
-            acc_phase ^= 1u;
-          }
+          acc_phase ^= 1u;
         }
       }
       // every issued MMA completes before TMEM is released
@@ -609,17 +643,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int quad = warp & 3;
     const int chunk0 = (warp - 2) >> 2;  // this warp's first 16-column chunk
     const int row = quad * 32 + lane;
-    uint32_t acc = 0, acc_phase = 0, tile_n = 0;
+    uint32_t acc = 0, acc_phase = 0;
     for (int64_t tt = blockIdx.x; tt < P.total_tiles; tt += gridDim.x) {
       const TileCoord c = decode_tile(P, tt);
       const TcCl& C = P.cl[c.cl];
       const TcPiece& pc = P.pc[c.piece];
       int got = 0;
-      if (!*abort_flag)
-        got = (P.rot ? ptx::mbar_wait(&tfull[tile_n & 1], (tile_n >> 1) & 1u, P.wait_ns)
-                     : ptx::mbar_wait(&tfull[acc], acc_phase, P.wait_ns))
-                  ? 1
-                  : 0;
+      if (!*abort_flag) got = ptx::mbar_wait(&tfull[acc], acc_phase, P.wait_ns) ? 1 : 0;
       // the decision is warp-uniform: tcgen05.ld below is a .sync.aligned instruction
       if (!__all_sync(0xffffffffu, got)) {
         if (!*abort_flag && lane == 0) record_abort(P, abort_flag, 4);
@@ -638,86 +668,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       float* const gslot = pc.gbuf + (int64_t)c.slot * C.slot_floats;
       const int roff = cube_row(x & 7, y & 7);
       const int zx = cube_zx(x & 7, y & 7);
-      if constexpr (is_ozaki(MODE) && GEMM_EPI_GROUPS == 2) {
-        if (P.rot) {
-          // levels 0 and 1 of this warp's (at most four) chunks into registers,
-          // their blocks released; then level 2 chunk by chunk, combined, stored
-          const uint32_t lane_q = tmem_base + ((uint32_t)(quad * 32) << 16);
-          const uint32_t t0 = lane_q + 128u * ((3u * tile_n) & 3u);
-          const uint32_t t1 = lane_q + 128u * ((3u * tile_n + 1u) & 3u);
-          const uint32_t t2 = lane_q + 128u * ((3u * tile_n + 2u) & 3u);
-          // Held as s = fl(L0 + L1) and e = (L0 + L1) - s.  L0 and L1 are exact
-          // integer multiples of the level-1 unit 2^-3beta, |L0 + L1| < 2^13 in
-          // either slice width, so e is an integer number of units with |e| <=
-          // 128: two per register as int16, exactly.
-          constexpr float EU = (float)(1u << (3 * MT::beta)), EU_INV = 1.f / EU;
-          float sv[4][16];
-          uint32_t ev[4][8];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int c0 = 16 * chunk0 + 32 * k;
-            if (c0 < C.NT) {
-              float l0[16], l1[16];
-              ptx::tmem_ld16x2(t0 + c0, t1 + c0, l0, l1);
-#pragma unroll
-              for (int j = 0; j < 16; j += 2) {
-                float s0, e0, s1, e1;
-                two_sum(l0[j], l1[j], s0, e0);
-                two_sum(l0[j + 1], l1[j + 1], s1, e1);
-                sv[k][j] = s0;
-                sv[k][j + 1] = s1;
-                ev[k][j >> 1] = ((uint32_t)__float2int_rn(e0 * EU) & 0xffffu) | ((uint32_t)__float2int_rn(e1 * EU) << 16);
-              }
-            }
-          }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&efree[tile_n & 1]);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int c0 = 16 * chunk0 + 32 * k;
-            if (c0 >= C.NT) break;
-            float ar[16];
-            ptx::tmem_ld16(t2 + c0, ar);
-            if (!valid) continue;
-            const int z = c.z0 + c0;
-            float hv[16], lv[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float s2 = sv[k][j];
-              const int eq = (j & 1) ? (int)ev[k][j >> 1] >> 16 : (int)(short)(ev[k][j >> 1] & 0xffffu);
-              const float e2 = (float)eq * EU_INV;
-              const float lo = __fadd_rn(e2, ar[j]);
-              const float hi = __fadd_rn(s2, lo);
-              hv[j] = hi * gscale;
-              lv[j] = __fsub_rn(lo, __fsub_rn(hi, s2)) * gscale;
-            }
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-              const int Z = (z >> 3) + h2;
-              if (Z < nb) {
-                int64_t bt;
-                unsigned mask;
-                orbit_slots(x >> 3, y >> 3, Z, &bt, &mask);
-                xor_permute8(hv + 8 * h2, zx);
-                xor_permute8(lv + 8 * h2, zx);
-                float* item = gslot + (bt * 18 + c.g * 6) * (512 * CWF);
-                for (int pid = 0; pid < 6; ++pid) {
-                  if (!((mask >> pid) & 1u)) continue;
-                  float* cube = item + pid * (512 * CWF);
-                  store8(cube + roff, hv + 8 * h2);
-                  store8(cube + 512 + roff, lv + 8 * h2);
-                }
-              }
-            }
-          }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&tempty[tile_n & 1]);
-          ++tile_n;
-          continue;
-        }
-      }
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * acc_stride;
       for (int c0 = 16 * chunk0; c0 < C.NT; c0 += 16 * GEMM_EPI_GROUPS) {
         const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
@@ -826,12 +776,6 @@ static te_status get_encoder(TcState* st) {
   return TE_OK;
 }
 
-// Exact-slice modes: N tiles of at most 128 columns in four rotating TMEM
-// blocks (the epilogue of one tile overlaps the next tile's MMAs)
-#ifndef TE_ROTATE_TILES
-#define TE_ROTATE_TILES 0
-#endif
-
 struct TcPlan {
   int mode, es, nparts, cw;
   int vp, op, vq;
@@ -840,7 +784,6 @@ struct TcPlan {
   int stages;
   uint32_t stage_bytes, a_part_bytes, b_part_bytes, tmem_cols;
   int nbuf;
-  int rot;
   int nslots;
   int ldz;
   size_t smem;
@@ -887,13 +830,12 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.TA = 128 / bestTB;
   pl.n_mx = (v + pl.TA - 1) / pl.TA;
   pl.n_my = (v + pl.TB - 1) / pl.TB;
-  const int ntmax = (oz && TE_ROTATE_TILES) ? 128 : std::min(256, (512 / (nacc * nbuf_max)) / 16 * 16);
+  const int ntmax = std::min(256, (512 / (nacc * nbuf_max)) / 16 * 16);
   pl.n_nt = (v + ntmax - 1) / ntmax;
   // a tuned split: any count whose N tile fits three accumulators in TMEM (N <= 160)
   if (force_nnt > 0 && round_up((v + force_nnt - 1) / force_nnt, 16) <= (oz ? 160 : 256)) pl.n_nt = force_nnt;
   pl.NT = round_up((v + pl.n_nt - 1) / pl.n_nt, 16);
-  pl.rot = (oz && TE_ROTATE_TILES && pl.NT <= 128) ? 1 : 0;
-  pl.nbuf = pl.rot ? 1 : ((2 * nacc * pl.NT <= 512) ? 2 : 1);
+  pl.nbuf = (2 * nacc * pl.NT <= 512) ? 2 : 1;
   pl.cbw = oz ? 64 : 128;
   pl.kw_elems = pl.cbw / pl.es;
   pl.kw_chunks = (pl.vp + pl.kw_elems - 1) / pl.kw_elems;
@@ -909,7 +851,7 @@ static TcPlan make_plan(const Handle* h, int o, int v, int mode, int64_t ntri, i
   pl.smem = (size_t)pl.stages * pl.stage_bytes + 1024 + 256;
   uint32_t cols = 32;
   while (cols < (uint32_t)(nacc * pl.nbuf * pl.NT)) cols <<= 1;
-  pl.tmem_cols = pl.rot ? 512u : cols;
+  pl.tmem_cols = cols;
   pl.ldz = round_up(v, 4);
   const int64_t tiles = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
   int64_t want = (4LL * std::max(1, h->num_sms) + tiles - 1) / tiles;
@@ -1077,27 +1019,133 @@ static te_status build_energy_maps(TcState* st, const TcPlan& pl, int o, int v, 
   return TE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// ovvv from density-fitting factors (t_energy_df):
+//   ovvv[p,x,y,d] = sum_P Bov[P,p,x] Bvv[P,y,d]
+// formed nst slabs at a time by the exact-slice strided GEMM (five 7-bit
+// slices per factor, K blocks of at most 1024 accumulated in float64) into a
+// float64 staging block, then cut into the contraction's operand form.
+// ---------------------------------------------------------------------------
+
+constexpr int DF_NS = 5;                                  // slices per factor
+constexpr size_t DF_STAGE_BYTES = size_t(2) << 30;        // staging block limit
+constexpr int64_t DF_KBLOCK = 1024;                       // exact level-0/1 sums
+
+// Scratch of the formation.  It shares the region of the G pool, which the
+// contraction only writes after every operand is ready (stream order).
+struct DfScratch {
+  __nv_bfloat16 *bov = nullptr, *bvv = nullptr;  // DF_NS planes each
+  unsigned long long* mx = nullptr;              // max |Bov|, max |Bvv| (bits)
+  int* ex = nullptr;                             // their scale exponents
+  double* stage = nullptr;                       // nst slabs of v^3
+  double* part = nullptr;                        // split-K partial tiles
+  int64_t part_cap = 0;
+  int nst = 0;
+};
+
+static size_t df_carve(char* base, int o, int v, int64_t naux, int num_sms, DfScratch* d) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = (off + 1023) & ~size_t(1023);
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t v3 = (size_t)v * v * v;
+  d->nst = (int)std::max<size_t>(1, std::min<size_t>((size_t)o, DF_STAGE_BYTES / (v3 * 8)));
+  d->bov = reinterpret_cast<__nv_bfloat16*>(take((size_t)DF_NS * naux * o * v * 2));
+  d->bvv = reinterpret_cast<__nv_bfloat16*>(take((size_t)DF_NS * naux * v * v * 2));
+  d->mx = reinterpret_cast<unsigned long long*>(take(16));
+  d->ex = reinterpret_cast<int*>(take(8));
+  d->stage = reinterpret_cast<double*>(take((size_t)d->nst * v3 * 8));
+  // the largest split-K scratch over the slab counts and K blocks that occur
+  int64_t cap = 0;
+  const int64_t kcs[2] = {std::min<int64_t>(naux, DF_KBLOCK), naux % DF_KBLOCK};
+  const int nes[2] = {d->nst, o % d->nst};
+  for (int64_t kc : kcs)
+    for (int ne : nes)
+      if (kc > 0 && ne > 0) cap = std::max(cap, gemm_oz_scratch((int64_t)ne * v, (int64_t)v * v, kc, num_sms));
+  d->part_cap = cap;
+  d->part = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(cap, 1) * 8));
+  return (off + 1023) & ~size_t(1023);
+}
+
+// slabs p0 .. p0+ne-1 of ovvv into the staging block ([p - p0][x][y][d])
+static cudaError_t df_form(const te_df* df, int o, int v, int p0, int ne, const DfScratch& d, int num_sms,
+                           cudaStream_t s, int64_t* launches) {
+  const int64_t P = df->naux, ov = (int64_t)o * v, vv = (int64_t)v * v;
+  for (int64_t k0 = 0; k0 < P; k0 += DF_KBLOCK) {
+    const int64_t kc = std::min<int64_t>(DF_KBLOCK, P - k0);
+    // rows m = (p, x) contiguous in Bov[P][o][v]; columns n = (y, d) contiguous in Bvv[P][v][v]
+    const OzView g{d.bov + k0 * ov + (int64_t)p0 * v, d.bvv + k0 * vv, P * ov, P * vv, d.stage,
+                   (int64_t)ne * v, 1, vv, kc, 1,
+                   1, 0, ov, 0,
+                   vv, 0, 1,
+                   vv, 0, 1,
+                   1.0, d.ex, d.ex + 1, k0 == 0 ? 1 : 0, DF_NS};
+    const cudaError_t e = gemm_oz(g, num_sms, d.part, d.part_cap, s, launches);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Operand planes of one cluster.  With df, ovvv comes from the factors (the
+// slabs are formed once for the maximum in the exact-slice modes, once for
+// the slices: the same bits both times); else from c->ovvv.
 template <int MODE>
-static cudaError_t launch_prep_tc(const te_cluster* c, const TcPlan& pl, const TcBuffers& b, cudaStream_t s) {
+static cudaError_t launch_prep_tc(const te_cluster* c, const TcPlan& pl, const TcBuffers& b, const te_df* df,
+                                  const DfScratch* dfs, int num_sms, cudaStream_t s, int64_t* launches) {
   const int o = (int)c->nocc, v = (int)c->nvir;
+  const int64_t v3 = (int64_t)v * v * v;
   const int* ex = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (df) {
+    e = slice_planes(df->Bov, df->naux * o * v, DF_NS, dfs->mx, dfs->ex, dfs->bov, s, launches);
+    if (e == cudaSuccess) e = slice_planes(df->Bvv, df->naux * v * v, DF_NS, dfs->mx + 1, dfs->ex + 1, dfs->bvv, s, launches);
+    if (e != cudaSuccess) return e;
+  }
   if (is_ozaki(MODE)) {
     cudaMemsetAsync(b.maxbits, 0, 4 * 8, s);
-    k_maxabs<<<1024, 256, 0, s>>>(c->ovvv, (int64_t)o * v * v * v, c->t2, (int64_t)o * o * v * v, c->ooov,
-                                  (int64_t)o * o * o * v, b.maxbits);
+    k_maxabs<<<1024, 256, 0, s>>>(df ? nullptr : c->ovvv, df ? 0 : (int64_t)o * v3, c->t2, (int64_t)o * o * v * v,
+                                  c->ooov, (int64_t)o * o * o * v, b.maxbits);
+    ++*launches;
+    for (int p0 = 0; df && p0 < o; p0 += dfs->nst) {
+      const int ne = std::min(dfs->nst, o - p0);
+      e = df_form(df, o, v, p0, ne, *dfs, num_sms, s, launches);
+      if (e != cudaSuccess) return e;
+      k_maxabs<<<1024, 256, 0, s>>>(dfs->stage, (int64_t)ne * v3, nullptr, 0, nullptr, 0, b.maxbits);
+      ++*launches;
+    }
     k_exponents<<<1, 1, 0, s>>>(b.maxbits, b.exps);
+    ++*launches;
     ex = b.exps;
   }
   const Parts A{{b.a[0], b.a[1], b.a[2], b.a[3], b.a[4]}}, B{{b.b[0], b.b[1], b.b[2], b.b[3], b.b[4]}};
   const Parts Lp{{b.l[0], b.l[1], b.l[2], b.l[3], b.l[4]}}, N{{b.n[0], b.n[1], b.n[2], b.n[3], b.n[4]}};
-  k_split_rows<MODE><<<gridn((int64_t)o * v * v * pl.vp), 256, 0, s>>>(c->ovvv, A, (int64_t)o * v * v, v, pl.vp, (int64_t)v * v,
-                                                                       ex, 0);
-  k_split_rows<MODE><<<gridn((int64_t)o * o * v * pl.vp), 256, 0, s>>>(c->t2, B, (int64_t)o * o * v, v, pl.vp, (int64_t)v,
-                                                                       ex, 1);
+  if (!df) {
+    k_split_rows<MODE><<<gridn((int64_t)o * v * v * pl.vp), 256, 0, s>>>(c->ovvv, A, (int64_t)o * v * v, v, pl.vp,
+                                                                         (int64_t)v * v, ex, 0);
+    ++*launches;
+  }
+  // one occupied index's slices of ovvv: nparts consecutive [v^2][vp] blocks
+  const size_t group = (size_t)pl.nparts * v * v * pl.vp * pl.es;
+  for (int p0 = 0; df && p0 < o; p0 += dfs->nst) {
+    const int ne = std::min(dfs->nst, o - p0);
+    e = df_form(df, o, v, p0, ne, *dfs, num_sms, s, launches);
+    if (e != cudaSuccess) return e;
+    Parts Ap{};
+    for (int k = 0; k < MAX_PARTS; ++k) Ap.p[k] = A.p[k] ? static_cast<char*>(A.p[k]) + (size_t)p0 * group : nullptr;
+    k_split_rows<MODE><<<gridn((int64_t)ne * v * v * pl.vp), 256, 0, s>>>(dfs->stage, Ap, (int64_t)ne * v * v, v,
+                                                                          pl.vp, (int64_t)v * v, ex, 0);
+    ++*launches;
+  }
+  k_split_rows<MODE><<<gridn((int64_t)o * o * v * pl.vp), 256, 0, s>>>(c->t2, B, (int64_t)o * o * v, v, pl.vp,
+                                                                       (int64_t)v, ex, 1);
   k_split_t2L<MODE><<<gridn((int64_t)o * v * v * pl.op), 256, 0, s>>>(c->t2, Lp, o, v, pl.op, ex, 2);
   k_split_noo<MODE><<<gridn((int64_t)o * o * v * pl.op), 256, 0, s>>>(c->ooov, N, o, v, pl.op, ex, 3);
   k_ovs32<<<gridn((int64_t)o * v * o * pl.vq), 256, 0, s>>>(c->ovov, b.ovs32, o, v, pl.vq);
   k_small_copies<<<gridn((int64_t)o * pl.vq), 256, 0, s>>>(c->t1, b.t1_32, o, v, pl.vq);
+  *launches += 5;
   return cudaGetLastError();
 }
 
@@ -1120,12 +1168,13 @@ static cudaError_t launch_gemm_any(int mode, const TcMapSet& M, const TcParams& 
 }
 
 static cudaError_t launch_prep_any(int mode, const te_cluster* c, const TcPlan& pl, const TcBuffers& b,
-                                   cudaStream_t s) {
-  if (mode == TC_BF16X3) return launch_prep_tc<TC_BF16X3>(c, pl, b, s);
-  if (mode == TC_TF32X3) return launch_prep_tc<TC_TF32X3>(c, pl, b, s);
-  if (mode == TC_TF32) return launch_prep_tc<TC_TF32>(c, pl, b, s);
-  if (mode == TC_OZAKI) return launch_prep_tc<TC_OZAKI>(c, pl, b, s);
-  return launch_prep_tc<TC_OZAKI6>(c, pl, b, s);
+                                   const te_df* df, const DfScratch* dfs, int num_sms, cudaStream_t s,
+                                   int64_t* launches) {
+  if (mode == TC_BF16X3) return launch_prep_tc<TC_BF16X3>(c, pl, b, df, dfs, num_sms, s, launches);
+  if (mode == TC_TF32X3) return launch_prep_tc<TC_TF32X3>(c, pl, b, df, dfs, num_sms, s, launches);
+  if (mode == TC_TF32) return launch_prep_tc<TC_TF32>(c, pl, b, df, dfs, num_sms, s, launches);
+  if (mode == TC_OZAKI) return launch_prep_tc<TC_OZAKI>(c, pl, b, df, dfs, num_sms, s, launches);
+  return launch_prep_tc<TC_OZAKI6>(c, pl, b, df, dfs, num_sms, s, launches);
 }
 
 // One cluster of a run: its plan, buffers, tensor maps and triple range.
@@ -1188,10 +1237,9 @@ static te_status gemm_params(const Handle* h, const std::vector<TcJob>& jobs, co
   if (P->stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
   P->nbuf = p0.nbuf;
   P->nt_max = nt_max;
-  P->rot = p0.rot;
   uint32_t cols = 32;
   while (cols < (uint32_t)(nacc * P->nbuf * nt_max)) cols <<= 1;
-  P->tmem_cols = P->rot ? 512u : cols;
+  P->tmem_cols = cols;
   P->total_tiles = tiles;
   P->triples = h->d_triples;
   P->err = h->d_err;
@@ -1238,14 +1286,14 @@ static te_status run_rounds(Handle* h, std::vector<TcJob>& jobs, int mode, float
       for (int q = 0; q < ncl; ++q)
         if (jl[q] == (int)j) cl = q;
       if (cl < 0) {
-        if (ncl == TC_MAX_CL || (nbuf >= 0 && J.pl.nbuf + 4 * J.pl.rot != nbuf)) break;
+        if (ncl == TC_MAX_CL || (nbuf >= 0 && J.pl.nbuf != nbuf)) break;
         cl = ncl;
       }
       const int64_t fit = std::min((pq.pool_floats - used) / J.slot_floats, pq.max_slots - nslots);
       if (fit <= 0) break;
       if (cl == ncl) {
         jl[ncl++] = (int)j;
-        nbuf = J.pl.nbuf + 4 * J.pl.rot;  // one TMEM scheme per launch
+        nbuf = J.pl.nbuf;  // one TMEM buffering per launch
       }
       const int ns = (int)std::min<int64_t>(fit, J.t_end - t);
       TcPiece pc{};
@@ -1326,7 +1374,8 @@ static te_status run_rounds(Handle* h, std::vector<TcJob>& jobs, int mode, float
 
 // Plan, buffers (carved from base), operand preparation and maps of one job.
 static te_status setup_job(Handle* h, TcState* st, const te_cluster* c, int mode, int64_t t_begin, int64_t t_end,
-                           const TcPlan& pl, char* base, TcJob* J, cudaStream_t s) {
+                           const TcPlan& pl, char* base, TcJob* J, cudaStream_t s, const te_df* df = nullptr,
+                           const DfScratch* dfs = nullptr) {
   J->c = c;
   J->pl = pl;
   J->o = (int)c->nocc;
@@ -1338,8 +1387,7 @@ static te_status setup_job(Handle* h, TcState* st, const te_cluster* c, int mode
   J->tiles_per_triple = 3LL * pl.n_mx * pl.n_my * pl.n_nt;
   tc_carve_cluster(base, pl, J->o, J->v, num_unique_triples(J->o), &J->b);
   J->shares = J->b.etri;
-  const cudaError_t e = launch_prep_any(mode, c, pl, J->b, s);
-  h->n_launches += is_ozaki(mode) ? 7 : 5;
+  const cudaError_t e = launch_prep_any(mode, c, pl, J->b, df, dfs, h->num_sms, s, &h->n_launches);
   if (e != cudaSuccess) return fail(TE_ECUDA, "operand split launch: %s", cudaGetErrorString(e));
   te_status rs = build_maps(st, pl, J->o, J->v, J->b, &J->maps);
   if (rs != TE_OK) return rs;
@@ -1362,18 +1410,35 @@ static TcPool single_pool(const TcPlan& pl, int v) {
   return q;
 }
 
-size_t tc_slices_bytes(int o, int v) {
-  const size_t vp = (size_t)round_up(v, 16), op = (size_t)round_up(o, 16), NS = 4, es = 2;
+size_t tc_slices_bytes(int o, int v, int ns) {
+  const size_t vp = (size_t)round_up(v, 16), op = (size_t)round_up(o, 16), NS = (size_t)ns, es = 2;
   const size_t na = (size_t)o * v * v * vp, nb = (size_t)o * o * v * vp;
   const size_t nl = (size_t)o * v * v * op, nn = (size_t)o * o * v * op;
   auto al = [](size_t b) { return (b + 1023) & ~size_t(1023); };
-  return al(NS * na * es) + al(NS * nb * es) + al(NS * nl * es) + al(NS * nn * es) + al(64) + al(64) + 1024;
+  const size_t ng = 2 * (size_t)o + 2 * (size_t)o * o;  // row groups of the four arrays
+  return al(NS * na * es) + al(NS * nb * es) + al(NS * nl * es) + al(NS * nn * es) + al(ng * 8) + al(ng * 4) + 1024;
 }
 
-te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, cudaStream_t s) {
+template <int MODE>
+static void launch_slice_set(const te_cluster* c, int vp, int op, const Parts& pa, const Parts& pb, const Parts& pL,
+                             const Parts& pN, const int* e_ovvv, const int* e_t2, const int* e_t2L,
+                             const int* e_nooT, cudaStream_t s) {
+  const int o = (int)c->nocc, v = (int)c->nvir;
+  const int64_t v2 = (int64_t)v * v;
+  k_split_rows<MODE><<<gridn((int64_t)o * v * v * vp), 256, 0, s>>>(c->ovvv, pa, (int64_t)o * v * v, v, vp, v2,
+                                                                    nullptr, 0, e_ovvv);
+  k_split_rows<MODE><<<gridn((int64_t)o * o * v * vp), 256, 0, s>>>(c->t2, pb, (int64_t)o * o * v, v, vp,
+                                                                    (int64_t)v, nullptr, 1, e_t2);
+  k_split_t2L<MODE><<<gridn((int64_t)o * v * v * op), 256, 0, s>>>(c->t2, pL, o, v, op, nullptr, 2, e_t2L);
+  k_split_noo<MODE><<<gridn((int64_t)o * o * v * op), 256, 0, s>>>(c->ooov, pN, o, v, op, nullptr, 3, e_nooT);
+}
+
+te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, int num_sms, cudaStream_t s,
+                            int ns) {
   const int o = (int)c->nocc, v = (int)c->nvir;
   const int vp = round_up(v, 16), op = round_up(o, 16);
-  constexpr int NS = 4;
+  if (ns != 4 && ns != 5) return fail(TE_EINVAL, "slice count %d (4 or 5)", ns);
+  const int NS = ns;
   const size_t es = 2;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base_v) + 1023) & ~uintptr_t(1023));
   size_t off = 0;
@@ -1389,8 +1454,13 @@ te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, cu
   char* B = take(NS * nb * es);
   char* L = take(NS * nl * es);
   char* N = take(NS * nn * es);
-  auto* maxbits = reinterpret_cast<unsigned long long*>(take(64));
-  int* exps = reinterpret_cast<int*>(take(64));
+  const int64_t oo = (int64_t)o * o, ng = 2 * (int64_t)o + 2 * oo;
+  auto* maxbits = reinterpret_cast<unsigned long long*>(take((size_t)ng * 8));
+  int* exps = reinterpret_cast<int*>(take((size_t)ng * 4));
+  int* e_ovvv = exps;           // [o]
+  int* e_t2 = e_ovvv + o;       // [o o]
+  int* e_t2L = e_t2 + oo;       // [o]
+  int* e_nooT = e_t2L + o;      // [o o]
   Parts pa{}, pb{}, pL{}, pN{};
   for (int k = 0; k < NS; ++k) {
     pa.p[k] = A + (size_t)k * v * v * vp * es;
@@ -1398,16 +1468,18 @@ te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, cu
     pL.p[k] = L + (size_t)k * v * v * op * es;
     pN.p[k] = N + (size_t)k * v * op * es;
   }
-  cudaMemsetAsync(maxbits, 0, 4 * 8, s);
-  k_maxabs<<<1024, 256, 0, s>>>(c->ovvv, (int64_t)o * v * v * v, c->t2, (int64_t)o * o * v * v, c->ooov,
-                                (int64_t)o * o * o * v, maxbits);
-  k_exponents<<<1, 1, 0, s>>>(maxbits, exps);
-  k_split_rows<TC_OZAKI><<<gridn((int64_t)o * v * v * vp), 256, 0, s>>>(c->ovvv, pa, (int64_t)o * v * v, v, vp,
-                                                                        (int64_t)v * v, exps, 0);
-  k_split_rows<TC_OZAKI><<<gridn((int64_t)o * o * v * vp), 256, 0, s>>>(c->t2, pb, (int64_t)o * o * v, v, vp,
-                                                                        (int64_t)v, exps, 1);
-  k_split_t2L<TC_OZAKI><<<gridn((int64_t)o * v * v * op), 256, 0, s>>>(c->t2, pL, o, v, op, exps, 2);
-  k_split_noo<TC_OZAKI><<<gridn((int64_t)o * o * v * op), 256, 0, s>>>(c->ooov, pN, o, v, op, exps, 3);
+  // one scale per row group (each strided GEMM reads one group of each
+  // operand), so a block far below the array's largest keeps its 28 bits
+  cudaMemsetAsync(maxbits, 0, (size_t)ng * 8, s);
+  const int64_t v2 = (int64_t)v * v, chunk = 65536;
+  const int gm = 4 * std::max(1, num_sms);
+  k_group_maxabs<<<gm, 256, 0, s>>>(c->ovvv, 0, o, v, v2 * v, o, chunk, maxbits);
+  k_group_maxabs<<<gm, 256, 0, s>>>(c->t2, 1, o, v, v2, oo, chunk, maxbits + o);
+  k_group_maxabs<<<gm, 256, 0, s>>>(c->t2, 2, o, v, (int64_t)o * v2, o, chunk, maxbits + o + oo);
+  k_group_maxabs<<<gm, 256, 0, s>>>(c->ooov, 3, o, v, (int64_t)o * v, oo, chunk, maxbits + 2 * o + oo);
+  k_group_exps<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(maxbits, ng, exps);
+  if (NS == 5) launch_slice_set<TC_SLICE5>(c, vp, op, pa, pb, pL, pN, e_ovvv, e_t2, e_t2L, e_nooT, s);
+  else launch_slice_set<TC_OZAKI>(c, vp, op, pa, pb, pL, pN, e_ovvv, e_t2, e_t2L, e_nooT, s);
   if (cudaGetLastError() != cudaSuccess) return fail(TE_ECUDA, "slice preparation launch failed");
   out->ovvv = A;
   out->t2 = B;
@@ -1423,15 +1495,22 @@ te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, cu
   out->nooT_pr = NS * (int64_t)v * op;
   out->vp = vp;
   out->op = op;
-  out->exps = exps;
+  out->ns = NS;
+  out->e_ovvv = e_ovvv;
+  out->e_t2 = e_t2;
+  out->e_t2L = e_t2L;
+  out->e_nooT = e_nooT;
   return TE_OK;
 }
 
-te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, size_t* bytes) {
+te_status tc_workspace_bytes(Handle* h, const te_cluster* c, te_precision p, size_t* bytes, const te_df* df) {
   const int o = (int)c->nocc, v = (int)c->nvir;
   const TcPlan pl = make_plan(h, o, v, tc_mode_of(p, o, v, h->ozaki_bits), num_unique_triples(c->nocc));
   TcBuffers b;
-  *bytes = tc_carve_cluster(nullptr, pl, o, v, num_unique_triples(o), &b) + tc_shared_bytes(single_pool(pl, v), h->num_sms);
+  DfScratch d;
+  const size_t region = std::max(tc_shared_bytes(single_pool(pl, v), h->num_sms),
+                                 df ? df_carve(nullptr, o, v, df->naux, h->num_sms, &d) : size_t(0));
+  *bytes = tc_carve_cluster(nullptr, pl, o, v, num_unique_triples(o), &b) + region;
   return TE_OK;
 }
 
@@ -1513,7 +1592,7 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
     const size_t cbytes = tc_carve_cluster(wbase, pl, o, v, nt, &J.b);
     cudaError_t e = cudaSuccess;
     if (!prepped) {  // the operand planes sit first in the workspace for every candidate
-      e = launch_prep_any(mode, c, pl, J.b, s);
+      e = launch_prep_any(mode, c, pl, J.b, nullptr, nullptr, h->num_sms, s, &h->n_launches);
       prepped = true;
     }
     if (e != cudaSuccess || build_maps(st, pl, o, v, J.b, &J.maps) != TE_OK) continue;
@@ -1559,7 +1638,7 @@ te_status tc_autotune(Handle* h, const te_cluster* c, te_precision p, cudaStream
 }
 
 te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin, int64_t t_end,
-                 double* e_tri_out, double* e_total_out, cudaStream_t s) {
+                 double* e_tri_out, double* e_total_out, cudaStream_t s, const te_df* df) {
   if (h->cc_major != 10 && h->cc_major != 11)
     return fail(TE_EUNSUPPORTED, "tensor-core modes need an sm_100-family GPU (found sm_%d%d)", h->cc_major,
                 h->cc_minor);
@@ -1576,7 +1655,9 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   TcBuffers b;
   const TcPool pq = single_pool(pl, v);
   const size_t cbytes = tc_carve_cluster(nullptr, pl, o, v, ntri, &b);
-  const size_t bytes = cbytes + tc_shared_bytes(pq, h->num_sms);
+  DfScratch dfs;
+  const size_t bytes = cbytes + std::max(tc_shared_bytes(pq, h->num_sms),
+                                         df ? df_carve(nullptr, o, v, df->naux, h->num_sms, &dfs) : size_t(0));
   if (h->log)
     std::fprintf(stderr,
                  "[tenergy] plan nocc=%d nvir=%d mode=%d: M tile %d x %d, N tile %d (%d per row block), %d stages "
@@ -1589,7 +1670,8 @@ te_status run_tc(Handle* h, const te_cluster* c, te_precision p, int64_t t_begin
   if (rs != TE_OK) return rs;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023));
   std::vector<TcJob> jobs(1);
-  rs = setup_job(h, st, c, mode, t_begin, t_end, pl, base, &jobs[0], s);
+  if (df) df_carve(base + cbytes, o, v, df->naux, h->num_sms, &dfs);  // over the G pool, before its first use
+  rs = setup_job(h, st, c, mode, t_begin, t_end, pl, base, &jobs[0], s, df, df ? &dfs : nullptr);
   if (rs != TE_OK) return rs;
   if (e_tri_out) jobs[0].shares = e_tri_out;  // shares[t - t_begin]
   else jobs[0].shares = jobs[0].b.etri;

@@ -24,9 +24,11 @@ enum : unsigned int {
 
 // Device-side input value checks of one cluster (checks.cu): every entry
 // finite and max(eps_o) < min(eps_v); a violation sets ERR_BAD_INPUT with the
-// site (1..7 the array, 8 the eps ordering) and `cluster` in the error word.
+// site (1..7 the array, 8 the eps ordering, 9 and 10 the density-fitting
+// factors) and `cluster` in the error word.  With df, ovvv is not checked
+// (not read) and Bov, Bvv are.
 cudaError_t launch_check_inputs(const te_cluster* c, int64_t cluster, unsigned int* err, int num_sms,
-                                cudaStream_t s);
+                                cudaStream_t s, const te_df* df = nullptr);
 // The same for the MP2 step's inputs (eps_o, eps_v, and the DF factor's ov
 // block of nB entries, site 9).
 cudaError_t launch_check_mp2(const double* eps_o, int64_t o, const double* eps_v, int64_t v, const double* Bov,

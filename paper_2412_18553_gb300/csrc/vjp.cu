@@ -237,16 +237,17 @@ cudaError_t gemm_strided(const GemmView& g, int num_sms, double* scratch, int64_
 // ---------------------------------------------------------------------------
 // exact-slice strided GEMM on the tensor cores (mma.sync, BF16 -> FP32):
 //   C[m,n] (+)= alpha 2^(ea + eb) sum_k A[m,k] B[k,n]
-// A and B are four BF16 slice planes each (slice s at base + s * plane), read
-// through the same two-index strided views as the float64 kernel.  The ten
-// slice products a_i b_j with i + j <= 3 go to three FP32 accumulators:
+// A and B are NS BF16 slice planes each (slice s at base + s * plane; NS = 4,
+// or 5 for 35-bit operands), read through the same two-index strided views as
+// the float64 kernel.  The slice products a_i b_j with i + j <= NS - 1 (ten,
+// or fifteen) go to three FP32 accumulators:
 // level 0 and level 1 exactly (K <= 1024 per block keeps their partial sums
 // integer multiples of the level's unit below 2^24), the higher levels
 // approximately; each block's sums go to float64 once, at its end.
 // ---------------------------------------------------------------------------
 
 
-constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_KMAX = 1024, OZ_NS = 4;
+constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_KMAX = 1024;
 constexpr int OZ_THREADS = 256;  // eight warps, each 32 x 16 outputs
 constexpr int OZ_LD = OZ_BK + 8;  // padded row (bf16): conflict-free fragment loads
 
@@ -263,11 +264,11 @@ __device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, cons
 // contiguous along k, else row-major ([k][row]) when contiguous along its rows
 // (columns); 16-byte chunks of eight BF16 values are copied asynchronously
 // where the view allows, element by element otherwise.
-template <bool AK, bool BK>
+template <bool AK, bool BK, int NS>
 struct OzTile {
   static constexpr int A = AK ? OZ_BM * OZ_LD : OZ_BK * (OZ_BM + 8);
   static constexpr int B = BK ? OZ_BN * OZ_LD : OZ_BK * (OZ_BN + 8);
-  static constexpr int STAGE = OZ_NS * (A + B);  // elements
+  static constexpr int STAGE = NS * (A + B);  // elements
   static constexpr size_t BYTES = 2 * STAGE * sizeof(__nv_bfloat16);
 };
 
@@ -296,8 +297,8 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const __nv_bfloat16* p) {
 // contiguous index.  Rolled loops, so the pipelined loop stays small enough
 // for the instruction cache.
 __device__ __forceinline__ void oz_fill_slow(const __nv_bfloat16* __restrict__ src, int64_t ps, __nv_bfloat16* dst,
-                                          int dps, int r, int k, int step_r, int step_k, int R, int ke, int R2,
-                                          int64_t r1s, int64_t r2s, int K2, int64_t k1s, int64_t k2s) {
+                                          int dps, int ns, int r, int k, int step_r, int step_k, int R, int ke,
+                                          int R2, int64_t r1s, int64_t r2s, int K2, int64_t k1s, int64_t k2s) {
 #pragma unroll 1
   for (int e = 0; e < 8; ++e) {
     const int rr = r + e * step_r, kk = k + e * step_k;
@@ -306,14 +307,14 @@ __device__ __forceinline__ void oz_fill_slow(const __nv_bfloat16* __restrict__ s
         ok ? (int64_t)(rr / R2) * r1s + (int64_t)(rr % R2) * r2s + (int64_t)(kk / K2) * k1s + (int64_t)(kk % K2) * k2s
            : 0;
 #pragma unroll 1
-    for (int sl = 0; sl < OZ_NS; ++sl) dst[sl * dps + e] = ok ? src[off + sl * ps] : __float2bfloat16_rn(0.f);
+    for (int sl = 0; sl < ns; ++sl) dst[sl * dps + e] = ok ? src[off + sl * ps] : __float2bfloat16_rn(0.f);
   }
 }
 
-template <bool AK, bool BK>
+template <bool AK, bool BK, int NS>
 __global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk, double* __restrict__ part,
                                                             int a_vec, int b_vec) {
-  using T = OzTile<AK, BK>;
+  using T = OzTile<AK, BK, NS>;
   extern __shared__ __align__(16) unsigned char oz_smem[];
   __nv_bfloat16* smem = reinterpret_cast<__nv_bfloat16*>(oz_smem);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk
   // one 8-element chunk: elements e = 0..7 along the tile's contiguous direction
   auto load_stage = [&](int buf, int k0) {
     __nv_bfloat16* As = smem + buf * T::STAGE;
-    __nv_bfloat16* Bs = As + OZ_NS * T::A;
+    __nv_bfloat16* Bs = As + NS * T::A;
 #pragma unroll
     for (int c2 = 0; c2 < OZ_CH; ++c2) {
       const int c = tid + OZ_THREADS * c2;
@@ -364,10 +365,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk
         if (full) {
           const __nv_bfloat16* src = g.A + a_roff[c2] + a_kof(k);
 #pragma unroll
-          for (int sl = 0; sl < OZ_NS; ++sl) cp_async16(dst0 + sl * T::A, src + sl * g.a_ps);
+          for (int sl = 0; sl < NS; ++sl) cp_async16(dst0 + sl * T::A, src + sl * g.a_ps);
         } else {
-          oz_fill_slow(g.A, g.a_ps, dst0, T::A, m, k, step_m, step_k, M, ke, (int)g.M2, g.a_m1, g.a_m2, K2, g.a_k1,
-                       g.a_k2);
+          oz_fill_slow(g.A, g.a_ps, dst0, T::A, NS, m, k, step_m, step_k, M, ke, (int)g.M2, g.a_m1, g.a_m2, K2,
+                       g.a_k1, g.a_k2);
         }
       }
       // ---- B ----
@@ -391,9 +392,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk
         if (full) {
           const __nv_bfloat16* src = g.B + (int64_t)n * g.b_n + b_kof(k);
 #pragma unroll
-          for (int sl = 0; sl < OZ_NS; ++sl) cp_async16(dst0 + sl * T::B, src + sl * g.b_ps);
+          for (int sl = 0; sl < NS; ++sl) cp_async16(dst0 + sl * T::B, src + sl * g.b_ps);
         } else {
-          oz_fill_slow(g.B, g.b_ps, dst0, T::B, n, k, step_n, step_k, N, ke, 1, g.b_n, 0, K2, g.b_k1, g.b_k2);
+          oz_fill_slow(g.B, g.b_ps, dst0, T::B, NS, n, k, step_n, step_k, N, ke, 1, g.b_n, 0, K2, g.b_k1, g.b_k2);
         }
       }
     }
@@ -419,14 +420,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk
     cp_async_wait1();  // every group but the newest: this stage's copies have landed
     __syncthreads();
     const __nv_bfloat16* As = smem + (st & 1) * T::STAGE;
-    const __nv_bfloat16* Bs = As + OZ_NS * T::A;
+    const __nv_bfloat16* Bs = As + NS * T::A;
 #pragma unroll
     for (int kk = 0; kk < OZ_BK; kk += 16) {
       // ldmatrix: lane l addresses row (l & 7) of 8 x 8 matrix (l >> 3)
       const int lr = lane & 7, lm = lane >> 3;
-      uint32_t bf[OZ_NS][2][2];
+      uint32_t bf[NS][2][2];
 #pragma unroll
-      for (int sl = 0; sl < OZ_NS; ++sl) {
+      for (int sl = 0; sl < NS; ++sl) {
         // matrices: (cols 0-7, k kk), (cols 0-7, k kk+8), (cols 8-15, k kk), (cols 8-15, k kk+8)
         const __nv_bfloat16* b = Bs + sl * T::B;
         uint32_t t[4];
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk
         bf[sl][1][1] = t[3];
       }
 #pragma unroll
-      for (int sa = 0; sa < OZ_NS; ++sa) {
+      for (int sa = 0; sa < NS; ++sa) {
         uint32_t af[2][4];  // A slice sa, loaded when its products are due
         const __nv_bfloat16* a = As + sa * T::A;
 #pragma unroll
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) k_gemm_oz2(OzView g, int kchunk
           else ldsm_x4_t(af[i], a + (kk + lr + (lm >> 1) * 8) * (OZ_BM + 8) + r + (lm & 1) * 8);
         }
 #pragma unroll
-        for (int sb = 0; sb < OZ_NS - sa; ++sb) {
+        for (int sb = 0; sb < NS - sa; ++sb) {
           const int lev = sa + sb == 0 ? 0 : (sa + sb == 1 ? 1 : 2);
 #pragma unroll
           for (int i = 0; i < 2; ++i)
@@ -512,20 +513,20 @@ __global__ void k_splitk_add_oz(OzView g, int nsplit, const double* __restrict__
   }
 }
 
-template <bool AK, bool BK>
+template <bool AK, bool BK, int NS>
 static cudaError_t launch_oz2(const OzView& g, dim3 grid, int kchunk, double* part, int av, int bv, cudaStream_t s) {
-  const size_t bytes = OzTile<AK, BK>::BYTES;
+  const size_t bytes = OzTile<AK, BK, NS>::BYTES;
   static std::atomic<unsigned long long> opted{0};  // devices this instantiation may use `bytes` on
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(opted.load() & bit)) {
-    e = cudaFuncSetAttribute(k_gemm_oz2<AK, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = cudaFuncSetAttribute(k_gemm_oz2<AK, BK, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     opted.fetch_or(bit);
   }
-  k_gemm_oz2<AK, BK><<<grid, OZ_THREADS, bytes, s>>>(g, kchunk, part, av, bv);
+  k_gemm_oz2<AK, BK, NS><<<grid, OZ_THREADS, bytes, s>>>(g, kchunk, part, av, bv);
   return cudaGetLastError();
 }
 
@@ -572,10 +573,19 @@ cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scrat
   const bool AK = !a_m, BK = !b_n;
   const int av = (a_k || a_m) ? 1 : 0, bv = (b_k || b_n) ? 1 : 0;
   cudaError_t err;
-  if (AK && BK) err = launch_oz2<true, true>(g, grid, kchunk, pp, av, bv, s);
-  else if (AK) err = launch_oz2<true, false>(g, grid, kchunk, pp, av, bv, s);
-  else if (BK) err = launch_oz2<false, true>(g, grid, kchunk, pp, av, bv, s);
-  else err = launch_oz2<false, false>(g, grid, kchunk, pp, av, bv, s);
+  if (g.ns == 5) {
+    if (AK && BK) err = launch_oz2<true, true, 5>(g, grid, kchunk, pp, av, bv, s);
+    else if (AK) err = launch_oz2<true, false, 5>(g, grid, kchunk, pp, av, bv, s);
+    else if (BK) err = launch_oz2<false, true, 5>(g, grid, kchunk, pp, av, bv, s);
+    else err = launch_oz2<false, false, 5>(g, grid, kchunk, pp, av, bv, s);
+  } else if (g.ns == 0 || g.ns == 4) {
+    if (AK && BK) err = launch_oz2<true, true, 4>(g, grid, kchunk, pp, av, bv, s);
+    else if (AK) err = launch_oz2<true, false, 4>(g, grid, kchunk, pp, av, bv, s);
+    else if (BK) err = launch_oz2<false, true, 4>(g, grid, kchunk, pp, av, bv, s);
+    else err = launch_oz2<false, false, 4>(g, grid, kchunk, pp, av, bv, s);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   if (err != cudaSuccess) return err;
   ++*launches;
   if (nsplit > 1) {
@@ -586,7 +596,52 @@ cudaError_t gemm_oz(const OzView& g, int num_sms, double* scratch, int64_t scrat
   return cudaGetLastError();
 }
 
-// four BF16 slices of dW~ (same layout), scale 2^-e with 2^e > max |dW~|
+// max |x| as the bit pattern of a non-negative double (they order as integers)
+__global__ void k_maxabs_bits(const double* __restrict__ x, int64_t n, unsigned long long* out) {
+  double m = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[idx]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// NS 7-bit BF16 slices of x (slice s at planes + s n): x = 2^e sum_s m_s
+// 2^-7(s+1) + r, 2^e > max |x|, |r| <= 2^(e - 7 NS - 1)
+template <int NS>
+__global__ void k_slice_planes(const double* __restrict__ x, int64_t n, const unsigned long long* __restrict__ xmax,
+                               int* __restrict__ e_out, __nv_bfloat16* __restrict__ planes) {
+  const double mx = __longlong_as_double((long long)*xmax);
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *e_out = ex;
+  const double sc = ldexp(1.0, -ex);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double t = x[i] * sc;  // |t| < 1
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      t = t * 128.0;
+      const double m = rint(t);
+      t = t - m;
+      planes[k * n + i] = __float2bfloat16_rn((float)(m * (1.0 / (double)(1ull << (7 * (k + 1))))));
+    }
+  }
+}
+
+cudaError_t slice_planes(const double* x, int64_t n, int ns, unsigned long long* mx, int* ex,
+                         __nv_bfloat16* planes, cudaStream_t s, int64_t* launches) {
+  if (ns != 4 && ns != 5) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(mx, 0, 8, s);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 8192);
+  k_maxabs_bits<<<std::min(grid, 1024), 256, 0, s>>>(x, n, mx);
+  if (ns == 5) k_slice_planes<5><<<grid, 256, 0, s>>>(x, n, mx, ex, planes);
+  else k_slice_planes<4><<<grid, 256, 0, s>>>(x, n, mx, ex, planes);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+// NS 7-bit BF16 slices of dW~ (same layout), scale 2^-e with 2^e > max |dW~|
+template <int NS>
 __global__ void k_slice_dw(const double* __restrict__ dW, int64_t n, const unsigned long long* __restrict__ dwmax,
                            int* __restrict__ e_out, __nv_bfloat16* __restrict__ planes) {
   const double mx = __longlong_as_double((long long)*dwmax);
@@ -597,7 +652,7 @@ __global__ void k_slice_dw(const double* __restrict__ dW, int64_t n, const unsig
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double t = dW[i] * sc;  // |t| < 1
 #pragma unroll
-    for (int k = 0; k < OZ_NS; ++k) {
+    for (int k = 0; k < NS; ++k) {
       t = t * 128.0;
       const double m = rint(t);
       t = t - m;
@@ -914,12 +969,20 @@ int64_t oz_scratch_cap(int64_t o, int64_t v, int num_sms) {
   return splits * std::max(v * v, o * v);
 }
 
+// Slices per element in the exact-slice adjoint: four (28 bits) up to nvir =
+// 200, five (35 bits) above.  Its back-contractions sum v (or v^2) products
+// whose largest terms can sit far above the result, and the rows of t2 and
+// ovvv away from the occupied-virtual boundary far below their scale; at
+// nocc=48 nvir=560 four slices left errors of 2.7e-6 of d ovvv's largest entry.
+static int adjoint_slices(int64_t v) { return v > 200 ? 5 : 4; }
+
 size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms) {
   const int64_t v3 = v * v * v, nt = num_unique_triples(o);
   const int64_t nblk = (v3 + 255) / 256;
+  const int ns = adjoint_slices(v);
   auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
-  return tc_slices_bytes((int)o, (int)v) + 1024 + a(o * v * o * v) +
-         a(3 * v3) + 3 * a(v3) + a(v3) /* dW slices: 4 x 2 B */ + a(o * v * o * v) + 2 * a(nblk) +
+  return tc_slices_bytes((int)o, (int)v, ns) + 1024 + a(o * v * o * v) +
+         a(3 * v3) + 3 * a(v3) + a((v3 * ns + 3) / 4) /* dW slices: ns x 2 B */ + a(o * v * o * v) + 2 * a(nblk) +
          a(std::max<int64_t>(1, nt)) + a(oz_scratch_cap(o, v, num_sms)) + a(4) + 1024;
 }
 
@@ -933,9 +996,10 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
   if (st != TE_OK) return st;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023));
   SliceSet S;
-  st = tc_prepare_slices(c, base, &S, s);
+  const int ns = adjoint_slices(v);
+  st = tc_prepare_slices(c, base, &S, h->num_sms, s, ns);
   if (st != TE_OK) return st;
-  char* p = base + ((tc_slices_bytes(o, v) + 1023) & ~size_t(1023));
+  char* p = base + ((tc_slices_bytes(o, v, ns) + 1023) & ~size_t(1023));
   auto take = [&](int64_t n) {
     double* r = reinterpret_cast<double*>(p);
     p += ((size_t)n * 8 + 255) & ~size_t(255);
@@ -949,7 +1013,7 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
   W.dW = take(v3);
   W.dY = take(v3);
   W.dD = take(v3);
-  __nv_bfloat16* dWs = reinterpret_cast<__nv_bfloat16*>(take(v3));  // 4 planes of v^3 BF16
+  __nv_bfloat16* dWs = reinterpret_cast<__nv_bfloat16*>(take((v3 * ns + 3) / 4));  // ns planes of v^3 BF16
   W.dOVS = take((int64_t)o * v * o * v);
   const int64_t nblk = (v3 + 255) / 256;
   W.epart = take(nblk);
@@ -995,10 +1059,15 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
   const bf* sL = static_cast<const bf*>(S.t2L);
   const bf* sN = static_cast<const bf*>(S.nooT);
   const int64_t vp = S.vp, op = S.op;
-  const int* EX = S.exps;  // 0 ovvv, 1 t2, 2 t2L, 3 nooT
+  // scale exponents of the row groups each GEMM reads
+  auto eO = [&](int p_) { return S.e_ovvv + p_; };
+  auto eT = [&](int r_, int q_) { return S.e_t2 + ((int64_t)r_ * o + q_); };
+  auto eL = [&](int q_) { return S.e_t2L + q_; };
+  auto eN = [&](int p_, int r_) { return S.e_nooT + ((int64_t)p_ * o + r_); };
 
   std::vector<Triple> trip = unique_triples(o);
-  auto run = [&](const OzView& gv) {
+  auto run = [&](OzView gv) {
+    gv.ns = ns;
     if (e == cudaSuccess) e = gemm_oz(gv, h->num_sms, W.splitk, cap, s, &h->n_launches);
   };
   // The order of the two row indices (or of the two k indices) of a view is a
@@ -1028,16 +1097,16 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
       double* Gg = W.G + gi * v3;
       // S1: sum_d ovvv[p,x,y,d] t2[r,q,z,d]
       run(OzView{sO + pp * S.ovvv_p, sT + ((int64_t)rr * o + qq) * S.t2_rq, S.ovvv_plane, S.t2_plane, Gg, v, v, v, v,
-                 1, v * vp, vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, EX + 0, EX + 1, 1});
+                 1, v * vp, vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, eO(pp), eT(rr, qq), 1});
       // S2: sum_d ovvv[q,y,x,d] t2[r,p,z,d]
       run(OzView{sO + qq * S.ovvv_p, sT + ((int64_t)rr * o + pp) * S.t2_rq, S.ovvv_plane, S.t2_plane, Gg, v, v, v, v,
-                 1, vp, v * vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, EX + 0, EX + 1, 0});
+                 1, vp, v * vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, eO(qq), eT(rr, pp), 0});
       // S3: -sum_l t2[l,p,y,x] ooov[q,l,r,z] = sum_l t2L[p][y][x][l] nooT[q][r][z][l]
       run(OzView{sL + pp * S.t2L_q, sN + ((int64_t)qq * o + rr) * S.nooT_pr, S.t2L_plane, S.nooT_plane, Gg, v, v, v,
-                 o, 1, op, v * op, 1, 0, 1, 0, op, v2, v, 1, 1.0, EX + 2, EX + 3, 0});
+                 o, 1, op, v * op, 1, 0, 1, 0, op, v2, v, 1, 1.0, eL(pp), eN(qq, rr), 0});
       // S4: -sum_l t2[l,q,x,y] ooov[p,l,r,z] = sum_l t2L[q][x][y][l] nooT[p][r][z][l]
       run(OzView{sL + qq * S.t2L_q, sN + ((int64_t)pp * o + rr) * S.nooT_pr, S.t2L_plane, S.nooT_plane, Gg, v, v, v,
-                 o, 1, v * op, op, 1, 0, 1, 0, op, v2, v, 1, 1.0, EX + 2, EX + 3, 0});
+                 o, 1, v * op, op, 1, 0, 1, 0, op, v2, v, 1, 1.0, eL(qq), eN(pp, rr), 0});
     }
     if (e != cudaSuccess) break;
     AdjArgs A{};  // value-initialised: optional pointers (dwmax) are null unless set
@@ -1048,7 +1117,10 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
     cudaMemsetAsync(dwmax, 0, 8, s);
     k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
     k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
-    k_slice_dw<<<(unsigned)std::min<int64_t>((v3 + 255) / 256, 8192), 256, 0, s>>>(W.dW, v3, dwmax, dwexp, dWs);
+    if (ns == 5)
+      k_slice_dw<5><<<(unsigned)std::min<int64_t>((v3 + 255) / 256, 8192), 256, 0, s>>>(W.dW, v3, dwmax, dwexp, dWs);
+    else
+      k_slice_dw<4><<<(unsigned)std::min<int64_t>((v3 + 255) / 256, 8192), 256, 0, s>>>(W.dW, v3, dwmax, dwexp, dWs);
     h->n_launches += 4;
     for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
       int pp, qq, rr;
@@ -1064,32 +1136,32 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
       if (g->ovvv) {
         // (a) dovvv[p,x,y,d] += sum_z G[x,y,z] t2[r,q,z,d]
         runI(OzView{dWs, t2rq, v3, S.t2_plane, g->ovvv + (int64_t)pp * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
-                   v2, v, 1, 1.0, dwexp, EX + 1, 0}, gi);
+                   v2, v, 1, 1.0, dwexp, eT(rr, qq), 0}, gi);
         // (b) dovvv[q,y,x,d] += sum_z G[x,y,z] t2[r,p,z,d]
         runI(OzView{dWs, t2rp, v3, S.t2_plane, g->ovvv + (int64_t)qq * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
-                   v, v2, 1, 1.0, dwexp, EX + 1, 0}, gi);
+                   v, v2, 1, 1.0, dwexp, eT(rr, pp), 0}, gi);
       }
       if (g->t2) {
         // (c) dt2[r,q,z,d] += sum_xy G[x,y,z] ovvv[p,x,y,d]
         runII(OzView{dWs, sO + pp * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + qq) * v2, v, 1, v, v, v,
-                   gz, 0, gx, gy, v * vp, vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0}, gi);
+                   gz, 0, gx, gy, v * vp, vp, 1, v, 0, 1, 1.0, dwexp, eO(pp), 0}, gi);
         // (d) dt2[r,p,z,d] += sum_xy G[x,y,z] ovvv[q,y,x,d]
         runII(OzView{dWs, sO + qq * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + pp) * v2, v, 1, v, v, v,
-                   gz, 0, gx, gy, vp, v * vp, 1, v, 0, 1, 1.0, dwexp, EX + 0, 0}, gi);
+                   gz, 0, gx, gy, vp, v * vp, 1, v, 0, 1, 1.0, dwexp, eO(qq), 0}, gi);
         // (e) dt2[l,p,y,x] -= sum_z G[x,y,z] ooov[q,l,r,z]; ooov[q,l,r,z] = -nooT[q][r][z][l]
         runI(OzView{dWs, sN + ((int64_t)qq * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)pp * v2, v, v,
-                   o, v, 1, gx, gy, gz, 0, op, 0, 1, 1, v, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0}, gi);
+                   o, v, 1, gx, gy, gz, 0, op, 0, 1, 1, v, (int64_t)o * v2, 1.0, dwexp, eN(qq, rr), 0}, gi);
         // (g) dt2[l,q,x,y] -= sum_z G[x,y,z] ooov[p,l,r,z]
         runI(OzView{dWs, sN + ((int64_t)pp * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)qq * v2, v, v,
-                   o, v, 1, gx, gy, gz, 0, op, 0, 1, v, 1, (int64_t)o * v2, 1.0, dwexp, EX + 3, 0}, gi);
+                   o, v, 1, gx, gy, gz, 0, op, 0, 1, v, 1, (int64_t)o * v2, 1.0, dwexp, eN(pp, rr), 0}, gi);
       }
       if (g->ooov) {
         // (f) dooov[q,l,r,z] -= sum_xy t2[l,p,y,x] G[x,y,z]; t2[l,p,y,x] = t2L[p][y][x][l]
         runII(OzView{sL + pp * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)qq * o * o + rr) * v, o, 1, v, v,
-                   v, 1, 0, op, v * op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0}, gi);
+                   v, 1, 0, op, v * op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, eL(pp), dwexp, 0}, gi);
         // (h) dooov[p,l,r,z] -= sum_xy t2[l,q,x,y] G[x,y,z]; t2[l,q,x,y] = t2L[q][x][y][l]
         runII(OzView{sL + qq * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)pp * o * o + rr) * v, o, 1, v, v,
-                   v, 1, 0, v * op, op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, EX + 2, dwexp, 0}, gi);
+                   v, 1, 0, v * op, op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, eL(qq), dwexp, 0}, gi);
       }
     }
     if (e != cudaSuccess) break;
