@@ -438,6 +438,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 constexpr int GEMM_EPI_WARPS = TE_GEMM_EPI_WARPS;
 constexpr int GEMM_EPI_GROUPS = GEMM_EPI_WARPS / 4;
 constexpr int GEMM_THREADS = (2 + GEMM_EPI_WARPS) * 32;
+// 16-column chunks one epilogue warp holds in registers with a single
+// accumulator set (exact-slice N tiles of at most 160 columns)
+constexpr int EPI_CHUNKS = 5;
+constexpr int EPI_NT_MAX = 16 * GEMM_EPI_GROUPS * EPI_CHUNKS;
 
 template <int MODE>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
@@ -669,6 +673,85 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const int roff = cube_row(x & 7, y & 7);
       const int zx = cube_zx(x & 7, y & 7);
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * acc_stride;
+      if constexpr (is_ozaki(MODE) && GEMM_EPI_GROUPS == 2) {
+        if (NBUF == 1) {
+          // One accumulator set: copy it to registers as (hi, lo) pairs and
+          // release it before the stores, so that the next tile's MMAs run
+          // while this tile's G is written.  A warp holds at most
+          // EPI_CHUNKS 16-column chunks (N tiles <= 160, checked on the
+          // host).  lo is held rounded to BF16 (two per register): |lo| <=
+          // ulp(hi) / 2, so the pair keeps 2^-33 of the value, far below the
+          // 2^-28 of the exact-slice operands.
+          float hv[EPI_CHUNKS][16];
+          uint32_t lp[EPI_CHUNKS][8];
+#pragma unroll
+          for (int k = 0; k < EPI_CHUNKS; ++k) {
+            const int c0 = 16 * chunk0 + 32 * k;
+            if (c0 < C.NT) {
+#pragma unroll
+              for (int half = 0; half < 2; ++half) {  // 8 columns at a time: fewer live registers
+                const int cc = c0 + 8 * half;
+                float a2[8], a3[8], ar[8];
+                ptx::tmem_ld8x3(tbase + cc, tbase + C.NT + cc, tbase + 2 * C.NT + cc, a2, a3, ar);
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                  float l2[2];
+#pragma unroll
+                  for (int q = 0; q < 2; ++q) {
+                    float s, e;
+                    two_sum(a2[j + q], a3[j + q], s, e);
+                    const float lo = __fadd_rn(e, ar[j + q]);
+                    const float hi = __fadd_rn(s, lo);
+                    hv[k][8 * half + j + q] = hi * gscale;
+                    l2[q] = __fsub_rn(lo, __fsub_rn(hi, s)) * gscale;
+                  }
+                  const __nv_bfloat162 b = __floats2bfloat162_rn(l2[0], l2[1]);
+                  lp[k][4 * half + (j >> 1)] = *reinterpret_cast<const uint32_t*>(&b);
+                }
+              }
+            }
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+          acc_phase ^= 1u;
+          if (valid) {
+#pragma unroll
+            for (int k = 0; k < EPI_CHUNKS; ++k) {
+              const int c0 = 16 * chunk0 + 32 * k;
+              if (c0 < C.NT) {
+                const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                  const int Z = (z >> 3) + h2;
+                  if (Z < nb) {
+                    int64_t bt;
+                    unsigned mask;
+                    orbit_slots(x >> 3, y >> 3, Z, &bt, &mask);
+                    float l8[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                      const uint32_t w = lp[k][4 * h2 + q];
+                      l8[2 * q] = __uint_as_float(w << 16);
+                      l8[2 * q + 1] = __uint_as_float(w & 0xffff0000u);
+                    }
+                    xor_permute8(hv[k] + 8 * h2, zx);
+                    xor_permute8(l8, zx);
+                    float* item = gslot + (bt * 18 + c.g * 6) * (512 * CWF);
+                    for (int pid = 0; pid < 6; ++pid) {
+                      if (!((mask >> pid) & 1u)) continue;
+                      float* cube = item + pid * (512 * CWF);
+                      store8(cube + roff, hv[k] + 8 * h2);
+                      store8(cube + 512 + roff, l8);
+                    }
+                  }
+                }
+              }
+            }
+          }
+          continue;
+        }
+      }
       for (int c0 = 16 * chunk0; c0 < C.NT; c0 += 16 * GEMM_EPI_GROUPS) {
         const int z = c.z0 + c0;  // multiple of 16: two whole Z blocks
         if constexpr (is_ozaki(MODE)) {
@@ -1237,6 +1320,8 @@ static te_status gemm_params(const Handle* h, const std::vector<TcJob>& jobs, co
   if (P->stages < 2) return fail(TE_EUNSUPPORTED, "not enough shared memory for two pipeline stages");
   P->nbuf = p0.nbuf;
   P->nt_max = nt_max;
+  if (is_ozaki(mode) && P->nbuf == 1 && nt_max > EPI_NT_MAX)
+    return fail(TE_EUNSUPPORTED, "N tile %d above the epilogue's %d columns", nt_max, EPI_NT_MAX);
   uint32_t cols = 32;
   while (cols < (uint32_t)(nacc * P->nbuf * nt_max)) cols <<= 1;
   P->tmem_cols = cols;
