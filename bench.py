@@ -28,7 +28,7 @@ import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
 WORKLOAD = "o32v320"
-TRAFFIC_PER_TRIPLE = 2.559e9  # k_gemm_tc DRAM bytes per triple at nvir = 320, 7-bit slices (ncu)
+TRAFFIC_PER_TRIPLE = 2.541e9  # k_gemm_tc DRAM bytes per triple at nvir = 320, 7-bit slices (ncu)
 METRIC = "(T) GFLOP/s & clusters/s, tensor-pipe % of peak, at |dE(T)|<=1e-7 Ha vs FP64"
 
 
