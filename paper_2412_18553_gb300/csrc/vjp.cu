@@ -21,10 +21,13 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <initializer_list>
+#include <vector>
 
 #include "strided.h"
 #include "tc_path.h"
 #include "te_internal.h"
+#include "view_tc.h"
 
 namespace te {
 
@@ -976,16 +979,143 @@ int64_t oz_scratch_cap(int64_t o, int64_t v, int num_sms) {
 // nocc=48 nvir=560 four slices left errors of 2.7e-6 of d ovvv's largest entry.
 static int adjoint_slices(int64_t v) { return v > 200 ? 5 : 4; }
 
+// ---------------------------------------------------------------------------
+// exact-slice adjoint on tcgen05 (view_tc.cu)
+// ---------------------------------------------------------------------------
+
+// Slices of three index permutations of dW~ into three layouts L[x][y][z]
+// (z padded to vp), layout b of phase f holding the slices of dW~[pi(x, y, z)]:
+//   phase 0: pi = (x,y,z), (z,x,y), (y,z,x);  phase 1: (z,y,x), (x,z,y), (y,x,z).
+// With 2^e > max |dW~| (e written to *e_out), N = rint(dW~ 2^(7 NS - e)) is cut
+// into balanced base-128 digits, N = sum_k d_k 128^(NS-1-k), |d_k| <= 128, and
+// slice k holds d_k 2^-7(k+1) (exact in BF16): dW~ = 2^e sum_k slice_k to within
+// 2^(e - 7 NS - 1).  Three float64 operations per element.  A block handles one
+// 32 x 32 tile of the (c, z) plane at one value of the third index, c being
+// the index along which dW~ is contiguous for this permutation (or y when that
+// is z), so both the reads and the writes are coalesced.
+template <int NS>
+__global__ void __launch_bounds__(256) k_dw_layouts(const double* __restrict__ dW, int v, int vp, int phase,
+                                                    const unsigned long long* __restrict__ dwmax,
+                                                    int* __restrict__ e_out, __nv_bfloat16* __restrict__ out,
+                                                    int64_t lay_elems) {
+  __shared__ double tile[32][33];
+  const double mx = __longlong_as_double((long long)*dwmax);
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0) *e_out = ex;
+  const double sc1 = ldexp(1.0, -ex), mul = (double)(1ll << (7 * NS));
+  const int perm = phase * 3 + (int)blockIdx.z;
+  const int64_t V = v, V2 = V * V, plane = V2 * vp;
+  // source strides of the output indices (x, y, z)
+  int64_t sx, sy, sz;
+  switch (perm) {
+    case 0: sx = V2; sy = V; sz = 1; break;
+    case 1: sx = V; sy = 1; sz = V2; break;
+    case 2: sx = 1; sy = V2; sz = V; break;
+    case 3: sx = 1; sy = V; sz = V2; break;
+    case 4: sx = V2; sy = 1; sz = V; break;
+    default: sx = V; sy = V2; sz = 1; break;
+  }
+  // c: the tile's other index (0 = x, 1 = y); w: the block's fixed index
+  const int cidx = (sx == 1) ? 0 : 1;
+  const int64_t sc_ = cidx == 0 ? sx : sy, sw = cidx == 0 ? sy : sx;
+  const int ntz = (v + 31) / 32;
+  const int c0 = (int)(blockIdx.x / ntz) * 32, z0 = (int)(blockIdx.x % ntz) * 32;
+  const int w = blockIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  // load: threads along c when dW~ is contiguous along c, else along z
+  for (int i = ty; i < 32; i += 8) {
+    const int cc = sz == 1 ? c0 + i : c0 + tx, zz = sz == 1 ? z0 + tx : z0 + i;
+    if (cc < v && zz < v) {
+      const double x = dW[w * sw + cc * sc_ + zz * sz];
+      if (sz == 1) tile[i][tx] = x;
+      else tile[tx][i] = x;
+    }
+  }
+  __syncthreads();
+  __nv_bfloat16* o = out + blockIdx.z * lay_elems;
+  for (int i = ty; i < 32; i += 8) {
+    const int cc = c0 + i, zz = z0 + tx;
+    if (cc >= v || zz >= v) continue;
+    long long N = __double2ll_rn((tile[i][tx] * sc1) * mul);  // |dW~ 2^-e| < 1
+    float d[NS];
+#pragma unroll
+    for (int k = NS - 1; k > 0; --k) {
+      const int dk = (int)((N + 64) & 127) - 64;
+      d[k] = (float)dk;
+      N = (N - dk) >> 7;
+    }
+    d[0] = (float)N;
+    const int64_t xi = cidx == 0 ? cc : w, yi = cidx == 0 ? w : cc;
+    const int64_t at = (xi * V + yi) * vp + zz;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) o[k * plane + at] = __float2bfloat16_rn(ldexpf(d[k], -7 * (k + 1)));
+  }
+}
+
+static int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+// N tile of an output with n columns: at most VT_NT_MAX, a multiple of 16
+static int vt_ntile(int64_t n) {
+  const int64_t t = (n + VT_NT_MAX - 1) / VT_NT_MAX;
+  return (int)rup((n + t - 1) / t, 16);
+}
+
+struct VjpTcSizes {
+  int ns, vp;
+  size_t lay;         // elements of one dW~ layout (ns planes of v v vp)
+  size_t region;      // bytes: G, dY and dD, later the three layouts
+  size_t ovt, t2t, t2p, noo;  // bytes of the operand copies
+  int64_t part_cap;   // doubles of split-K partials
+};
+
+static VjpTcSizes vjp_tc_sizes(int64_t o, int64_t v, int num_sms) {
+  VjpTcSizes z;
+  z.ns = adjoint_slices(v);
+  z.vp = (int)rup(v, 16);
+  const int64_t v3 = v * v * v, vp = z.vp, NS = z.ns;
+  auto a = [](size_t b) { return (b + 1023) & ~size_t(1023); };
+  z.lay = (size_t)NS * v * v * vp;
+  z.region = std::max(a((size_t)3 * v3 * 8) + 2 * a((size_t)v3 * 8), 3 * a(z.lay * 2));
+  z.ovt = a((size_t)NS * v * v * vp * 2);
+  z.t2t = a((size_t)6 * NS * v * vp * 2);
+  z.t2p = a((size_t)3 * NS * o * v * vp * 2);
+  z.noo = a((size_t)NS * o * o * o * vp * 2);
+  // partials of the split jobs of one launch (an upper bound over the launches)
+  const int64_t ntv = vt_ntile(v), nto = vt_ntile(o);
+  const int64_t rows_xy = ((v + 7) / 8) * ((v + 15) / 16), rows_z = (v + 127) / 128;
+  const int64_t pair_blk = 3 * vt_seg_blocks((int)v, (int)v, VT_SPLIT_CHUNKS);
+  const int64_t one_blk = 4 * vt_seg_blocks(1, (int)v, VT_SPLIT_CHUNKS);
+  const int64_t d_ovvv = vt_split_doubles(rows_xy * ((v + ntv - 1) / ntv), one_blk, v * v * v, num_sms);
+  const int64_t d_t2s = vt_split_doubles(rows_xy * ((o + nto - 1) / nto), one_blk, v * v * o, num_sms);
+  const int64_t d_ooov = vt_split_doubles(rows_z * ((o + nto - 1) / nto), pair_blk, v * o, num_sms);
+  const int64_t d_t2 = vt_split_doubles(rows_z * ((v + ntv - 1) / ntv), pair_blk, v * v, num_sms);
+  z.part_cap = std::max(3 * (d_ovvv + d_t2s + d_ooov), 3 * (d_t2 + d_ooov)) + 1024;
+  return z;
+}
+
 size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms) {
   const int64_t v3 = v * v * v, nt = num_unique_triples(o);
   const int64_t nblk = (v3 + 255) / 256;
-  const int ns = adjoint_slices(v);
-  auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
-  return tc_slices_bytes((int)o, (int)v, ns) + 1024 + a(o * v * o * v) +
-         a(3 * v3) + 3 * a(v3) + a((v3 * ns + 3) / 4) /* dW slices: ns x 2 B */ + a(o * v * o * v) + 2 * a(nblk) +
-         a(std::max<int64_t>(1, nt)) + a(oz_scratch_cap(o, v, num_sms)) + a(4) + 1024;
+  const VjpTcSizes z = vjp_tc_sizes(o, v, num_sms);
+  auto a = [](int64_t n) { return ((size_t)n * 8 + 1023) & ~size_t(1023); };
+  return tc_slices_bytes((int)o, (int)v, z.ns) + 1024 + a(o * v * o * v) + z.region + a(v3) + a(o * v * o * v) +
+         2 * a(nblk) + a(std::max<int64_t>(1, nt)) + a(4) + z.ovt + z.t2t + z.t2p + z.noo + a(z.part_cap) + 4096;
 }
 
+// The contractions of one triple (g = 0, 1, 2 the G blocks with occupied
+// indices (p, q, r) = (i, j, k), (j, k, i), (k, i, j); dG_g the views of dW~):
+//   G:  G_g[x,y,z] = S1 + S2 + S3 + S4 (four K segments, the forward's form)
+//   (a) dovvv[p,x,y,d] += sum_z dG[x,y,z] t2[r,q,z,d]    (b) dovvv[q,y,x,d] += sum_z dG[x,y,z] t2[r,p,z,d]
+//   (c) dt2[r,q,z,d] += sum_xy dG[x,y,z] ovvv[p,x,y,d]   (d) dt2[r,p,z,d] += sum_xy dG[x,y,z] ovvv[q,y,x,d]
+//   (e) dt2[l,p,y,x] -= sum_z dG[x,y,z] ooov[q,l,r,z]    (g) dt2[l,q,x,y] -= sum_z dG[x,y,z] ooov[p,l,r,z]
+//   (f) dooov[q,l,r,z] -= sum_xy t2[l,p,y,x] dG[x,y,z]   (h) dooov[p,l,r,z] -= sum_xy t2[l,q,x,y] dG[x,y,z]
+// Every operand is read along a contiguous K index: dG_g comes in the layouts
+// L1_g[x][y][z] (K = z), L2_g[z][x][y] (K = (x, y)) and L3_g[z][y][x] (K =
+// (y, x)), the index permutations of dW~ that k_dw_layouts writes; t2, ovvv
+// and ooov enter as transposed slice copies (t2T[d][z] per pair (r, q),
+// ovvvT[d][x][y] per slab, t2P[l][x][y] per occupied index, nooTT[q][r][l][z]).
+// Outputs of the same launch are disjoint: the contributions to one output
+// slab (or pair block) are the segments of one job.
 te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_end, double gE,
                      double* e_out, te_cluster_grad* g, cudaStream_t s) {
   const int o = (int)c->nocc, v = (int)c->nvir;
@@ -994,36 +1124,44 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
   if (st != TE_OK) return st;
   st = ensure_triples_public(h, o);
   if (st != TE_OK) return st;
+  const VjpTcSizes Z = vjp_tc_sizes(o, v, h->num_sms);
+  const int ns = Z.ns;
+  const int64_t vp = Z.vp;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->ws) + 1023) & ~uintptr_t(1023));
   SliceSet S;
-  const int ns = adjoint_slices(v);
   st = tc_prepare_slices(c, base, &S, h->num_sms, s, ns);
   if (st != TE_OK) return st;
   char* p = base + ((tc_slices_bytes(o, v, ns) + 1023) & ~size_t(1023));
-  auto take = [&](int64_t n) {
-    double* r = reinterpret_cast<double*>(p);
-    p += ((size_t)n * 8 + 255) & ~size_t(255);
+  auto takeb = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 1023) & ~size_t(1023);
     return r;
   };
+  auto take = [&](int64_t n) { return reinterpret_cast<double*>(takeb((size_t)n * 8)); };
   VjpWork W;
-  W.t2L = nullptr;  // the contractions read the slice planes of t2L and nooT
+  W.t2L = nullptr;
   W.nooT = nullptr;
   W.ovs = take((int64_t)o * v * o * v);
-  W.G = take(3 * v3);
+  char* region = takeb(Z.region);
+  W.G = reinterpret_cast<double*>(region);
+  W.dY = reinterpret_cast<double*>(region + (((size_t)3 * v3 * 8 + 1023) & ~size_t(1023)));
+  W.dD = W.dY + ((((size_t)v3 * 8 + 1023) & ~size_t(1023)) / 8);
   W.dW = take(v3);
-  W.dY = take(v3);
-  W.dD = take(v3);
-  __nv_bfloat16* dWs = reinterpret_cast<__nv_bfloat16*>(take((v3 * ns + 3) / 4));  // ns planes of v^3 BF16
   W.dOVS = take((int64_t)o * v * o * v);
   const int64_t nblk = (v3 + 255) / 256;
   W.epart = take(nblk);
   W.dpart = take(nblk);
   W.shares = take(std::max<int64_t>(1, nt));
-  const int64_t cap = oz_scratch_cap(o, v, h->num_sms);
-  W.splitk = take(cap);
-  // per-triple scalars: max |dW~| (bit pattern) and the exponent of its slices
   unsigned long long* dwmax = reinterpret_cast<unsigned long long*>(take(4));
   int* dwexp = reinterpret_cast<int*>(dwmax + 1);
+  using bf = __nv_bfloat16;
+  bf* ovT = reinterpret_cast<bf*>(takeb(Z.ovt));
+  bf* t2T = reinterpret_cast<bf*>(takeb(Z.t2t));
+  bf* t2P = reinterpret_cast<bf*>(takeb(Z.t2p));
+  bf* nooTT = reinterpret_cast<bf*>(takeb(Z.noo));
+  double* part = take(Z.part_cap);
+  const size_t lay_stride = ((Z.lay * 2 + 1023) & ~size_t(1023)) / 2;  // elements between layouts
+  bf* lay = reinterpret_cast<bf*>(region);
 
   auto zero = [&](double* ptr, int64_t n) {
     return ptr ? cudaMemsetAsync(ptr, 0, sizeof(double) * n, s) : cudaSuccess;
@@ -1053,62 +1191,155 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
   e = launch_prep_fp64(c, &P, s);
   if (e != cudaSuccess) return fail(TE_ECUDA, "prep: %s", cudaGetErrorString(e));
 
-  using bf = __nv_bfloat16;
   const bf* sO = static_cast<const bf*>(S.ovvv);
   const bf* sT = static_cast<const bf*>(S.t2);
   const bf* sL = static_cast<const bf*>(S.t2L);
   const bf* sN = static_cast<const bf*>(S.nooT);
-  const int64_t vp = S.vp, op = S.op;
-  // scale exponents of the row groups each GEMM reads
+  const int64_t op = S.op, O = o, V = v, NS = ns;
+  // nooTT[q][r][l][z] = nooT[q][r][z][l] = -ooov[q,l,r,z], once per call
+  e = vt_transpose(sN, S.nooT_plane, S.nooT_pr, op, nooTT, O * O * O * vp, O * vp, vp, ns, o * o, v, o, s);
+  if (e != cudaSuccess) return fail(TE_ECUDA, "transpose: %s", cudaGetErrorString(e));
+  ++h->n_launches;
+
+  // tensor maps, encoded once: rows (x, y) in tiles of 8 x 16, rows z alone in tiles of 128
+  const int NTv = vt_ntile(v), NTo = vt_ntile(o);
+  VtBank bank;
+  bank.n = 0;
+  auto add = [&](const void* b0, std::initializer_list<int64_t> dims, std::initializer_list<int64_t> str,
+                 VtRoles r, int rows2, int rows1, int* idx) {
+    VtView w;
+    w.base = b0;
+    int q = 0;
+    for (int64_t d : dims) w.dims[q++] = (uint64_t)d;
+    q = 0;
+    for (int64_t x : str) w.stride[q++] = (uint64_t)x;
+    w.roles = r;
+    return vt_bank_add(&bank, w, rows2, rows1, idx);
+  };
+  const VtRoles XY{0, 1, 2, -1, 3};       // k2 | rows y, x | slice
+  const VtRoles ROW{0, 1, -1, -1, 2};     // k2 | rows | slice
+  const VtRoles ZK{0, 2, -1, 1, 3};       // k2 | k1 | rows | slice
+  int m_on, m_ot, m_ln, m_lt, m_t2, m_no, m_l1n[3], m_l1t[3], m_lz[3], m_t2T, m_noo, m_ovT, m_t2P;
+  const int64_t U1 = 1;
+  if ((st = add(sO, {U1 * v, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, U1 * vp, V * vp, U1 * S.ovvv_plane, U1 * S.ovvv_p},
+                XY, 16, 8, &m_on)) != TE_OK)
+    return st;
+  if ((st = add(sO, {U1 * v, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, V * vp, U1 * vp, U1 * S.ovvv_plane, U1 * S.ovvv_p},
+                XY, 16, 8, &m_ot)) != TE_OK)
+    return st;
+  if ((st = add(sL, {U1 * O, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, U1 * op, V * op, U1 * S.t2L_plane, U1 * S.t2L_q},
+                XY, 16, 8, &m_ln)) != TE_OK)
+    return st;
+  if ((st = add(sL, {U1 * O, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, V * op, U1 * op, U1 * S.t2L_plane, U1 * S.t2L_q},
+                XY, 16, 8, &m_lt)) != TE_OK)
+    return st;
+  if ((st = add(sT, {U1 * v, U1 * v, U1 * NS, U1 * O, U1 * O},
+                {1, U1 * vp, U1 * S.t2_plane, U1 * S.t2_rq, O * S.t2_rq}, ROW, NTv, 1, &m_t2)) != TE_OK)
+    return st;
+  if ((st = add(sN, {U1 * O, U1 * v, U1 * NS, U1 * O, U1 * O},
+                {1, U1 * op, U1 * S.nooT_plane, U1 * S.nooT_pr, O * S.nooT_pr}, ROW, NTv, 1, &m_no)) != TE_OK)
+    return st;
+  const int64_t lplane = V * V * vp;
+  for (int b = 0; b < 3; ++b) {
+    const bf* lb = lay + b * lay_stride;
+    if ((st = add(lb, {U1 * v, U1 * v, U1 * v, U1 * NS, 1}, {1, U1 * vp, V * vp, lplane, 0}, XY, 16, 8,
+                  &m_l1n[b])) != TE_OK)
+      return st;
+    if ((st = add(lb, {U1 * v, U1 * v, U1 * v, U1 * NS, 1}, {1, V * vp, U1 * vp, lplane, 0}, XY, 16, 8,
+                  &m_l1t[b])) != TE_OK)
+      return st;
+    if ((st = add(lb, {U1 * v, U1 * v, U1 * v, U1 * NS, 1}, {1, U1 * vp, V * vp, lplane, 0}, ZK, 128, 1,
+                  &m_lz[b])) != TE_OK)
+      return st;
+  }
+  if ((st = add(t2T, {U1 * v, U1 * v, U1 * NS, 6, 1}, {1, U1 * vp, V * vp, NS * V * vp, 0}, ROW, NTv, 1, &m_t2T)) !=
+      TE_OK)
+    return st;
+  if ((st = add(nooTT, {U1 * v, U1 * O, U1 * O, U1 * O, U1 * NS}, {1, U1 * vp, O * vp, O * O * vp, O * O * O * vp},
+                VtRoles{0, 1, -1, -1, 4}, NTo, 1, &m_noo)) != TE_OK)
+    return st;
+  if ((st = add(ovT, {U1 * v, U1 * v, U1 * v, U1 * NS, 1}, {1, U1 * vp, V * vp, V * V * vp, 0}, ZK, NTv, 1,
+                &m_ovT)) != TE_OK)
+    return st;
+  if ((st = add(t2P, {U1 * v, U1 * v, U1 * O, U1 * NS, 3}, {1, U1 * vp, V * vp, O * V * vp, NS * O * V * vp}, ZK,
+                NTo, 1, &m_t2P)) != TE_OK)
+    return st;
+  // layout buffers: phase 0 holds L1_g in buffer g and L2_g in buffer (g + 2) % 3; phase 1 holds L3_g in buffer g
+  const int l2buf[3] = {2, 0, 1};
+
   auto eO = [&](int p_) { return S.e_ovvv + p_; };
   auto eT = [&](int r_, int q_) { return S.e_t2 + ((int64_t)r_ * o + q_); };
   auto eL = [&](int q_) { return S.e_t2L + q_; };
   auto eN = [&](int p_, int r_) { return S.e_nooT + ((int64_t)p_ * o + r_); };
 
   std::vector<Triple> trip = unique_triples(o);
-  auto run = [&](OzView gv) {
-    gv.ns = ns;
-    if (e == cudaSuccess) e = gemm_oz(gv, h->num_sms, W.splitk, cap, s, &h->n_launches);
+  int slab = -1;  // the ovvv slab whose transpose ovT holds
+  auto launch = [&](VtBuild& b) -> te_status {
+    te_status q = vt_finish(&b, h->num_sms, part, Z.part_cap, nullptr);
+    if (q != TE_OK) return q;
+    return vt_launch(h, &b, s);
   };
-  // The order of the two row indices (or of the two k indices) of a view is a
-  // free choice: put the unit-stride one second so the loads vectorise.
-  auto swapM = [](OzView gv) {
-    std::swap(gv.M1, gv.M2);
-    std::swap(gv.a_m1, gv.a_m2);
-    std::swap(gv.c_m1, gv.c_m2);
-    return gv;
+  auto need_slab = [&](int sb) -> cudaError_t {
+    if (slab == sb) return cudaSuccess;
+    slab = sb;
+    ++h->n_launches;
+    return vt_transpose(sO + (int64_t)sb * S.ovvv_p, S.ovvv_plane, V * vp, vp, ovT, V * V * vp, vp, V * vp, ns, v, v,
+                        v, s);
   };
-  auto swapK = [](OzView gv) {
-    std::swap(gv.K1, gv.K2);
-    std::swap(gv.a_k1, gv.a_k2);
-    std::swap(gv.b_k1, gv.b_k2);
-    return gv;
-  };
-  auto runI = [&](const OzView& gv, int gi) { run(gi == 2 ? swapM(gv) : gv); };   // rows (x, y) of Gamma
-  auto runII = [&](const OzView& gv, int gi) { run(gi == 2 ? swapK(gv) : gv); };  // k = (x, y) of Gamma
-  for (int64_t t = t_begin; t < t_end && e == cudaSuccess; ++t) {
+  for (int64_t t = t_begin; t < t_end; ++t) {
     const Triple T = trip[t];
-    // forward G blocks, natural [g][x][y][z], four K segments each
+    const int PQR[3][3] = {{T.i, T.j, T.k}, {T.j, T.k, T.i}, {T.k, T.i, T.j}};
+    // t2T slots: the (r, q) pairs the (a) and (b) contractions read
+    int pr[6][2], npair = 0;
+    auto pair_slot = [&](int r_, int q_) {
+      for (int x = 0; x < npair; ++x)
+        if (pr[x][0] == r_ && pr[x][1] == q_) return x;
+      pr[npair][0] = r_;
+      pr[npair][1] = q_;
+      return npair++;
+    };
+    int sl_rq[3], sl_rp[3];
     for (int gi = 0; gi < 3; ++gi) {
-      int pp, qq, rr;
-      if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
-      else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
-      else { pp = T.k; qq = T.i; rr = T.j; }
-      double* Gg = W.G + gi * v3;
-      // S1: sum_d ovvv[p,x,y,d] t2[r,q,z,d]
-      run(OzView{sO + pp * S.ovvv_p, sT + ((int64_t)rr * o + qq) * S.t2_rq, S.ovvv_plane, S.t2_plane, Gg, v, v, v, v,
-                 1, v * vp, vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, eO(pp), eT(rr, qq), 1});
-      // S2: sum_d ovvv[q,y,x,d] t2[r,p,z,d]
-      run(OzView{sO + qq * S.ovvv_p, sT + ((int64_t)rr * o + pp) * S.t2_rq, S.ovvv_plane, S.t2_plane, Gg, v, v, v, v,
-                 1, vp, v * vp, 1, 0, 1, 0, vp, v2, v, 1, 1.0, eO(qq), eT(rr, pp), 0});
-      // S3: -sum_l t2[l,p,y,x] ooov[q,l,r,z] = sum_l t2L[p][y][x][l] nooT[q][r][z][l]
-      run(OzView{sL + pp * S.t2L_q, sN + ((int64_t)qq * o + rr) * S.nooT_pr, S.t2L_plane, S.nooT_plane, Gg, v, v, v,
-                 o, 1, op, v * op, 1, 0, 1, 0, op, v2, v, 1, 1.0, eL(pp), eN(qq, rr), 0});
-      // S4: -sum_l t2[l,q,x,y] ooov[p,l,r,z] = sum_l t2L[q][x][y][l] nooT[p][r][z][l]
-      run(OzView{sL + qq * S.t2L_q, sN + ((int64_t)pp * o + rr) * S.nooT_pr, S.t2L_plane, S.nooT_plane, Gg, v, v, v,
-                 o, 1, v * op, op, 1, 0, 1, 0, op, v2, v, 1, 1.0, eL(qq), eN(pp, rr), 0});
+      sl_rq[gi] = pair_slot(PQR[gi][2], PQR[gi][1]);
+      sl_rp[gi] = pair_slot(PQR[gi][2], PQR[gi][0]);
     }
+    // t2P slots: the distinct occupied indices of the triple
+    int occ[3], nocc_ = 0;
+    auto occ_slot = [&](int x_) {
+      for (int q = 0; q < nocc_; ++q)
+        if (occ[q] == x_) return q;
+      occ[nocc_] = x_;
+      return nocc_++;
+    };
+    occ_slot(T.i);
+    occ_slot(T.j);
+    occ_slot(T.k);
+    for (int x = 0; x < npair && e == cudaSuccess; ++x)
+      e = vt_transpose(sT + ((int64_t)pr[x][0] * o + pr[x][1]) * S.t2_rq, S.t2_plane, 0, vp, t2T + x * NS * V * vp,
+                       V * vp, 0, vp, ns, 1, v, v, s);
+    for (int x = 0; x < nocc_ && e == cudaSuccess; ++x)
+      e = vt_transpose(sL + (int64_t)occ[x] * S.t2L_q, S.t2L_plane, V * op, op, t2P + x * NS * O * V * vp, O * V * vp,
+                       vp, V * vp, ns, v, v, o, s);
+    h->n_launches += npair + nocc_;
     if (e != cudaSuccess) break;
+
+    // forward G blocks, float64 [g][x][y][z]
+    {
+      VtBuild b;
+      vt_begin(&b, ns);
+      for (int gi = 0; gi < 3; ++gi) {
+        const int pp = PQR[gi][0], qq = PQR[gi][1], rr = PQR[gi][2];
+        VtJob* J = vt_job(&b, v, v, v, 8, 16, NTv, W.G + gi * v3, v2, v, 1, 1);
+        const int f_p[5] = {0, 0, 0, 0, pp}, f_q[5] = {0, 0, 0, 0, qq};
+        const int t_qr[5] = {0, 0, 0, qq, rr}, t_pr[5] = {0, 0, 0, pp, rr};
+        const int n_rq[5] = {0, 0, 0, rr, qq}, n_rp[5] = {0, 0, 0, rr, pp};
+        vt_seg(J, vt_use(&b, bank, m_on), vt_use(&b, bank, m_t2), 1, v, f_p, t_qr, eO(pp), eT(rr, qq), 1.0);
+        vt_seg(J, vt_use(&b, bank, m_ot), vt_use(&b, bank, m_t2), 1, v, f_q, t_pr, eO(qq), eT(rr, pp), 1.0);
+        vt_seg(J, vt_use(&b, bank, m_lt), vt_use(&b, bank, m_no), 1, o, f_p, n_rq, eL(pp), eN(qq, rr), 1.0);
+        vt_seg(J, vt_use(&b, bank, m_ln), vt_use(&b, bank, m_no), 1, o, f_q, n_rp, eL(qq), eN(pp, rr), 1.0);
+      }
+      if ((st = launch(b)) != TE_OK) return st;
+    }
     AdjArgs A{};  // value-initialised: optional pointers (dwmax) are null unless set
     A.o = o; A.v = v; A.i = T.i; A.j = T.j; A.k = T.k;
     A.w = gE * (double)T.m / 3.0;
@@ -1117,54 +1348,8 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
     cudaMemsetAsync(dwmax, 0, 8, s);
     k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
     k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
-    if (ns == 5)
-      k_slice_dw<5><<<(unsigned)std::min<int64_t>((v3 + 255) / 256, 8192), 256, 0, s>>>(W.dW, v3, dwmax, dwexp, dWs);
-    else
-      k_slice_dw<4><<<(unsigned)std::min<int64_t>((v3 + 255) / 256, 8192), 256, 0, s>>>(W.dW, v3, dwmax, dwexp, dWs);
-    h->n_launches += 4;
-    for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
-      int pp, qq, rr;
-      if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
-      else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
-      else { pp = T.k; qq = T.i; rr = T.j; }
-      int64_t gx, gy, gz;  // Gamma[x,y,z] strides in dW~ (and its slice planes)
-      if (gi == 0) { gx = v2; gy = v; gz = 1; }
-      else if (gi == 1) { gx = v; gy = 1; gz = v2; }
-      else { gx = 1; gy = v2; gz = v; }
-      const bf* t2rq = sT + ((int64_t)rr * o + qq) * S.t2_rq;
-      const bf* t2rp = sT + ((int64_t)rr * o + pp) * S.t2_rq;
-      if (g->ovvv) {
-        // (a) dovvv[p,x,y,d] += sum_z G[x,y,z] t2[r,q,z,d]
-        runI(OzView{dWs, t2rq, v3, S.t2_plane, g->ovvv + (int64_t)pp * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
-                   v2, v, 1, 1.0, dwexp, eT(rr, qq), 0}, gi);
-        // (b) dovvv[q,y,x,d] += sum_z G[x,y,z] t2[r,p,z,d]
-        runI(OzView{dWs, t2rp, v3, S.t2_plane, g->ovvv + (int64_t)qq * v3, v, v, v, v, 1, gx, gy, gz, 0, vp, 0, 1,
-                   v, v2, 1, 1.0, dwexp, eT(rr, pp), 0}, gi);
-      }
-      if (g->t2) {
-        // (c) dt2[r,q,z,d] += sum_xy G[x,y,z] ovvv[p,x,y,d]
-        runII(OzView{dWs, sO + pp * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + qq) * v2, v, 1, v, v, v,
-                   gz, 0, gx, gy, v * vp, vp, 1, v, 0, 1, 1.0, dwexp, eO(pp), 0}, gi);
-        // (d) dt2[r,p,z,d] += sum_xy G[x,y,z] ovvv[q,y,x,d]
-        runII(OzView{dWs, sO + qq * S.ovvv_p, v3, S.ovvv_plane, g->t2 + ((int64_t)rr * o + pp) * v2, v, 1, v, v, v,
-                   gz, 0, gx, gy, vp, v * vp, 1, v, 0, 1, 1.0, dwexp, eO(qq), 0}, gi);
-        // (e) dt2[l,p,y,x] -= sum_z G[x,y,z] ooov[q,l,r,z]; ooov[q,l,r,z] = -nooT[q][r][z][l]
-        runI(OzView{dWs, sN + ((int64_t)qq * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)pp * v2, v, v,
-                   o, v, 1, gx, gy, gz, 0, op, 0, 1, 1, v, (int64_t)o * v2, 1.0, dwexp, eN(qq, rr), 0}, gi);
-        // (g) dt2[l,q,x,y] -= sum_z G[x,y,z] ooov[p,l,r,z]
-        runI(OzView{dWs, sN + ((int64_t)pp * o + rr) * S.nooT_pr, v3, S.nooT_plane, g->t2 + (int64_t)qq * v2, v, v,
-                   o, v, 1, gx, gy, gz, 0, op, 0, 1, v, 1, (int64_t)o * v2, 1.0, dwexp, eN(pp, rr), 0}, gi);
-      }
-      if (g->ooov) {
-        // (f) dooov[q,l,r,z] -= sum_xy t2[l,p,y,x] G[x,y,z]; t2[l,p,y,x] = t2L[p][y][x][l]
-        runII(OzView{sL + pp * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)qq * o * o + rr) * v, o, 1, v, v,
-                   v, 1, 0, op, v * op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, eL(pp), dwexp, 0}, gi);
-        // (h) dooov[p,l,r,z] -= sum_xy t2[l,q,x,y] G[x,y,z]; t2[l,q,x,y] = t2L[q][x][y][l]
-        runII(OzView{sL + qq * S.t2L_q, dWs, S.t2L_plane, v3, g->ooov + ((int64_t)pp * o * o + rr) * v, o, 1, v, v,
-                   v, 1, 0, v * op, op, gx, gy, gz, (int64_t)o * v, 0, 1, -1.0, eL(qq), dwexp, 0}, gi);
-      }
-    }
-    if (e != cudaSuccess) break;
+    // the Y and denominator parts; G, dY and dD are dead afterwards and their
+    // memory takes the dW~ layouts
     const unsigned gb2 = (unsigned)((v2 + 255) / 256);
     for (int mode = 0; mode < 3; ++mode) {
       if (g->ovov) k_dovs<<<gb2, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, c->t1, W.dOVS);
@@ -1172,7 +1357,135 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
     }
     if (g->eps_v) k_deps_v<<<(unsigned)v, 256, 0, s>>>(v, W.dD, g->eps_v);
     if (g->eps_o) k_deps_o<<<1, 256, 0, s>>>(nblk, W.dpart, T.i, T.j, T.k, g->eps_o);
-    h->n_launches += 8;
+    const int nt32 = (v + 31) / 32;
+    const dim3 lgrid((unsigned)(nt32 * nt32), (unsigned)v, 3), lblk(32, 8);
+    if (ns == 5) k_dw_layouts<5><<<lgrid, lblk, 0, s>>>(W.dW, v, (int)vp, 0, dwmax, dwexp, lay, (int64_t)lay_stride);
+    else k_dw_layouts<4><<<lgrid, lblk, 0, s>>>(W.dW, v, (int)vp, 0, dwmax, dwexp, lay, (int64_t)lay_stride);
+    h->n_launches += 11;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+
+    // d ovvv (a, b), d t2 slabs from ooov (e, g), d ooov (h): layouts L1, L2
+    {
+      VtBuild b;
+      vt_begin(&b, ns);
+      int dist[3], nd = 0;
+      for (int x_ : {T.i, T.j, T.k}) {
+        bool seen = false;
+        for (int q = 0; q < nd; ++q) seen |= dist[q] == x_;
+        if (!seen) dist[nd++] = x_;
+      }
+      for (int q = 0; q < nd && g->ovvv; ++q) {
+        const int sb = dist[q];
+        VtJob* J = vt_job(&b, v, v, v, 8, 16, NTv, g->ovvv + (int64_t)sb * v3, v2, v, 1, 0);
+        for (int gi = 0; gi < 3; ++gi) {
+          const int pp = PQR[gi][0], qq = PQR[gi][1], rr = PQR[gi][2];
+          const int f_rq[5] = {0, 0, 0, sl_rq[gi], 0}, f_rp[5] = {0, 0, 0, sl_rp[gi], 0};
+          if (pp == sb) vt_seg(J, vt_use(&b, bank, m_l1n[gi]), vt_use(&b, bank, m_t2T), 1, v, nullptr, f_rq, dwexp,
+                               eT(rr, qq), 1.0);
+          if (qq == sb) vt_seg(J, vt_use(&b, bank, m_l1t[gi]), vt_use(&b, bank, m_t2T), 1, v, nullptr, f_rp, dwexp,
+                               eT(rr, pp), 1.0);
+        }
+      }
+      for (int q = 0; q < nd && g->t2; ++q) {
+        const int sb = dist[q];
+        // element dt2[l][sb][X][Y]: rows (X, Y), columns l
+        VtJob* J = vt_job(&b, v, v, o, 8, 16, NTo, g->t2 + (int64_t)sb * v2, v, 1, (int64_t)o * v2, 0);
+        for (int gi = 0; gi < 3; ++gi) {
+          const int pp = PQR[gi][0], qq = PQR[gi][1], rr = PQR[gi][2];
+          const int f_rq[5] = {0, 0, rr, qq, 0}, f_rp[5] = {0, 0, rr, pp, 0};
+          // (e): X = y, Y = x: transposed rows; B = nooTT = -ooov
+          if (pp == sb) vt_seg(J, vt_use(&b, bank, m_l1t[gi]), vt_use(&b, bank, m_noo), 1, v, nullptr, f_rq, dwexp,
+                               eN(qq, rr), 1.0);
+          if (qq == sb) vt_seg(J, vt_use(&b, bank, m_l1n[gi]), vt_use(&b, bank, m_noo), 1, v, nullptr, f_rp, dwexp,
+                               eN(pp, rr), 1.0);
+        }
+      }
+      if (g->ooov) {
+        bool done[3] = {false, false, false};
+        for (int gi = 0; gi < 3; ++gi) {
+          if (done[gi]) continue;
+          const int P_ = PQR[gi][0], R_ = PQR[gi][2];
+          VtJob* J = vt_job(&b, 1, v, o, 1, 128, NTo, g->ooov + ((int64_t)P_ * o * o + R_) * v, 0, 1, (int64_t)o * v, 0);
+          for (int g2 = gi; g2 < 3; ++g2) {
+            if (done[g2] || PQR[g2][0] != P_ || PQR[g2][2] != R_) continue;
+            done[g2] = true;
+            const int f_q[5] = {0, 0, 0, 0, occ_slot(PQR[g2][1])};
+            vt_seg(J, vt_use(&b, bank, m_lz[l2buf[g2]]), vt_use(&b, bank, m_t2P), v, v, nullptr, f_q, dwexp,
+                   eL(PQR[g2][1]), -1.0);
+          }
+        }
+      }
+      if (b.P.njobs && (st = launch(b)) != TE_OK) return st;
+    }
+    // d t2 pair blocks from ovvv (c): layouts L2, one slab transpose per launch
+    const int order[3] = {T.i, T.j, T.k};
+    for (int q = 0; q < 3 && g->t2; ++q) {
+      const int sb = order[q];
+      if ((q == 1 && sb == order[0]) || (q == 2 && (sb == order[0] || sb == order[1]))) continue;
+      VtBuild b;
+      vt_begin(&b, ns);
+      bool done[3] = {false, false, false};
+      for (int gi = 0; gi < 3; ++gi) {
+        if (done[gi] || PQR[gi][0] != sb) continue;
+        const int R_ = PQR[gi][2], Q_ = PQR[gi][1];
+        VtJob* J = vt_job(&b, 1, v, v, 1, 128, NTv, g->t2 + ((int64_t)R_ * o + Q_) * v2, 0, v, 1, 0);
+        for (int g2 = gi; g2 < 3; ++g2) {
+          if (done[g2] || PQR[g2][0] != sb || PQR[g2][2] != R_ || PQR[g2][1] != Q_) continue;
+          done[g2] = true;
+          vt_seg(J, vt_use(&b, bank, m_lz[l2buf[g2]]), vt_use(&b, bank, m_ovT), v, v, nullptr, nullptr, dwexp, eO(sb),
+                 1.0);
+        }
+      }
+      if (!b.P.njobs) continue;
+      if ((e = need_slab(sb)) != cudaSuccess) break;
+      if ((st = launch(b)) != TE_OK) return st;
+    }
+    if (e != cudaSuccess) break;
+    // phase 1 layouts: L3_g
+    if (ns == 5) k_dw_layouts<5><<<lgrid, lblk, 0, s>>>(W.dW, v, (int)vp, 1, dwmax, dwexp, lay, (int64_t)lay_stride);
+    else k_dw_layouts<4><<<lgrid, lblk, 0, s>>>(W.dW, v, (int)vp, 1, dwmax, dwexp, lay, (int64_t)lay_stride);
+    ++h->n_launches;
+    // d t2 pair blocks from ovvv (d), slabs in reverse order (the last slab of
+    // (c) is still transposed), and d ooov (f) in the first launch: layouts L3
+    bool first = true;
+    for (int q = 2; q >= 0; --q) {
+      const int sb = order[q];
+      if ((q == 1 && sb == order[2]) || (q == 0 && (sb == order[2] || sb == order[1]))) continue;
+      VtBuild b;
+      vt_begin(&b, ns);
+      bool done[3] = {false, false, false};
+      for (int gi = 0; gi < 3 && g->t2; ++gi) {
+        if (done[gi] || PQR[gi][1] != sb) continue;
+        const int R_ = PQR[gi][2], P_ = PQR[gi][0];
+        VtJob* J = vt_job(&b, 1, v, v, 1, 128, NTv, g->t2 + ((int64_t)R_ * o + P_) * v2, 0, v, 1, 0);
+        for (int g2 = gi; g2 < 3; ++g2) {
+          if (done[g2] || PQR[g2][1] != sb || PQR[g2][2] != R_ || PQR[g2][0] != P_) continue;
+          done[g2] = true;
+          vt_seg(J, vt_use(&b, bank, m_lz[g2]), vt_use(&b, bank, m_ovT), v, v, nullptr, nullptr, dwexp, eO(sb), 1.0);
+        }
+      }
+      const bool need = b.P.njobs > 0;
+      if (first && g->ooov) {
+        bool done2[3] = {false, false, false};
+        for (int gi = 0; gi < 3; ++gi) {
+          if (done2[gi]) continue;
+          const int Q_ = PQR[gi][1], R_ = PQR[gi][2];
+          VtJob* J = vt_job(&b, 1, v, o, 1, 128, NTo, g->ooov + ((int64_t)Q_ * o * o + R_) * v, 0, 1, (int64_t)o * v, 0);
+          for (int g2 = gi; g2 < 3; ++g2) {
+            if (done2[g2] || PQR[g2][1] != Q_ || PQR[g2][2] != R_) continue;
+            done2[g2] = true;
+            const int f_p[5] = {0, 0, 0, 0, occ_slot(PQR[g2][0])};
+            vt_seg(J, vt_use(&b, bank, m_lz[g2]), vt_use(&b, bank, m_t2P), v, v, nullptr, f_p, dwexp,
+                   eL(PQR[g2][0]), -1.0);
+          }
+        }
+      }
+      first = false;
+      if (!b.P.njobs) continue;
+      if (need && (e = need_slab(sb)) != cudaSuccess) break;
+      if ((st = launch(b)) != TE_OK) return st;
+    }
+    if (e != cudaSuccess) break;
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && g->ovov) {
