@@ -77,6 +77,33 @@ __device__ __forceinline__ void orbit_values(const AdjArgs& A, int a, int b, int
   }
 }
 
+// Exact slices of x with |x| < 2^e: N = round(x 2^(7 NS - e)) taken from the
+// bits of x (no float64 arithmetic: GB300's float64 rate is low), written as
+// balanced base-128 digits N = sum_k d_k 128^(NS-1-k), |d_k| <= 128.  Slice k
+// is d_k 2^-7(k+1), exact in BF16, and x = 2^e sum_k slice_k to within
+// 2^(e - 7 NS - 1).  Zeros and subnormals give N = 0; non-finite x gives
+// unspecified digits.
+template <int NS>
+__device__ __forceinline__ void slice_digits(double x, int e, float* d) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FFull);
+  long long N = 0;
+  if (E != 0) {
+    // x = M 2^(E - 1075), so x 2^(7 NS - e) = M 2^-sh; |x| < 2^e gives sh >= 18
+    const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 1075 - E - 7 * NS + e;
+    if (sh > 0 && sh < 64) N = (long long)((M + (1ull << (sh - 1))) >> sh);
+    if (bits >> 63) N = -N;
+  }
+#pragma unroll
+  for (int k = NS - 1; k > 0; --k) {
+    const int dk = (int)((N + 64) & 127) - 64;
+    d[k] = (float)dk;
+    N = (N - dk) >> 7;
+  }
+  d[0] = (float)N;
+}
+
 // C[m,n] += alpha sum_k A[m,k] B[k,n], m = (m1, m2) and k = (k1, k2) with a
 // stride per index (float64, DFMA; deterministic split-K)
 struct GemmView {

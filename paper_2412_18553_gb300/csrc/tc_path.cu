@@ -42,9 +42,10 @@ namespace te {
 // TC_OZAKI: four 7-bit slices, ten slice products (K = 2 (v + o) <= 1024).
 // TC_OZAKI6: five 6-bit slices, fifteen slice products (K <= 4096); chosen
 // for the same user mode when the K axis is too long for 7-bit slices.
-// TC_SLICE5: five 7-bit slices (35 bits), an operand form of the strided
-// exact-slice GEMMs only (no contraction kernel of its own).
-enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2, TC_OZAKI = 3, TC_OZAKI6 = 4, TC_SLICE5 = 5 };
+// TC_SLICE4, TC_SLICE5: four or five 7-bit slices, the operand form of the
+// strided exact-slice GEMMs (no contraction kernel of their own), cut from the
+// integer N = round(x 2^(7 NS - s)) in balanced base-128 digits.
+enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2, TC_OZAKI = 3, TC_OZAKI6 = 4, TC_SLICE5 = 5, TC_SLICE4 = 6 };
 
 constexpr int OZ_K_MAX7 = 1024;  // K * 2^14 < 2^24: exact level-2/3 sums with 7-bit slices
 constexpr int OZ_K_MAX6 = 4096;  // K * 2^12 < 2^24 with 6-bit slices
@@ -63,14 +64,15 @@ static int tc_mode_of(te_precision p, int o, int v, int ozaki_bits) {
 }
 
 __host__ __device__ constexpr bool is_ozaki(int mode) {
-  return mode == TC_OZAKI || mode == TC_OZAKI6 || mode == TC_SLICE5;
+  return mode == TC_OZAKI || mode == TC_OZAKI6 || mode == TC_SLICE5 || mode == TC_SLICE4;
 }
 
 template <int MODE>
 struct ModeTraits {
   static constexpr bool tf32 = (MODE == TC_TF32 || MODE == TC_TF32X3);
   static constexpr int nparts =
-      (MODE == TC_TF32) ? 1 : (MODE == TC_OZAKI ? 4 : ((MODE == TC_OZAKI6 || MODE == TC_SLICE5) ? 5 : 2));
+      (MODE == TC_TF32) ? 1
+                        : ((MODE == TC_OZAKI || MODE == TC_SLICE4) ? 4 : ((MODE == TC_OZAKI6 || MODE == TC_SLICE5) ? 5 : 2));
   static constexpr int nacc = is_ozaki(MODE) ? 3 : 1;   // accumulators per tile
   static constexpr int beta = MODE == TC_OZAKI6 ? 6 : 7;  // bits per slice
 };
@@ -101,6 +103,16 @@ __device__ __forceinline__ void split_store(double x, const Parts& parts, int64_
     const double l = round_sig<8>(x - h);
     reinterpret_cast<__nv_bfloat16*>(parts.p[0])[idx] = __float2bfloat16_rn((float)h);
     reinterpret_cast<__nv_bfloat16*>(parts.p[1])[idx] = __float2bfloat16_rn((float)l);
+  } else if (MODE == TC_SLICE4 || MODE == TC_SLICE5) {
+    // integer digits of x 2^-s (slice_digits): no float64 arithmetic, against
+    // five float64 operations per slice for the repeated rounding below
+    constexpr int NS = ModeTraits<MODE>::nparts;
+    const int e = 1023 - (int)((((unsigned long long)__double_as_longlong(scale)) >> 52) & 0x7FFull);  // scale = 2^-e
+    float d[NS];
+    slice_digits<NS>(x, e, d);
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      reinterpret_cast<__nv_bfloat16*>(parts.p[k])[idx] = __float2bfloat16_rn(ldexpf(d[k], -7 * (k + 1)));
   } else if (is_ozaki(MODE)) {
     constexpr int BETA = ModeTraits<MODE>::beta, NS = ModeTraits<MODE>::nparts;
     double t = x * scale;  // |t| < 1, exact power-of-two scaling
@@ -1564,7 +1576,7 @@ te_status tc_prepare_slices(const te_cluster* c, void* base_v, SliceSet* out, in
   k_group_maxabs<<<gm, 256, 0, s>>>(c->ooov, 3, o, v, (int64_t)o * v, oo, chunk, maxbits + 2 * o + oo);
   k_group_exps<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(maxbits, ng, exps);
   if (NS == 5) launch_slice_set<TC_SLICE5>(c, vp, op, pa, pb, pL, pN, e_ovvv, e_t2, e_t2L, e_nooT, s);
-  else launch_slice_set<TC_OZAKI>(c, vp, op, pa, pb, pL, pN, e_ovvv, e_t2, e_t2L, e_nooT, s);
+  else launch_slice_set<TC_SLICE4>(c, vp, op, pa, pb, pL, pN, e_ovvv, e_t2, e_t2L, e_nooT, s);
   if (cudaGetLastError() != cudaSuccess) return fail(TE_ECUDA, "slice preparation launch failed");
   out->ovvv = A;
   out->t2 = B;

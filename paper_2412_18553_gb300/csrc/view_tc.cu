@@ -371,24 +371,42 @@ __global__ void __launch_bounds__(256) k_vt_reduce(const __grid_constant__ VtPar
   }
 }
 
-// dst[p][b][c][r] = src[p][b][r][c] through a 32 x 32 shared tile
-__global__ void __launch_bounds__(256) k_vt_transpose(const __nv_bfloat16* __restrict__ src, int64_t src_ps,
-                                                       int64_t src_bs, int64_t src_rs, __nv_bfloat16* __restrict__ dst,
+// dst[p][b][c][r] = src[p][b][r][c] through a 64 x 64 shared tile; pairs of
+// BF16 elements move as one 32-bit access when every offset is even (`pairs`)
+__global__ void __launch_bounds__(256) k_vt_transpose(const unsigned short* __restrict__ src, int64_t src_ps,
+                                                       int64_t src_bs, int64_t src_rs, unsigned short* __restrict__ dst,
                                                        int64_t dst_ps, int64_t dst_bs, int64_t dst_cs, int nb, int R,
-                                                       int Cc) {
-  __shared__ __nv_bfloat16 tile[32][34];
+                                                       int Cc, int pairs) {
+  __shared__ unsigned short tile[64][65];
   const int pb = blockIdx.z, p = pb / nb, b = pb - p * nb;
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const __nv_bfloat16* s = src + p * src_ps + b * src_bs;
-  __nv_bfloat16* d = dst + p * dst_ps + b * dst_bs;
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    const int r = r0 + i, c = c0 + threadIdx.x;
-    if (r < R && c < Cc) tile[i][threadIdx.x] = s[r * src_rs + c];
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const unsigned short* s = src + p * src_ps + b * src_bs;
+  unsigned short* d = dst + p * dst_ps + b * dst_bs;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int i = ty; i < 64; i += 8) {
+    const int r = r0 + i, c = c0 + 2 * tx;
+    if (r >= R) continue;
+    const unsigned short* sr = s + r * src_rs;
+    if (pairs && c + 1 < Cc) {
+      const unsigned int w = *reinterpret_cast<const unsigned int*>(sr + c);
+      tile[i][2 * tx] = (unsigned short)(w & 0xffffu);
+      tile[i][2 * tx + 1] = (unsigned short)(w >> 16);
+    } else {
+      if (c < Cc) tile[i][2 * tx] = sr[c];
+      if (c + 1 < Cc) tile[i][2 * tx + 1] = sr[c + 1];
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    const int c = c0 + i, r = r0 + threadIdx.x;
-    if (c < Cc && r < R) d[c * dst_cs + r] = tile[threadIdx.x][i];
+  for (int i = ty; i < 64; i += 8) {
+    const int c = c0 + i, r = r0 + 2 * tx;
+    if (c >= Cc) continue;
+    unsigned short* dc = d + c * dst_cs;
+    if (pairs && r + 1 < R) {
+      *reinterpret_cast<unsigned int*>(dc + r) = (unsigned int)tile[2 * tx][i] | ((unsigned int)tile[2 * tx + 1][i] << 16);
+    } else {
+      if (r < R) dc[r] = tile[2 * tx][i];
+      if (r + 1 < R) dc[r + 1] = tile[2 * tx + 1][i];
+    }
   }
 }
 
@@ -606,15 +624,19 @@ te_status vt_launch(Handle* h, VtBuild* b, cudaStream_t s) {
 
 cudaError_t vt_transpose(const void* src, int64_t src_ps, int64_t src_bs, int64_t src_rs, void* dst, int64_t dst_ps,
                          int64_t dst_bs, int64_t dst_cs, int np, int nb, int R, int Cc, cudaStream_t s) {
-  if (nb > 65535 || R <= 0 || Cc <= 0 || (R + 31) / 32 > 65535) return cudaErrorInvalidValue;
+  if (nb > 65535 || R <= 0 || Cc <= 0 || (R + 63) / 64 > 65535) return cudaErrorInvalidValue;
+  const int pairs = (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 3) == 0 &&
+                     ((src_ps | src_bs | src_rs | dst_ps | dst_bs | dst_cs) & 1) == 0)
+                        ? 1
+                        : 0;
   // planes in groups whose (plane, batch) pairs fit the grid's z extent
   const int per = std::max(1, std::min(np, 65535 / nb));
   for (int p0 = 0; p0 < np; p0 += per) {
     const int n = std::min(per, np - p0);
-    dim3 grid((unsigned)((Cc + 31) / 32), (unsigned)((R + 31) / 32), (unsigned)(n * nb));
-    k_vt_transpose<<<grid, dim3(32, 8), 0, s>>>(static_cast<const __nv_bfloat16*>(src) + p0 * src_ps, src_ps,
-                                                 src_bs, src_rs, static_cast<__nv_bfloat16*>(dst) + p0 * dst_ps,
-                                                 dst_ps, dst_bs, dst_cs, nb, R, Cc);
+    dim3 grid((unsigned)((Cc + 63) / 64), (unsigned)((R + 63) / 64), (unsigned)(n * nb));
+    k_vt_transpose<<<grid, dim3(32, 8), 0, s>>>(static_cast<const unsigned short*>(src) + p0 * src_ps, src_ps, src_bs,
+                                                 src_rs, static_cast<unsigned short*>(dst) + p0 * dst_ps, dst_ps, dst_bs,
+                                                 dst_cs, nb, R, Cc, pairs);
   }
   return cudaGetLastError();
 }

@@ -35,39 +35,64 @@ namespace te {
 // per-triple adjoint of the energy epilogue, one thread per ordered (a,b,c)
 // ---------------------------------------------------------------------------
 
-// One thread per orbit representative a >= b >= c (the other threads of the
-// v^3 grid have nothing to do): W~ and Y are formed once per orbit and every
-// distinct element of the orbit gets its dW~, dY and dD.
+// orbit index t = a(a+1)(a+2)/6 + b(b+1)/2 + c -> (a, b, c), a >= b >= c
+// (FP32 estimates, exact integer fix-ups)
+__device__ __forceinline__ void orbit_abc(int64_t t, int* pa, int* pb, int* pc) {
+  int a = (int)cbrtf(6.0f * (float)t);
+  while (a > 0 && (int64_t)a * (a + 1) * (a + 2) / 6 > t) --a;
+  while ((int64_t)(a + 1) * (a + 2) * (a + 3) / 6 <= t) ++a;
+  const int64_t rem = t - (int64_t)a * (a + 1) * (a + 2) / 6;
+  int b = (int)sqrtf(2.0f * (float)rem);
+  while (b > 0 && (int64_t)b * (b + 1) / 2 > rem) --b;
+  while ((int64_t)(b + 1) * (b + 2) / 2 <= rem) ++b;
+  *pa = a;
+  *pb = b;
+  *pc = (int)(rem - (int64_t)b * (b + 1) / 2);
+}
+
+// blocks of the adjoint epilogue: a fixed number per device, so the orbits
+// each block takes, and every partial sum, do not depend on the cluster
+int adjoint_grid(int num_sms) { return std::min(4 * std::max(1, num_sms), 8192); }
+
+// Threads stride over the orbits a >= b >= c (v(v+1)(v+2)/6 of them): W~ and Y
+// are formed once per orbit and every distinct element of the orbit gets its
+// dW~, dY and dD.  1/D is Newton's iteration x <- x (2 - D x) from an FP32
+// seed, twice (relative error below 2^-90 before rounding): float64 division
+// costs several times more on GB300's float64 units.  Each block writes its
+// energy and dD partial sums to epart, dpart[blockIdx.x].
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs A) {
   __shared__ double red[8], redd[8];
-  const int64_t v = A.v, v3 = v * v * v;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t v = A.v;
+  const int64_t norb = v * (v + 1) * (v + 2) / 6;
+  const double eo = A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k];
   double contrib = 0.0, dsum = 0.0, wmax = 0.0;
-  if (e < v3) {
-    const int a = (int)(e / (v * v)), b = (int)((e / v) % v), c = (int)(e % v);
-    if (a >= b && b >= c) {
-      double W[6], Y[6], RW[6], RY[6];
-      int64_t idx[6];
-      orbit_values(A, a, b, c, W, Y);
-      orbit_index(v, a, b, c, idx);
-      r_orbit(W, RW);
-      r_orbit(Y, RY);
-      const unsigned distinct = orbit_distinct(a, b, c);
-      const double D = (A.eps_o[A.i] + A.eps_o[A.j] + A.eps_o[A.k]) - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
-      const double rD = 1.0 / D, q = A.w * rD;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < norb; t += (int64_t)gridDim.x * blockDim.x) {
+    int a, b, c;
+    orbit_abc(t, &a, &b, &c);
+    double W[6], Y[6], RW[6], RY[6];
+    int64_t idx[6];
+    orbit_values(A, a, b, c, W, Y);
+    orbit_index(v, a, b, c, idx);
+    r_orbit(W, RW);
+    r_orbit(Y, RY);
+    const unsigned distinct = orbit_distinct(a, b, c);
+    const double D = eo - A.eps_v[a] - A.eps_v[b] - A.eps_v[c];
+    double rD = (double)__frcp_rn((float)D);
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    const double q = A.w * rD;
 #pragma unroll
-      for (int n = 0; n < 6; ++n) {
-        if (!(distinct >> n & 1u)) continue;
-        const double RV = RW[n] + RY[n];
-        const double dw = q * (2.0 * RW[n] + RY[n]);
-        const double dd = -q * W[n] * RV * rD;
-        A.dW[idx[n]] = dw;
-        A.dY[idx[n]] = q * RW[n];
-        A.dD[idx[n]] = dd;
-        dsum += dd;
-        contrib += W[n] * RV * rD;
-        wmax = fmax(wmax, fabs(dw));
-      }
+    for (int n = 0; n < 6; ++n) {
+      if (!(distinct >> n & 1u)) continue;
+      const double RV = RW[n] + RY[n];
+      const double dw = q * (2.0 * RW[n] + RY[n]);
+      const double dd = -q * W[n] * RV * rD;
+      A.dW[idx[n]] = dw;
+      A.dY[idx[n]] = q * RW[n];
+      A.dD[idx[n]] = dd;
+      dsum += dd;
+      contrib += W[n] * RV * rD;
+      wmax = fmax(wmax, fabs(dw));
     }
   }
   for (int off = 16; off > 0; off >>= 1) {
@@ -809,7 +834,7 @@ int64_t splitk_cap(int64_t o, int64_t v) { return 80 * std::max(v * v, o * v); }
 
 size_t vjp_fp64_bytes(int64_t o, int64_t v) {
   const int64_t v3 = v * v * v, nt = num_unique_triples(o);
-  const int64_t nblk = (v3 + 255) / 256;
+  const int64_t nblk = std::max<int64_t>((v3 + 255) / 256, 8192);  // at least adjoint_grid's largest
   auto a = [](int64_t n) { return ((size_t)n * 8 + 255) & ~size_t(255); };
   return a(o * v * v * o) + a(o * o * v * o) + a(o * v * o * v) + a(3 * v3) + 3 * a(v3) + a(o * v * o * v) +
          2 * a(nblk) + a(std::max<int64_t>(1, nt)) + a(splitk_cap(o, v)) + 1024;
@@ -841,7 +866,8 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64_t 
   W.dY = take(v3);
   W.dD = take(v3);
   W.dOVS = take((int64_t)o * v * o * v);
-  const int64_t nblk = (v3 + 255) / 256;
+  const int64_t nblk = std::max<int64_t>((v3 + 255) / 256, adjoint_grid(h->num_sms));
+  const int64_t agrid = adjoint_grid(h->num_sms);
   W.epart = take(nblk);
   W.dpart = take(nblk);
   W.shares = take(std::max<int64_t>(1, nt));
@@ -886,8 +912,8 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64_t 
     A.w = gE * (double)T.m / 3.0;
     A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v;
     A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart; A.dpart = W.dpart;
-    k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
-    k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
+    k_adjoint<<<(unsigned)agrid, 256, 0, s>>>(A);
+    k_sum_share<<<1, 256, 0, s>>>(W.epart, agrid, (double)T.m / 3.0, W.shares + t);
     h->n_launches += 3;
     // back-propagation through the three G blocks; Gamma_g is a strided view of dW~
     for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
@@ -942,7 +968,7 @@ te_status run_vjp_fp64(Handle* h, const te_cluster* c, int64_t t_begin, int64_t 
       if (g->t1) k_dt1<<<(unsigned)v, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
     }
     if (g->eps_v) k_deps_v<<<(unsigned)v, 256, 0, s>>>(v, W.dD, g->eps_v);
-    if (g->eps_o) k_deps_o<<<1, 256, 0, s>>>(nblk, W.dpart, T.i, T.j, T.k, g->eps_o);
+    if (g->eps_o) k_deps_o<<<1, 256, 0, s>>>(agrid, W.dpart, T.i, T.j, T.k, g->eps_o);
     h->n_launches += 8;
     e = cudaGetLastError();
   }
@@ -986,10 +1012,8 @@ static int adjoint_slices(int64_t v) { return v > 200 ? 5 : 4; }
 // Slices of three index permutations of dW~ into three layouts L[x][y][z]
 // (z padded to vp), layout b of phase f holding the slices of dW~[pi(x, y, z)]:
 //   phase 0: pi = (x,y,z), (z,x,y), (y,z,x);  phase 1: (z,y,x), (x,z,y), (y,x,z).
-// With 2^e > max |dW~| (e written to *e_out), N = rint(dW~ 2^(7 NS - e)) is cut
-// into balanced base-128 digits, N = sum_k d_k 128^(NS-1-k), |d_k| <= 128, and
-// slice k holds d_k 2^-7(k+1) (exact in BF16): dW~ = 2^e sum_k slice_k to within
-// 2^(e - 7 NS - 1).  Three float64 operations per element.  A block handles one
+// With 2^e > max |dW~| (e written to *e_out), the slices are slice_digits'
+// (integer arithmetic on the bits of dW~, no float64 operations).  A block handles one
 // 32 x 32 tile of the (c, z) plane at one value of the third index, c being
 // the index along which dW~ is contiguous for this permutation (or y when that
 // is z), so both the reads and the writes are coalesced.
@@ -1003,7 +1027,6 @@ __global__ void __launch_bounds__(256) k_dw_layouts(const double* __restrict__ d
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0) *e_out = ex;
-  const double sc1 = ldexp(1.0, -ex), mul = (double)(1ll << (7 * NS));
   const int perm = phase * 3 + (int)blockIdx.z;
   const int64_t V = v, V2 = V * V, plane = V2 * vp;
   // source strides of the output indices (x, y, z)
@@ -1037,15 +1060,8 @@ __global__ void __launch_bounds__(256) k_dw_layouts(const double* __restrict__ d
   for (int i = ty; i < 32; i += 8) {
     const int cc = c0 + i, zz = z0 + tx;
     if (cc >= v || zz >= v) continue;
-    long long N = __double2ll_rn((tile[i][tx] * sc1) * mul);  // |dW~ 2^-e| < 1
     float d[NS];
-#pragma unroll
-    for (int k = NS - 1; k > 0; --k) {
-      const int dk = (int)((N + 64) & 127) - 64;
-      d[k] = (float)dk;
-      N = (N - dk) >> 7;
-    }
-    d[0] = (float)N;
+    slice_digits<NS>(tile[i][tx], ex, d);
     const int64_t xi = cidx == 0 ? cc : w, yi = cidx == 0 ? w : cc;
     const int64_t at = (xi * V + yi) * vp + zz;
 #pragma unroll
@@ -1095,7 +1111,7 @@ static VjpTcSizes vjp_tc_sizes(int64_t o, int64_t v, int num_sms) {
 
 size_t vjp_tc_bytes(int64_t o, int64_t v, int num_sms) {
   const int64_t v3 = v * v * v, nt = num_unique_triples(o);
-  const int64_t nblk = (v3 + 255) / 256;
+  const int64_t nblk = std::max<int64_t>((v3 + 255) / 256, 8192);  // at least adjoint_grid's largest
   const VjpTcSizes z = vjp_tc_sizes(o, v, num_sms);
   auto a = [](int64_t n) { return ((size_t)n * 8 + 1023) & ~size_t(1023); };
   return tc_slices_bytes((int)o, (int)v, z.ns) + 1024 + a(o * v * o * v) + z.region + a(v3) + a(o * v * o * v) +
@@ -1148,7 +1164,8 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
   W.dD = W.dY + ((((size_t)v3 * 8 + 1023) & ~size_t(1023)) / 8);
   W.dW = take(v3);
   W.dOVS = take((int64_t)o * v * o * v);
-  const int64_t nblk = (v3 + 255) / 256;
+  const int64_t nblk = std::max<int64_t>((v3 + 255) / 256, adjoint_grid(h->num_sms));
+  const int64_t agrid = adjoint_grid(h->num_sms);
   W.epart = take(nblk);
   W.dpart = take(nblk);
   W.shares = take(std::max<int64_t>(1, nt));
@@ -1346,8 +1363,8 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
     A.G = W.G; A.ovs = W.ovs; A.t1 = c->t1; A.eps_o = c->eps_o; A.eps_v = c->eps_v;
     A.dW = W.dW; A.dY = W.dY; A.dD = W.dD; A.epart = W.epart; A.dpart = W.dpart; A.dwmax = dwmax;
     cudaMemsetAsync(dwmax, 0, 8, s);
-    k_adjoint<<<(unsigned)nblk, 256, 0, s>>>(A);
-    k_sum_share<<<1, 256, 0, s>>>(W.epart, nblk, (double)T.m / 3.0, W.shares + t);
+    k_adjoint<<<(unsigned)agrid, 256, 0, s>>>(A);
+    k_sum_share<<<1, 256, 0, s>>>(W.epart, agrid, (double)T.m / 3.0, W.shares + t);
     // the Y and denominator parts; G, dY and dD are dead afterwards and their
     // memory takes the dW~ layouts
     const unsigned gb2 = (unsigned)((v2 + 255) / 256);
@@ -1356,7 +1373,7 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
       if (g->t1) k_dt1<<<(unsigned)v, 256, 0, s>>>(mode, o, v, T.i, T.j, T.k, W.dY, W.ovs, g->t1);
     }
     if (g->eps_v) k_deps_v<<<(unsigned)v, 256, 0, s>>>(v, W.dD, g->eps_v);
-    if (g->eps_o) k_deps_o<<<1, 256, 0, s>>>(nblk, W.dpart, T.i, T.j, T.k, g->eps_o);
+    if (g->eps_o) k_deps_o<<<1, 256, 0, s>>>(agrid, W.dpart, T.i, T.j, T.k, g->eps_o);
     const int nt32 = (v + 31) / 32;
     const dim3 lgrid((unsigned)(nt32 * nt32), (unsigned)v, 3), lblk(32, 8);
     if (ns == 5) k_dw_layouts<5><<<lgrid, lblk, 0, s>>>(W.dW, v, (int)vp, 0, dwmax, dwexp, lay, (int64_t)lay_stride);
