@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-fp64-anchor", action="store_true",
                     help="skip the one float64 GPU pass over the whole cluster (about 11 minutes at "
                          "nocc=32 nvir=320) that gives the FP64 GPU rate and the whole-cluster |dE|")
+    ap.add_argument("--adjoint-sample", type=int, default=0,
+                    help="only the adjoint sample leg (N single-triple ranges) of the workload, one JSON line")
     ap.add_argument("--vjp-triples", type=int, default=0,
                     help="time the adjoint of this many single-triple ranges of the workload itself "
                          "(both modes) and extrapolate; for clusters whose whole adjoint is too long")
@@ -283,7 +285,9 @@ def run_batch96(args):
 def vjp_sample_leg(te, h, arrs, o, v, ntrip, world):
     """t_energy_vjp_triples over ``ntrip`` single-triple ranges spread over the
     canonical order (the heaviest last), exact slices and float64, CUDA-event
-    timed; the whole-cluster adjoint time is extrapolated by triple count.
+    timed.  A call's setup (operand slices, zeroed gradients) is timed on an
+    empty range and taken out of the per-triple time; the whole-cluster
+    adjoint time is extrapolated as setup + triples x per-triple time.
     The two modes' gradients are compared per input on 4096 entries (the 2048
     largest of the exact-slice gradient and 2048 seeded ones), relative to the
     float64 gradient's largest magnitude; only one gradient set is alive on
@@ -311,59 +315,72 @@ def vjp_sample_leg(te, h, arrs, o, v, ntrip, world):
             return max(float(x[p].abs().max()) for p in set(_triple_of(tt, o)))
         return float(x.abs().max())
     grouped = False
+
+    def consume(prec, gg, tt, rel):
+        # sample (exact slices) or compare (float64) the gradients of one call;
+        # no reference to a gradient survives the call
+        for n, x in gg.items():
+            flat = x.view(-1)
+            if prec == "ozaki":
+                k = min(2048, flat.numel())
+                idx = torch.cat([top_entries(n, x, tt, k),
+                                 torch.randint(0, flat.numel(), (k,), device="cuda", generator=gen)])
+                sample[(tt, n)] = (idx, flat[idx].clone())
+            else:
+                idx, vo = sample.pop((tt, n))
+                scale = max(max_abs(n, x, tt), 1e-300)
+                rel[n] = max(rel.get(n, 0.0), float((vo - flat[idx]).abs().max()) / scale)
+
+    def timed(prec, tt, grp):
+        torch.cuda.synchronize()
+        e0.record()
+        e, gg = te.t_energy_vjp_triples(arrs, tt, tt + 1, precision=prec, handle=h, grads=grp)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), float(e), gg
+
     for prec in ("ozaki", "fp64"):
         ms, es, rel = 0.0, [], {}
         for tt in picks:
-            torch.cuda.synchronize()
+            groups = ((("ovvv",), tuple(n for n in te.NAMES if n != "ovvv")) if grouped else (None,))
             try:
-                e0.record()
-                e, g = te.t_energy_vjp_triples(arrs, tt, tt + 1, precision=prec, handle=h)
-                e1.record()
-                torch.cuda.synchronize()
-                ms += e0.elapsed_time(e1)
+                for grp in groups:
+                    t_ms, ev, gg = timed(prec, tt, grp)
+                    ms += t_ms
+                    consume(prec, gg, tt, rel)
+                    del gg
+                    torch.cuda.empty_cache()
             except (torch.cuda.OutOfMemoryError, te.TEnergyError):
+                if grouped:
+                    raise
                 # all seven gradients do not fit beside the inputs and the
                 # workspace: ovvv's alone, then the rest (the time is the sum
                 # of the two calls, which repeats the recomputed G blocks)
                 torch.cuda.synchronize()
                 torch.cuda.empty_cache()
                 grouped = True
-                g = {}
                 for grp in (("ovvv",), tuple(n for n in te.NAMES if n != "ovvv")):
-                    e0.record()
-                    e, gg = te.t_energy_vjp_triples(arrs, tt, tt + 1, precision=prec, handle=h, grads=grp)
-                    e1.record()
-                    torch.cuda.synchronize()
-                    ms += e0.elapsed_time(e1)
-                    for n, x in gg.items():
-                        flat = x.view(-1)
-                        if prec == "ozaki":
-                            k = min(2048, flat.numel())
-                            idx = torch.cat([top_entries(n, x, tt, k),
-                                             torch.randint(0, flat.numel(), (k,), device="cuda", generator=gen)])
-                            sample[(tt, n)] = (idx, flat[idx].clone())
-                        else:
-                            idx, vo = sample.pop((tt, n))
-                            scale = max(max_abs(n, x, tt), 1e-300)
-                            rel[n] = max(rel.get(n, 0.0), float((vo - flat[idx]).abs().max()) / scale)
+                    t_ms, ev, gg = timed(prec, tt, grp)
+                    ms += t_ms
+                    consume(prec, gg, tt, rel)
                     del gg
                     torch.cuda.empty_cache()
-            es.append(float(e))
-            for n, x in g.items():
-                flat = x.view(-1)
-                if prec == "ozaki":
-                    k = min(2048, flat.numel())
-                    rnd = torch.randint(0, flat.numel(), (k,), device="cuda", generator=gen)
-                    idx = torch.cat([top_entries(n, x, tt, k), rnd])
-                    sample[(tt, n)] = (idx, flat[idx].clone())
-                else:
-                    idx, vo = sample.pop((tt, n))
-                    scale = max(max_abs(n, x, tt), 1e-300)
-                    rel[n] = max(rel.get(n, 0.0), float((vo - flat[idx]).abs().max()) / scale)
-            del e, g
+            es.append(ev)
+        # the setup of a call: an empty range with the same gradient groups
+        setup_ms = 0.0
+        for grp in ((("ovvv",), tuple(n for n in te.NAMES if n != "ovvv")) if grouped else (None,)):
+            torch.cuda.synchronize()
+            e0.record()
+            _e, _g = te.t_energy_vjp_triples(arrs, 0, 0, precision=prec, handle=h, grads=grp)
+            e1.record()
+            torch.cuda.synchronize()
+            setup_ms += e0.elapsed_time(e1)
+            del _e, _g
             torch.cuda.empty_cache()
-        out[prec] = {"ms_per_triple": ms / len(picks), "ms_cluster_extrapolated": ms / len(picks) * nt,
-                     "gflops_3F": world * 3 * 12.0 * v ** 3 * (v + o) / (ms / len(picks) / 1e3) / 1e9,
+        per = max(1e-9, ms / len(picks) - setup_ms)
+        out[prec] = {"setup_ms": setup_ms, "ms_per_call": ms / len(picks), "ms_per_triple": per,
+                     "ms_cluster_extrapolated": setup_ms + per * nt,
+                     "gflops_3F": world * 3 * 12.0 * v ** 3 * (v + o) / (per / 1e3) / 1e9,
                      "shares": es}
         if prec == "fp64":
             out["grad_rel_diff_ozaki_vs_fp64"] = rel
@@ -439,12 +456,33 @@ def run_reference(args):
     return 0
 
 
+def run_adjoint_sample(args):
+    """The exact-slice and float64 adjoints on single-triple ranges of one
+    cluster (vjp_sample_leg), without the energy steps: one JSON line."""
+    import paper_2412_18553_gb300 as te
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    (o, v, naux, seed), arrs = make_workload(args.workload, local)
+    h = te.Handle(local)
+    te.t_energy_vjp_triples(arrs, 0, 1, precision="ozaki", handle=h, grads=("t1",))  # warm-up: workspace
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    out = vjp_sample_leg(te, h, arrs, o, v, args.adjoint_sample, 1)
+    h.sync()
+    print(json.dumps({"metric": "adjoint of E(T) per unique triple (ms)", "unit": "ms", "higher_is_better": False,
+                      "config": {"workload": f"{args.workload}: nocc={o} nvir={v} naux={naux} seed={seed}"},
+                      "data": "synthetic", "adjoint": out}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch96":
         return run_batch96(args)
+    if args.adjoint_sample > 0:
+        return run_adjoint_sample(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
