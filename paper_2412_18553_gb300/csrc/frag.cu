@@ -7,6 +7,7 @@
 
 #include "strided.h"
 #include "tc_path.h"
+#include "view_tc.h"
 #include "te_internal.h"
 
 namespace te {
@@ -191,91 +192,87 @@ te_status run_frag(Handle* h, const te_cluster* c, const double* cf, te_precisio
     if (st != TE_OK) return st;
     h->n_launches += 18;
   }
+  // exact slices: the tcgen05 view GEMM (view_tc.cu) over the six segment
+  // views of each slice set, encoded once
+  VtBank bank;
+  bank.n = 0;
+  int m0[6], mA[6], mB[6];
+  const int NT = vt_ntile(v);
+  if (oz) {
+    if ((st = vt_slice_maps(&bank, S0, o, v, NT, m0)) != TE_OK) return st;
+    if ((st = vt_slice_maps(&bank, SA, o, v, NT, mA)) != TE_OK) return st;
+    if ((st = vt_slice_maps(&bank, SB, o, v, NT, mB)) != TE_OK) return st;
+  }
 
-  using bf = __nv_bfloat16;
   std::vector<Triple> trip = unique_triples(o);
   const double third = 1.0 / 3.0;
   for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
     const Triple T = trip[t];
-    e = cudaMemsetAsync(W.SG, 0, sizeof(double) * 3 * v3, s);
-    if (e != cudaSuccess) break;
+    if (oz) {
+      // per G block (p, q, r): the block itself (S1..S4 of the input slices)
+      // and its projection SG (two products per segment, one operand
+      // transformed), 1/3 for the average over the three occupied slots
+      VtBuild b;
+      vt_begin(&b, S0.ns);
+      for (int gi = 0; gi < 3; ++gi) {
+        int pp, qq, rr;
+        if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
+        else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
+        else { pp = T.k; qq = T.i; rr = T.j; }
+        const int f_p[5] = {0, 0, 0, 0, pp}, f_q[5] = {0, 0, 0, 0, qq};
+        const int t_qr[5] = {0, 0, 0, qq, rr}, t_pr[5] = {0, 0, 0, pp, rr};
+        const int n_rq[5] = {0, 0, 0, rr, qq}, n_rp[5] = {0, 0, 0, rr, pp};
+        const int64_t rq = (int64_t)rr * o + qq, rp = (int64_t)rr * o + pp;
+        const int64_t nqr = (int64_t)qq * o + rr, npr = (int64_t)pp * o + rr;
+        auto u = [&](int m) { return vt_use(&b, bank, m); };
+        VtJob* J = vt_job(&b, v, v, v, 8, 16, NT, W.G + gi * v3, v2, v, 1, 1);
+        vt_seg(J, u(m0[0]), u(m0[4]), 1, v, f_p, t_qr, S0.e_ovvv + pp, S0.e_t2 + rq, 1.0);
+        vt_seg(J, u(m0[1]), u(m0[4]), 1, v, f_q, t_pr, S0.e_ovvv + qq, S0.e_t2 + rp, 1.0);
+        vt_seg(J, u(m0[3]), u(m0[5]), 1, o, f_p, n_rq, S0.e_t2L + pp, S0.e_nooT + nqr, 1.0);
+        vt_seg(J, u(m0[2]), u(m0[5]), 1, o, f_q, n_rp, S0.e_t2L + qq, S0.e_nooT + npr, 1.0);
+        VtJob* JS = vt_job(&b, v, v, v, 8, 16, NT, W.SG + gi * v3, v2, v, 1, 1);
+        JS->jalpha = third;
+        vt_seg(JS, u(mA[0]), u(m0[4]), 1, v, f_p, t_qr, SA.e_ovvv + pp, S0.e_t2 + rq, 1.0);  // ovvvC[p] t2[r,q]
+        vt_seg(JS, u(m0[0]), u(mA[4]), 1, v, f_p, t_qr, S0.e_ovvv + pp, SA.e_t2 + rq, 1.0);  // ovvv[p] t2C[r,q]
+        vt_seg(JS, u(mA[1]), u(m0[4]), 1, v, f_q, t_pr, SA.e_ovvv + qq, S0.e_t2 + rp, 1.0);  // ovvvC[q] t2[r,p]
+        vt_seg(JS, u(m0[1]), u(mA[4]), 1, v, f_q, t_pr, S0.e_ovvv + qq, SA.e_t2 + rp, 1.0);  // ovvv[q] t2C[r,p]
+        vt_seg(JS, u(mB[3]), u(m0[5]), 1, o, f_p, n_rq, SB.e_t2L + pp, S0.e_nooT + nqr, 1.0);  // t2LC[p] nooT[q][r]
+        vt_seg(JS, u(m0[3]), u(mA[5]), 1, o, f_p, n_rq, S0.e_t2L + pp, SA.e_nooT + nqr, 1.0);  // t2L[p] nooTC[q][r]
+        vt_seg(JS, u(mB[2]), u(m0[5]), 1, o, f_q, n_rp, SB.e_t2L + qq, S0.e_nooT + npr, 1.0);  // t2LC[q] nooT[p][r]
+        vt_seg(JS, u(m0[2]), u(mA[5]), 1, o, f_q, n_rp, S0.e_t2L + qq, SA.e_nooT + npr, 1.0);  // t2L[q] nooTC[p][r]
+      }
+      if ((st = vt_finish(&b, h->num_sms, nullptr, 0, nullptr)) != TE_OK) return st;
+      if ((st = vt_launch(h, &b, s)) != TE_OK) return st;
+    }
     if (!oz) {
+      e = cudaMemsetAsync(W.SG, 0, sizeof(double) * 3 * v3, s);
+      if (e != cudaSuccess) break;
       e = launch_gemm_fp64(&P, h->d_triples, t, 1, W.G, s);
       ++h->n_launches;
     }
-    for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
+    for (int gi = 0; gi < 3 && e == cudaSuccess && !oz; ++gi) {
       int pp, qq, rr;
       if (gi == 0) { pp = T.i; qq = T.j; rr = T.k; }
       else if (gi == 1) { pp = T.j; qq = T.k; rr = T.i; }
       else { pp = T.k; qq = T.i; rr = T.j; }
-      double* Gg = W.G + gi * v3;
       double* SGg = W.SG + gi * v3;
-      if (!oz) {
-        // float64: the eight products of SG(p,q,r), rows (x, y), columns z
-        auto run = [&](const double* A, int64_t am1, int64_t am2, int64_t K, const double* B, int64_t bn) {
-          if (e == cudaSuccess)
-            e = gemm_strided(GemmView{A, B, SGg, v, v, v, K, 1, am1, am2, 1, 0, 1, 0, bn, v2, v, 1, third}, h->num_sms,
-                     W.scratch, W.scratch_cap, s, &h->n_launches);
-        };
-        const int64_t orq = ((int64_t)rr * o + qq) * v2, orp = ((int64_t)rr * o + pp) * v2;
-        run(W.ovvvC + pp * v3, v2, v, v, c->t2 + orq, v);     // S1: ovvvC[p,x,y,d] t2[r,q,z,d]
-        run(c->ovvv + pp * v3, v2, v, v, W.t2C + orq, v);     //     ovvv[p] t2C[r,q]
-        run(W.ovvvC + qq * v3, v, v2, v, c->t2 + orp, v);     // S2: ovvvC[q,y,x,d] t2[r,p,z,d]
-        run(c->ovvv + qq * v3, v, v2, v, W.t2C + orp, v);     //     ovvv[q] t2C[r,p]
-        const int64_t lp = (int64_t)pp * v2 * o, lq = (int64_t)qq * v2 * o;
-        const int64_t nqr = ((int64_t)qq * o + rr) * v * o, npr = ((int64_t)pp * o + rr) * v * o;
-        run(W.t2LC + lp, o, (int64_t)v * o, o, W.nooT + nqr, o);   // S3: t2LC[p][y][x][l] nooT[q][r][z][l]
-        run(W.t2L + lp, o, (int64_t)v * o, o, W.nooTC + nqr, o);   //     t2L[p] nooTC[q][r]
-        run(W.t2LC + lq, (int64_t)v * o, o, o, W.nooT + npr, o);   // S4: t2LC[q][x][y][l] nooT[p][r][z][l]
-        run(W.t2L + lq, (int64_t)v * o, o, o, W.nooTC + npr, o);   //     t2L[q] nooTC[p][r]
-      } else {
-        auto run = [&](const OzView& gv) {
-          if (e == cudaSuccess) e = gemm_oz(gv, h->num_sms, W.scratch, W.scratch_cap, s, &h->n_launches);
-        };
-        const int64_t vp = S0.vp, op = S0.op;
-        auto ovvv_of = [&](const SliceSet& S, int x) { return static_cast<const bf*>(S.ovvv) + x * S.ovvv_p; };
-        auto t2_of = [&](const SliceSet& S, int r, int q) {
-          return static_cast<const bf*>(S.t2) + ((int64_t)r * o + q) * S.t2_rq;
-        };
-        auto t2L_of = [&](const SliceSet& S, int q) { return static_cast<const bf*>(S.t2L) + q * S.t2L_q; };
-        auto nooT_of = [&](const SliceSet& S, int p, int r) {
-          return static_cast<const bf*>(S.nooT) + ((int64_t)p * o + r) * S.nooT_pr;
-        };
-        // S1: rows (x, y) of ovvv[p] (K = d), columns z of t2[r,q]
-        auto s1 = [&](const SliceSet& SX, const SliceSet& ST, int ov, int r, int q, double* C, double al, int ow) {
-          run(OzView{ovvv_of(SX, ov), t2_of(ST, r, q), SX.ovvv_plane, ST.t2_plane, C, v, v, v, v, 1, v * vp, vp, 1,
-                     0, 1, 0, vp, v2, v, 1, al, SX.e_ovvv + ov, ST.e_t2 + ((int64_t)r * o + q), ow});
-        };
-        // S2: rows (x, y) of ovvv[q] read transposed (y, x)
-        auto s2 = [&](const SliceSet& SX, const SliceSet& ST, int ov, int r, int q, double* C, double al) {
-          run(OzView{ovvv_of(SX, ov), t2_of(ST, r, q), SX.ovvv_plane, ST.t2_plane, C, v, v, v, v, 1, vp, v * vp, 1,
-                     0, 1, 0, vp, v2, v, 1, al, SX.e_ovvv + ov, ST.e_t2 + ((int64_t)r * o + q), 0});
-        };
-        // S3: t2L[p][y][x][l] nooT[q][r][z][l]
-        auto s3 = [&](const SliceSet& SL, const SliceSet& SN, int lp, int nq, int nr, double* C, double al) {
-          run(OzView{t2L_of(SL, lp), nooT_of(SN, nq, nr), SL.t2L_plane, SN.nooT_plane, C, v, v, v, o, 1, op,
-                     v * op, 1, 0, 1, 0, op, v2, v, 1, al, SL.e_t2L + lp, SN.e_nooT + ((int64_t)nq * o + nr), 0});
-        };
-        // S4: t2L[q][x][y][l] nooT[p][r][z][l]
-        auto s4 = [&](const SliceSet& SL, const SliceSet& SN, int lq, int np, int nr, double* C, double al) {
-          run(OzView{t2L_of(SL, lq), nooT_of(SN, np, nr), SL.t2L_plane, SN.nooT_plane, C, v, v, v, o, 1, v * op,
-                     op, 1, 0, 1, 0, op, v2, v, 1, al, SL.e_t2L + lq, SN.e_nooT + ((int64_t)np * o + nr), 0});
-        };
-        // the G block itself (first product overwrites)
-        s1(S0, S0, pp, rr, qq, Gg, 1.0, 1);
-        s2(S0, S0, qq, rr, pp, Gg, 1.0);
-        s3(S0, S0, pp, qq, rr, Gg, 1.0);
-        s4(S0, S0, qq, pp, rr, Gg, 1.0);
-        // its projection
-        s1(SA, S0, pp, rr, qq, SGg, third, 0);
-        s1(S0, SA, pp, rr, qq, SGg, third, 0);
-        s2(SA, S0, qq, rr, pp, SGg, third);
-        s2(S0, SA, qq, rr, pp, SGg, third);
-        s3(SB, S0, pp, qq, rr, SGg, third);
-        s3(S0, SA, pp, qq, rr, SGg, third);
-        s4(SB, S0, qq, pp, rr, SGg, third);
-        s4(S0, SA, qq, pp, rr, SGg, third);
-      }
+      // float64: the eight products of SG(p,q,r), rows (x, y), columns z
+      auto run = [&](const double* A, int64_t am1, int64_t am2, int64_t K, const double* B, int64_t bn) {
+        if (e == cudaSuccess)
+          e = gemm_strided(GemmView{A, B, SGg, v, v, v, K, 1, am1, am2, 1, 0, 1, 0, bn, v2, v, 1, third}, h->num_sms,
+                           W.scratch, W.scratch_cap, s, &h->n_launches);
+      };
+      const int64_t orq = ((int64_t)rr * o + qq) * v2, orp = ((int64_t)rr * o + pp) * v2;
+      run(W.ovvvC + pp * v3, v2, v, v, c->t2 + orq, v);     // S1: ovvvC[p,x,y,d] t2[r,q,z,d]
+      run(c->ovvv + pp * v3, v2, v, v, W.t2C + orq, v);     //     ovvv[p] t2C[r,q]
+      run(W.ovvvC + qq * v3, v, v2, v, c->t2 + orp, v);     // S2: ovvvC[q,y,x,d] t2[r,p,z,d]
+      run(c->ovvv + qq * v3, v, v2, v, W.t2C + orp, v);     //     ovvv[q] t2C[r,p]
+      const int64_t lp = (int64_t)pp * v2 * o, lq = (int64_t)qq * v2 * o;
+      const int64_t nqr = ((int64_t)qq * o + rr) * v * o, npr = ((int64_t)pp * o + rr) * v * o;
+      run(W.t2LC + lp, o, (int64_t)v * o, o, W.nooT + nqr, o);   // S3: t2LC[p][y][x][l] nooT[q][r][z][l]
+      run(W.t2L + lp, o, (int64_t)v * o, o, W.nooTC + nqr, o);   //     t2L[p] nooTC[q][r]
+      run(W.t2LC + lq, (int64_t)v * o, o, o, W.nooT + npr, o);   // S4: t2LC[q][x][y][l] nooT[p][r][z][l]
+      run(W.t2L + lq, (int64_t)v * o, o, o, W.nooTC + npr, o);   //     t2L[q] nooTC[p][r]
     }
     if (e != cudaSuccess) break;
     AdjArgs A{};

@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include "ptx_sm100.cuh"
+#include "tc_path.h"
 #include "view_tc.h"
 
 namespace te {
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(VT_THREADS, 1)
         acc_phase ^= 1u;
       }
       if (!ok || !valid) continue;
-      const double scale = ldexp(1.0, eref);
+      const double scale = ldexp(J.jalpha, eref);
       double* dst;
       int64_t dn;
       const bool store = J.nsplit > 1 || J.overwrite;
@@ -504,11 +505,16 @@ VtJob* vt_job(VtBuild* b, int M1, int M2, int N, int TA, int TB, int NT, double*
   j->c_m2 = c_m2;
   j->c_n = c_n;
   j->overwrite = overwrite;
+  j->jalpha = 1.0;
   return j;
 }
 
 void vt_seg(VtJob* j, int amap, int bmap, int K1, int K2, const int* afix, const int* bfix, const int* ea,
             const int* eb, double alpha) {
+  if (j->nseg >= VT_MAX_SEGS) {  // vt_finish reports it
+    j->seg[0].amap = -1;
+    return;
+  }
   VtSeg& s = j->seg[j->nseg++];
   s.amap = (int8_t)amap;
   s.bmap = (int8_t)bmap;
@@ -541,9 +547,12 @@ te_status vt_finish(VtBuild* b, int num_sms, double* part_scratch, int64_t scrat
   for (int q = 0; q < b->P.njobs; ++q) {
     VtJob& J = b->P.job[q];
     if (J.nseg == 0) return fail(TE_EINVAL, "view GEMM: job without segments");
-    for (int g = 0; g < J.nseg; ++g)
+    for (int g = 0; g < J.nseg; ++g) {
       if (J.seg[g].amap < 0 || J.seg[g].bmap < 0 || J.seg[g].amap >= b->nmaps || J.seg[g].bmap >= b->nmaps)
         return fail(TE_EINVAL, "view GEMM: segment without a tensor map");
+      if (J.seg[g].alpha != 1.0 && J.seg[g].alpha != -1.0)
+        return fail(TE_EINVAL, "view GEMM: segment factor other than +-1");
+    }
     const int64_t tiles = (int64_t)J.nm1 * J.nm2 * J.nn;
     if (!J.overwrite && part_scratch && tiles < num_sms && J.nblocks * VT_BLOCK_CHUNKS >= 8 * VT_SPLIT_CHUNKS) {
       J.nblocks = 0;
@@ -619,6 +628,42 @@ te_status vt_launch(Handle* h, VtBuild* b, cudaStream_t s) {
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(TE_ECUDA, "view GEMM reduce: %s", cudaGetErrorString(e));
+  return TE_OK;
+}
+
+int vt_ntile(int64_t n) {
+  const int64_t t = (n + VT_NT_MAX - 1) / VT_NT_MAX;
+  return (int)(((n + t - 1) / t + 15) / 16 * 16);
+}
+
+te_status vt_slice_maps(VtBank* k, const SliceSet& S, int o, int v, int nt, int* idx) {
+  const uint64_t V = (uint64_t)v, O = (uint64_t)o, NS = (uint64_t)S.ns, vp = (uint64_t)S.vp, op = (uint64_t)S.op;
+  const VtRoles XY{0, 1, 2, -1, 3}, ROW{0, 1, -1, -1, 2};
+  struct Spec {
+    const void* base;
+    uint64_t dims[5], str[5];
+    VtRoles r;
+    int rows2, rows1;
+  } sp[6] = {
+      {S.ovvv, {V, V, V, NS, O}, {1, vp, V * vp, (uint64_t)S.ovvv_plane, (uint64_t)S.ovvv_p}, XY, 16, 8},
+      {S.ovvv, {V, V, V, NS, O}, {1, V * vp, vp, (uint64_t)S.ovvv_plane, (uint64_t)S.ovvv_p}, XY, 16, 8},
+      {S.t2L, {O, V, V, NS, O}, {1, op, V * op, (uint64_t)S.t2L_plane, (uint64_t)S.t2L_q}, XY, 16, 8},
+      {S.t2L, {O, V, V, NS, O}, {1, V * op, op, (uint64_t)S.t2L_plane, (uint64_t)S.t2L_q}, XY, 16, 8},
+      {S.t2, {V, V, NS, O, O}, {1, vp, (uint64_t)S.t2_plane, (uint64_t)S.t2_rq, O * (uint64_t)S.t2_rq}, ROW, nt, 1},
+      {S.nooT, {O, V, NS, O, O}, {1, op, (uint64_t)S.nooT_plane, (uint64_t)S.nooT_pr, O * (uint64_t)S.nooT_pr}, ROW,
+       nt, 1},
+  };
+  for (int q = 0; q < 6; ++q) {
+    VtView w;
+    w.base = sp[q].base;
+    for (int d = 0; d < 5; ++d) {
+      w.dims[d] = sp[q].dims[d];
+      w.stride[d] = sp[q].str[d];
+    }
+    w.roles = sp[q].r;
+    const te_status st = vt_bank_add(k, w, sp[q].rows2, sp[q].rows1, &idx[q]);
+    if (st != TE_OK) return st;
+  }
   return TE_OK;
 }
 

@@ -2,7 +2,8 @@
 //
 // One launch runs a list of jobs.  A job is an output C[(m1, m2), n] in
 // float64 and a list of K segments, each
-//   C[(m1, m2), n] += alpha 2^(ea + eb) sum_{k1, k2} A[(m1, m2), (k1, k2)] B[n, (k1, k2)]
+//   C[(m1, m2), n] += jalpha alpha 2^(ea + eb) sum_{k1, k2} A[(m1, m2), (k1, k2)] B[n, (k1, k2)]
+// (alpha = +-1 per segment, jalpha per job)
 // where A and B are BF16 slice planes (value = 2^e sum_s slice_s) read through
 // TMA tensor maps whose innermost dimension is the contiguous K index k2.
 // Slice products a_i b_j with i + j <= NS - 1 go to three FP32 accumulators in
@@ -25,7 +26,7 @@
 namespace te {
 
 constexpr int VT_MAX_MAPS = 16;
-constexpr int VT_MAX_SEGS = 4;
+constexpr int VT_MAX_SEGS = 8;
 constexpr int VT_MAX_JOBS = 12;
 constexpr int VT_KC = 32;            // K elements per pipeline stage: 64-byte rows, 64-byte swizzle
 constexpr int VT_BLOCK_CHUNKS = 32;  // stages per exact accumulation block: K <= 1024
@@ -48,7 +49,7 @@ struct VtSeg {
   int afix[5], bfix[5];  // coordinates of the dimensions with no role (group indices)
   const int* ea;    // scale exponents (device)
   const int* eb;
-  double alpha;
+  double alpha;     // +1 or -1 (a job's common factor is VtJob::jalpha)
 };
 
 struct VtJob {
@@ -56,6 +57,7 @@ struct VtJob {
   int TA, TB, NT;   // row tile TA values of m1 x TB values of m2 (TA TB = 128); NT columns
   int nm1, nm2, nn, nsplit, nseg;
   int overwrite;    // the first block of a unit stores (nsplit == 1 only)
+  double jalpha;    // factor of the whole job (1 unless set)
   int64_t unit0;    // first unit of the job in the launch
   int64_t nblocks;  // accumulation blocks over all segments
   double* C;        // element (m1, m2, n) at m1 c_m1 + m2 c_m2 + n c_n
@@ -139,6 +141,18 @@ constexpr int VT_SPLIT_CHUNKS = 8;
 // Launch the units (grid: min(units, SMs)), then add the split partials of
 // every job into C in split order.
 te_status vt_launch(Handle* h, VtBuild* b, cudaStream_t s);
+
+// N tile for an output of n columns: at most VT_NT_MAX, a multiple of 16.
+int vt_ntile(int64_t n);
+
+struct SliceSet;
+// The six views of an exact-slice operand set (tc_prepare_slices) that the
+// four K segments of a G block read, rows (x, y) in tiles of 8 x 16 and z in
+// tiles of nt: idx[0..5] = ovvv rows (x, y), ovvv rows (y, x), t2L rows
+// (x, y), t2L rows (y, x), t2 rows z, nooT rows z.  Group coordinates: ovvv
+// and t2L take their occupied index at dimension 4; t2[r][q] takes q at 3 and
+// r at 4; nooT[p][r] takes r at 3 and p at 4.
+te_status vt_slice_maps(VtBank* k, const SliceSet& S, int o, int v, int nt, int* idx);
 
 // Tiled transpose of BF16 slice planes: for every plane p < np and batch b <
 // nb, dst[p][b][c][r] = src[p][b][r][c] over r < R, c < Cc (element strides

@@ -1070,11 +1070,6 @@ __global__ void __launch_bounds__(256) k_dw_layouts(const double* __restrict__ d
 }
 
 static int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
-// N tile of an output with n columns: at most VT_NT_MAX, a multiple of 16
-static int vt_ntile(int64_t n) {
-  const int64_t t = (n + VT_NT_MAX - 1) / VT_NT_MAX;
-  return (int)rup((n + t - 1) / t, 16);
-}
 
 struct VjpTcSizes {
   int ns, vp;
@@ -1236,26 +1231,10 @@ te_status run_vjp_tc(Handle* h, const te_cluster* c, int64_t t_begin, int64_t t_
   const VtRoles XY{0, 1, 2, -1, 3};       // k2 | rows y, x | slice
   const VtRoles ROW{0, 1, -1, -1, 2};     // k2 | rows | slice
   const VtRoles ZK{0, 2, -1, 1, 3};       // k2 | k1 | rows | slice
-  int m_on, m_ot, m_ln, m_lt, m_t2, m_no, m_l1n[3], m_l1t[3], m_lz[3], m_t2T, m_noo, m_ovT, m_t2P;
+  int m_g[6], m_l1n[3], m_l1t[3], m_lz[3], m_t2T, m_noo, m_ovT, m_t2P;
   const int64_t U1 = 1;
-  if ((st = add(sO, {U1 * v, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, U1 * vp, V * vp, U1 * S.ovvv_plane, U1 * S.ovvv_p},
-                XY, 16, 8, &m_on)) != TE_OK)
-    return st;
-  if ((st = add(sO, {U1 * v, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, V * vp, U1 * vp, U1 * S.ovvv_plane, U1 * S.ovvv_p},
-                XY, 16, 8, &m_ot)) != TE_OK)
-    return st;
-  if ((st = add(sL, {U1 * O, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, U1 * op, V * op, U1 * S.t2L_plane, U1 * S.t2L_q},
-                XY, 16, 8, &m_ln)) != TE_OK)
-    return st;
-  if ((st = add(sL, {U1 * O, U1 * v, U1 * v, U1 * NS, U1 * O}, {1, V * op, U1 * op, U1 * S.t2L_plane, U1 * S.t2L_q},
-                XY, 16, 8, &m_lt)) != TE_OK)
-    return st;
-  if ((st = add(sT, {U1 * v, U1 * v, U1 * NS, U1 * O, U1 * O},
-                {1, U1 * vp, U1 * S.t2_plane, U1 * S.t2_rq, O * S.t2_rq}, ROW, NTv, 1, &m_t2)) != TE_OK)
-    return st;
-  if ((st = add(sN, {U1 * O, U1 * v, U1 * NS, U1 * O, U1 * O},
-                {1, U1 * op, U1 * S.nooT_plane, U1 * S.nooT_pr, O * S.nooT_pr}, ROW, NTv, 1, &m_no)) != TE_OK)
-    return st;
+  if ((st = vt_slice_maps(&bank, S, o, v, NTv, m_g)) != TE_OK) return st;
+  const int m_on = m_g[0], m_ot = m_g[1], m_ln = m_g[2], m_lt = m_g[3], m_t2 = m_g[4], m_no = m_g[5];
   const int64_t lplane = V * V * vp;
   for (int b = 0; b < 3; ++b) {
     const bf* lb = lay + b * lay_stride;
