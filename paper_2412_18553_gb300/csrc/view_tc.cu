@@ -669,19 +669,32 @@ te_status vt_slice_maps(VtBank* k, const SliceSet& S, int o, int v, int nt, int*
 
 cudaError_t vt_transpose(const void* src, int64_t src_ps, int64_t src_bs, int64_t src_rs, void* dst, int64_t dst_ps,
                          int64_t dst_bs, int64_t dst_cs, int np, int nb, int R, int Cc, cudaStream_t s) {
-  if (nb > 65535 || R <= 0 || Cc <= 0 || (R + 63) / 64 > 65535) return cudaErrorInvalidValue;
+  if (np <= 0 || nb <= 0 || R <= 0 || Cc <= 0 || (R + 63) / 64 > 65535) return cudaErrorInvalidValue;
   const int pairs = (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 3) == 0 &&
                      ((src_ps | src_bs | src_rs | dst_ps | dst_bs | dst_cs) & 1) == 0)
                         ? 1
                         : 0;
-  // planes in groups whose (plane, batch) pairs fit the grid's z extent
-  const int per = std::max(1, std::min(np, 65535 / nb));
-  for (int p0 = 0; p0 < np; p0 += per) {
-    const int n = std::min(per, np - p0);
-    dim3 grid((unsigned)((Cc + 63) / 64), (unsigned)((R + 63) / 64), (unsigned)(n * nb));
-    k_vt_transpose<<<grid, dim3(32, 8), 0, s>>>(static_cast<const unsigned short*>(src) + p0 * src_ps, src_ps, src_bs,
-                                                 src_rs, static_cast<unsigned short*>(dst) + p0 * dst_ps, dst_ps, dst_bs,
-                                                 dst_cs, nb, R, Cc, pairs);
+  const unsigned short* s16 = static_cast<const unsigned short*>(src);
+  unsigned short* d16 = static_cast<unsigned short*>(dst);
+  // the grid's z extent covers (plane, batch) pairs: planes in groups when
+  // all batches fit, else one plane at a time in batch chunks
+  if (nb <= 65535) {
+    const int per = std::max(1, std::min(np, 65535 / nb));
+    for (int p0 = 0; p0 < np; p0 += per) {
+      const int n = std::min(per, np - p0);
+      dim3 grid((unsigned)((Cc + 63) / 64), (unsigned)((R + 63) / 64), (unsigned)(n * nb));
+      k_vt_transpose<<<grid, dim3(32, 8), 0, s>>>(s16 + p0 * src_ps, src_ps, src_bs, src_rs, d16 + p0 * dst_ps, dst_ps,
+                                                   dst_bs, dst_cs, nb, R, Cc, pairs);
+    }
+  } else {
+    for (int p0 = 0; p0 < np; ++p0)
+      for (int b0 = 0; b0 < nb; b0 += 65535) {
+        const int n = std::min(65535, nb - b0);
+        dim3 grid((unsigned)((Cc + 63) / 64), (unsigned)((R + 63) / 64), (unsigned)n);
+        k_vt_transpose<<<grid, dim3(32, 8), 0, s>>>(s16 + p0 * src_ps + b0 * src_bs, src_ps, src_bs, src_rs,
+                                                     d16 + p0 * dst_ps + b0 * dst_bs, dst_ps, dst_bs, dst_cs, n, R, Cc,
+                                                     pairs);
+      }
   }
   return cudaGetLastError();
 }
