@@ -668,27 +668,6 @@ cudaError_t slice_planes(const double* x, int64_t n, int ns, unsigned long long*
   return cudaGetLastError();
 }
 
-// NS 7-bit BF16 slices of dW~ (same layout), scale 2^-e with 2^e > max |dW~|
-template <int NS>
-__global__ void k_slice_dw(const double* __restrict__ dW, int64_t n, const unsigned long long* __restrict__ dwmax,
-                           int* __restrict__ e_out, __nv_bfloat16* __restrict__ planes) {
-  const double mx = __longlong_as_double((long long)*dwmax);
-  int ex = 0;
-  if (mx > 0.0) frexp(mx, &ex);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *e_out = ex;
-  const double sc = ldexp(1.0, -ex);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double t = dW[i] * sc;  // |t| < 1
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      t = t * 128.0;
-      const double m = rint(t);
-      t = t - m;
-      planes[k * n + i] = __float2bfloat16_rn((float)(m * (1.0 / (double)(1ull << (7 * (k + 1))))));
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Y and denominator reductions for one triple
 // ---------------------------------------------------------------------------
