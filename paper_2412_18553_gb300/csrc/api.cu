@@ -88,7 +88,9 @@ static te_status ensure_workspace(Handle* h, size_t bytes) {
     h->ws = nullptr;
     h->ws_bytes = 0;
   }
-  size_t want = bytes + bytes / 8;
+  // room to grow a little without reallocating; at most 1 GiB of it, so a
+  // workspace of a hundred gigabytes does not crowd out the caller's arrays
+  size_t want = bytes + std::min(bytes / 8, (size_t)1 << 30);
   if (h->ws_limit) want = std::min(want, h->ws_limit);
   if (h->log) std::fprintf(stderr, "[tenergy] workspace: %zu bytes (needed %zu)\n", want, bytes);
   if (cudaMalloc(&h->ws, want) != cudaSuccess) {
