@@ -157,9 +157,9 @@ te_status t_energy_batched(te_handle h, const te_cluster* cs, int64_t n,
  * of *g, every stored entry of every input treated as an independent variable
  * (no symmetrisation of t2 or of the integrals).  If e_out is non-null it
  * receives E(T) (one device double).  TE_FP64 runs every contraction in
- * float64; the other modes run them on the tensor cores in exact 7-bit BF16
- * slices (the TE_OZAKI scheme; gradients to ~1e-7 of each tensor's largest
- * entry), with the epilogue and all sums in float64.  Deterministic. */
+ * float64; the other modes run them on the tcgen05 tensor cores in exact
+ * 7-bit BF16 slices (the TE_OZAKI scheme; gradients to ~1e-7 of each tensor's
+ * largest entry), with the epilogue and all sums in float64.  Deterministic. */
 te_status t_energy_vjp(te_handle h, const te_cluster* c, te_precision p,
                        double gE, double* e_out, te_cluster_grad* g,
                        te_stream_t s);
@@ -202,8 +202,8 @@ te_status t_energy_vjp_batched(te_handle h, const te_cluster* cs, int64_t n,
  * e_triples (nullable, not both null): device [nocc (nocc+1)(nocc+2)/6 -
  * nocc] doubles, the per-triple shares in t_energy_triples' canonical order,
  * (1/3) sum over each triple's distinct orderings.  Costs about three
- * times t_energy's contractions, on the strided-view GEMMs of the adjoint;
- * deterministic.  Workspace (what te_reserve with TE_RESERVE_FRAG
+ * times t_energy's contractions, on the adjoint's GEMMs (DFMA in TE_FP64,
+ * tcgen05 in TE_OZAKI); deterministic.  Workspace (what te_reserve with TE_RESERVE_FRAG
  * allocates): about 8 nocc nvir^3 bytes for the transformed ovvv, plus three
  * exact-slice operand sets of the same size each in TE_OZAKI (about 34 GB at
  * nocc=32, nvir=320); TE_ENOMEM before any launch when the device cannot
