@@ -46,7 +46,7 @@ ETOL = {"fp64": 1e-12, "ozaki": 1e-7}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "ozaki"])
-@pytest.mark.parametrize("o,v,seed", [(2, 3, 1), (3, 7, 2), (4, 12, 3), (5, 17, 4), (3, 70, 5), (2, 131, 6)])
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 1), (3, 7, 2), (4, 12, 3), (5, 17, 4), (3, 70, 5), (2, 131, 6), (2, 211, 8)])
 def test_matches_oracle_gradient(te, o, v, seed, prec):
     cl = tegen.make_cluster(o, v, 4 * (o + v), seed)
     arrs = shuffled(cl.arrays(), seed)
